@@ -1,0 +1,445 @@
+"""Benchmark of the matrix-free SEM-NI monodomain time step on GB300.
+
+One benchmark step = one full time step of the partitioned scheme
+(Section 3, Algorithm 1) on the ~2 M DOF operator-sweep slab at p = 4
+(20 x 7 x 3 mm, 83 x 29 x 13 hexahedra, 2,064,933 nodes, vertices perturbed by
++-10 % of h, fibre angle rotating -60 -> +60 degrees through z):
+  fused ionic update + right-hand side  ->  Jacobi-CG to ||r|| <= 1e-10 ||b||
+  with one matrix-free operator apply per iteration.
+
+Prints ONE JSON line (rank 0).  ``value`` is whole-job DOF-steps per second
+(nodes advanced by one time step per second, summed over ranks);
+``roofline`` describes the operator-apply kernel, timed live with CUDA events
+on its launching stream inside the timed region; ``cpu_baseline`` is the CPU
+oracle timed on a bounded sample of the same workload.
+
+``--impl reference`` times the CPU oracle itself as the reference arm.
+``--sweep`` prints one extra JSON line per (p, quadrature) of the operator
+sweep (apply GDOF/s and roofline), not used by the default run.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "SEM operator GDOF/s and monodomain steps/s, mixed vs FP64 at 1e-8; % roofline"
+UNIT = "GDOF-steps/s"
+DT = 0.05            # ms
+RTOL = 1e-10
+MAXIT = 2000
+STIM_RADIUS = 1.5    # mm
+STIM_AMP = 50.0      # mV/ms
+STIM_T_OFF = 1.0     # ms
+FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64: 152 SMs x 2 DFMA/clk x 2 flop x ~2.06 GHz
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def apply_flops_per_element(p: int, quad: str) -> int:
+    """Algorithmic flops of one element apply with plain sum factorization:
+    SEM-NI 6 sweeps of 2 n^4, SEM 12 sweeps, plus 22 n^3 at the quadrature points."""
+    n = p + 1
+    sweeps = 6 if quad == "LGL" else 12
+    return sweeps * 2 * n ** 4 + 22 * n ** 3
+
+
+def apply_bytes_per_element(p: int) -> int:
+    """Algorithmic HBM bytes of one FP64 element apply: 7 metric doubles per
+    quadrature point, the int32 map, and u read + y written once per node."""
+    n = p + 1
+    return 56 * n ** 3 + 4 * n ** 3 + 16 * p ** 3
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        mhz, maxmhz, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                mhz.append(float(parts[1]))
+                maxmhz = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not mhz:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": maxmhz, "reasons": sorted(reasons),
+                "samples": len(mhz)}
+
+
+def workload(p=4):
+    s = W.sweep_slab(p)
+    ne = s.n_elements
+    tissue = (np.full(ne, 0.12), np.full(ne, 0.03), W.transmural_fiber_angles(s))
+    centre = W.seeded_point(s.lengths, STIM_RADIUS, seed=W.SEED_STIM)
+    return s, tissue, centre
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_sample(p, quad, target_s):
+    """Times the oracle's element-by-element apply (dense local matrices) over a
+    bounded sample of the workload's elements; returns (seconds per element,
+    elements timed)."""
+    from oracle import mesh as Mh
+    s, tissue, _ = workload(p)
+    sp_ = Mh.SlabSpace(s.flat_vertices(), s.nx, s.ny, s.nz, p, quad)
+    u = W.uniform_vector(sp_.ndofs, -85.0, 20.0, seed=W.SEED_U)
+    Mh.apply_element_by_element(sp_, tissue, u, 30.0, 1.0, elements=range(2))  # tables, caches
+    t0 = time.perf_counter()
+    done = 0
+    e = 0
+    while True:
+        Mh.apply_element_by_element(sp_, tissue, u, 30.0, 1.0, elements=range(e, e + 8))
+        e = (e + 8) % sp_.nelem
+        done += 8
+        if time.perf_counter() - t0 >= target_s:
+            break
+    return (time.perf_counter() - t0) / done, done
+
+
+def _oracle_worker(p, quad, target_s):
+    sec, done = oracle_sample(p, quad, target_s)
+    print(json.dumps({"sec_per_element": sec, "elements": done}))
+
+
+def run_oracle_subprocess(p, quad, target_s):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    cmd = [sys.executable, "-c",
+           f"import bench; bench._oracle_worker({p}, {quad!r}, {target_s})"]
+    r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_equivalent(sec_per_element, nelem, ndofs, applies_per_step):
+    """Oracle DOF-steps/s: one step needs `applies_per_step` applies over all elements."""
+    step_s = sec_per_element * nelem * applies_per_step
+    return ndofs / step_s / 1e9, step_s
+
+
+# --------------------------------------------------------------- GPU arm
+def init_dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, None
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl")
+    return rank, ws, dist
+
+
+def run_gpu(args):
+    import torch
+    rank, ws, dist = init_dist()
+    dev = torch.cuda.current_device()
+    from paper_2205_05136_gb300 import build as gbuild
+    if rank == 0:
+        gbuild.build()
+    if dist is not None:
+        dist.barrier()
+    import paper_2205_05136_gb300 as gb
+
+    p, quad = args.p, args.quad
+    s, tissue, centre = workload(p)
+    slab = gb.Slab(s.flat_vertices(), s.nx, s.ny, s.nz, p, quad, device=dev)
+    slab.set_tissue(*tissue)
+    slab.set_ionic()
+    slab.set_stimulus("sphere", (*centre, STIM_RADIUS), STIM_AMP, 0.0, STIM_T_OFF)
+    state = slab.new_state(-85.0, 1.0)
+    slab.set_timing(True)
+    stream = torch.cuda.current_stream()
+
+    # warm-up (the first step is BDF1; BDF2 from the second on)
+    wstats = state.step(DT, args.warmup, rtol=RTOL, maxit=MAXIT)
+
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev) as clk:
+        ev0.record(stream)
+        stats = state.step(DT, args.steps, rtol=RTOL, maxit=MAXIT)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    n_d, n_e = slab.ndofs, slab.nelem
+    value = ws * n_d * args.steps / (ms * 1e-3) / 1e9
+    iters = stats.cg_iters / max(args.steps, 1)
+    apply_ms = stats.apply_ms / max(stats.n_apply, 1)
+    flops = n_e * apply_flops_per_element(p, quad)
+    achieved_tf = flops / (apply_ms * 1e-3) / 1e12
+    algo_bytes = n_e * apply_bytes_per_element(p)
+
+    # end to end through the public C ABI with host buffers (page-locked), one
+    # step per call, continuing from the device state reached above
+    ck = state.checkpoint()
+    hu, hup = ck["u"].cpu().pin_memory(), ck["u_prev"].cpu().pin_memory()
+    hh, hhp = ck["h"].cpu().pin_memory(), ck["h_prev"].cpu().pin_memory()
+    n2 = ck["n"]
+    from paper_2205_05136_gb300 import capi
+    n_e2e = max(1, min(args.steps, 10))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(n_e2e):
+        capi.sem_step_host(slab.ctx, hu, hup, hh, hhp, n2 + k, DT, RTOL, 0.0, MAXIT)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_value = n_d * n_e2e / e2e_s / 1e9 * ws
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            r = run_oracle_subprocess(p, quad, args.cpu_seconds)
+            applies = iters + 1.0
+            v, step_s = cpu_equivalent(r["sec_per_element"], n_e, n_d, applies)
+            cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": (f"oracle element-by-element apply (dense local matrices, numpy fp64, 1 thread) "
+                              f"over {r['elements']} of {n_e} elements of this slab, "
+                              f"{r['sec_per_element'] * 1e3:.2f} ms/element; scaled to one time step of "
+                              f"{applies:.2f} applies ({step_s:.0f} s/step)")}
+        except Exception as exc:  # report, never fail the GPU line
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {exc}"}
+
+    pk = peaks()
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {
+            "workload": (f"monodomain BDF2 time step, SEM-NI Q{p} slab 20x7x3 mm, {s.nx}x{s.ny}x{s.nz} "
+                         f"hexahedra, {n_d} DOFs, +-10% vertex perturbation, fibres -60..+60 deg, "
+                         f"dt {DT} ms, Jacobi-CG rtol {RTOL}") if quad == "LGL" else
+                        (f"monodomain BDF2 time step, SEM Q{p} slab {s.nx}x{s.ny}x{s.nz}, {n_d} DOFs"),
+            "p": p, "quadrature": quad, "ndofs": n_d, "nelem": n_e,
+            "parallelism": f"replicas x{ws}",
+            "l2": f"inputs larger than L2: {n_e * 7 * (p + 1) ** 3 * 8 / 1e6:.0f} MB FP64 metric streamed per apply",
+        },
+        "steps_per_s": args.steps / (ms * 1e-3),
+        "cg_iters_per_step": iters,
+        "apply_gdofs": n_d / (apply_ms * 1e-3) / 1e9,
+        "apply_ms": apply_ms,
+        "roofline": {
+            "bound": "alu",
+            "achieved": achieved_tf,
+            "peak": FP64_PEAK_TFLOPS,
+            "unit": "TFLOP/s",
+            "frac": achieved_tf / FP64_PEAK_TFLOPS,
+            "traffic": args.traffic,
+            "kernel": f"sem_apply_kernel<P={p},{quad},f64,dot>",
+            "algorithmic_flops_per_launch": flops,
+            "algorithmic_bytes_per_launch": algo_bytes,
+            "hbm_frac_of_measured": (algo_bytes / (apply_ms * 1e-3) / 1e9) / pk.get("hbm_gbs", 6780.0),
+            "peak_note": "nominal FP64 1.25 TFLOP/s (no FP64 figure in MEASURED_PEAKS.json; DFMA probe measured 1.19)",
+        },
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * 8 * n_d,
+                "d2h_bytes_per_step": 4 * 8 * n_d, "steps": n_e2e},
+        "gpu_launches": int(stats.kernel_launches),
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
+    }
+    _ = wstats
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    slab.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_sweep(args):
+    """Operator-apply sweep: p = 1..6, SEM and SEM-NI, ~2 M DOFs each."""
+    import torch
+    import paper_2205_05136_gb300 as gb
+    from paper_2205_05136_gb300 import build as gbuild
+    gbuild.build()
+    for p in args.sweep_p:
+        for quad in ("LGL", "LG"):
+            s, tissue, _ = workload(p)
+            slab = gb.Slab(s.flat_vertices(), s.nx, s.ny, s.nz, p, quad)
+            slab.set_tissue(*tissue)
+            u = torch.tensor(W.uniform_vector(slab.ndofs, seed=W.SEED_U), device="cuda")
+            y = torch.empty_like(u)
+            for _ in range(3):
+                slab.apply(u, 30.0, 1.0, out=y)
+            torch.cuda.synchronize()
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(args.steps)]
+            for a, b in evs:
+                a.record()
+                slab.apply(u, 30.0, 1.0, out=y)
+                b.record()
+            torch.cuda.synchronize()
+            t = statistics.median(a.elapsed_time(b) for a, b in evs) * 1e-3
+            flops = slab.nelem * apply_flops_per_element(p, quad)
+            out = {"sweep": True, "p": p, "quad": quad, "ndofs": slab.ndofs, "nelem": slab.nelem,
+                   "apply_ms": t * 1e3, "gdofs": slab.ndofs / t / 1e9,
+                   "tflops_algorithmic": flops / t / 1e12,
+                   "frac_fp64_peak": flops / t / 1e12 / FP64_PEAK_TFLOPS,
+                   "gbs_algorithmic": slab.nelem * apply_bytes_per_element(p) / t / 1e9}
+            for prec, name in ((gb.SEM_PREC_FP32, "fp32"), (gb.SEM_PREC_FP32_BF16, "fp32_bf16")):
+                u32 = u.float()
+                y32 = torch.empty_like(u32)
+                slab.apply(u32, 30.0, 1.0, precision=prec, out=y32)
+                torch.cuda.synchronize()
+                ts = []
+                for _ in range(args.steps):
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record()
+                    slab.apply(u32, 30.0, 1.0, precision=prec, out=y32)
+                    b.record()
+                    torch.cuda.synchronize()
+                    ts.append(a.elapsed_time(b) * 1e-3)
+                t32 = statistics.median(ts)
+                out[f"{name}_gdofs"] = slab.ndofs / t32 / 1e9
+                out[f"{name}_apply_ms"] = t32 * 1e3
+            print(json.dumps(out), flush=True)
+            slab.close()
+            torch.cuda.empty_cache()
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle as it stands, on this workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    p, quad = args.p, args.quad
+    s, _, _ = workload(p)
+    nel = s.n_elements
+    ndofs = (p * s.nx + 1) * (p * s.ny + 1) * (p * s.nz + 1)
+    # applies per step of the GPU arm's solver on this workload (measured there)
+    applies = args.ref_applies_per_step
+    per_step = max(1.0, min(8.0, 150.0 / max(args.steps + args.warmup, 1)))
+    vals = []
+    for k in range(args.warmup + args.steps):
+        r = run_oracle_subprocess(p, quad, per_step)
+        v, _ = cpu_equivalent(r["sec_per_element"], nel, ndofs, applies)
+        if k >= args.warmup:
+            vals.append((v, r))
+    v = statistics.median(x[0] for x in vals)
+    spe = statistics.median(x[1]["sec_per_element"] for x in vals)
+    ms_per_step = spe * nel * applies * 1e3
+    sample = (f"each step: oracle element-by-element apply (numpy fp64, 1 thread) over a bounded "
+              f"sample of ~{per_step:.0f} s of this slab's {nel} elements, scaled to a full time step of "
+              f"{applies} applies")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"monodomain time step, SEM-NI Q{p} slab {s.nx}x{s.ny}x{s.nz}, {ndofs} DOFs",
+                   "p": p, "quadrature": quad},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--p", type=int, default=4)
+    ap.add_argument("--quad", default="LGL", choices=["LGL", "LG"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="dram bytes per apply launch from an ncu capture of the current kernel")
+    ap.add_argument("--ref-applies-per-step", type=float, default=12.0)
+    ap.add_argument("--sweep", action="store_true")
+    ap.add_argument("--sweep-p", type=int, nargs="*", default=[1, 2, 3, 4, 5, 6])
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours" and not args.sweep:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    elif args.sweep:
+        run_sweep(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

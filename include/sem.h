@@ -1,0 +1,206 @@
+/*
+ * sem.h -- C ABI of libsem, a GB300 (sm_103a) matrix-free spectral-element
+ * solver for the monodomain equation of cardiac electrophysiology.
+ *
+ * What it computes (arXiv 2205.05136):
+ *   - Section 2, Eq. (monodomain) and Eq. (diffusiontensor): the monodomain
+ *     equation with homogeneous Neumann data and the anisotropic conductivity
+ *     D = sigma_t I + (sigma_l - sigma_t) f f^T (sigma_n = sigma_t), fibre
+ *     f = (cos theta, sin theta, 0) per element.
+ *   - Section 3: Q_p spectral elements on hexahedra with the LGL nodal basis;
+ *     SEM integrates with the (p+1)-point Legendre-Gauss rule, SEM-NI with the
+ *     (p+1)-point Legendre-Gauss-Lobatto rule (diagonal mass).
+ *   - Section 3, Eqs. (ionic_discr), (monodomain_discr), (algebraic_ionic),
+ *     (linsys), (matrix_rhs): the partitioned semi-implicit BDF2 step with the
+ *     extrapolated potential u* = 2u^n - u^{n-1}.
+ *   - Section 4 and Algorithm 1: the matrix-free application of
+ *     A = alpha M + K by a cell loop with sum factorization, inside CG.
+ *
+ * Conventions
+ *   - Every function returns an int status: SEM_OK (0) or a negative
+ *     SEM_ERR_* code.  sem_last_error() returns a message for the last failure
+ *     on a context.  No function exits the process or traps on the device.
+ *   - "device" pointers point to memory of the context's CUDA device (for
+ *     example torch tensors); they are checked with cudaPointerGetAttributes and
+ *     rejected with SEM_ERR_ARG when they are host memory.  The library never
+ *     frees caller memory.
+ *   - Vectors over the global nodes have length ndofs (sem_num_dofs), node
+ *     (I, J, K) of the (p nx + 1) x (p ny + 1) x (p nz + 1) lattice at index
+ *     I + (p nx + 1) (J + (p ny + 1) K).  Per-element arrays have length
+ *     nx ny nz, element (ex, ey, ez) at ex + nx (ey + ny ez).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued on it; functions that return host scalars
+ *     (iteration counts, residuals) synchronise that stream only.
+ *   - Memory for mesh data, metric terms and solver work vectors is owned by
+ *     the context (cudaMalloc at creation or on first use) and released by
+ *     sem_destroy.
+ */
+#ifndef SEM_H
+#define SEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SEM_OK 0
+#define SEM_ERR_ARG (-1)           /* bad argument: null, size, range, host pointer */
+#define SEM_ERR_CUDA (-2)          /* a CUDA runtime call failed */
+#define SEM_ERR_BAD_MESH (-3)      /* det J <= 0 at some quadrature point */
+#define SEM_ERR_NOT_CONVERGED (-4) /* CG reached maxit; x holds the last iterate */
+#define SEM_ERR_NONFINITE (-5)     /* NaN or Inf met in a CG inner product */
+#define SEM_ERR_UNSUPPORTED (-6)   /* valid request this build does not provide */
+#define SEM_ERR_NOMEM (-7)         /* device allocation failed */
+
+#define SEM_QUAD_LG 0  /* SEM: (p+1)-point Legendre-Gauss quadrature */
+#define SEM_QUAD_LGL 1 /* SEM-NI: (p+1)-point Legendre-Gauss-Lobatto quadrature */
+
+#define SEM_PREC_FP64 0      /* double vectors, double metric, double arithmetic */
+#define SEM_PREC_FP32 1      /* float vectors, float metric, float arithmetic */
+#define SEM_PREC_FP32_BF16 2 /* float vectors, bfloat16 metric, float arithmetic */
+
+#define SEM_PC_NONE 0
+#define SEM_PC_JACOBI 1
+#define SEM_PC_GMG 2
+
+#define SEM_REGION_BOX 0    /* params: x0 y0 z0 x1 y1 z1 (closed box) */
+#define SEM_REGION_SPHERE 1 /* params: cx cy cz r (closed ball) */
+
+typedef struct sem_ctx sem_ctx;
+typedef struct sem_state sem_state;
+
+/* Parameters of the two-variable stand-in ionic model (the paper's TTP06
+ * equations are not printed in it):
+ *   v = (u - u_rest) / u_amp
+ *   I_ion = -u_amp (h v^2 (1 - v) / tau_in - v / tau_out)
+ *   s(v) = 1 / (1 + exp(-(v - v_gate) / kappa))
+ *   dh/dt = (1 - s)(1 - h) / tau_open - s h / tau_close
+ * Units: mV and ms, chi = C_m = 1 as in Section 2. */
+typedef struct {
+  double u_rest, u_amp, tau_in, tau_out, tau_open, tau_close, v_gate, kappa;
+} sem_ionic_params;
+
+/* Counters filled by sem_step and sem_cg_solve. */
+typedef struct {
+  int64_t steps;          /* time steps taken by this call */
+  int64_t cg_iters;       /* CG iterations summed over the call */
+  double last_residual;   /* ||r||_2 at the end of the last solve */
+  double apply_ms;        /* device time of operator-apply kernels (when timing on) */
+  int64_t n_apply;        /* operator-apply launches timed */
+  int64_t kernel_launches; /* libsem kernels launched by the call */
+} sem_stats;
+
+/* Library version string (static storage). */
+const char* sem_version(void);
+
+/* Create a context for a structured hexahedral slab of nx x ny x nz elements.
+ * vertices: HOST array of (nx+1)(ny+1)(nz+1) points x y z, x fastest; element
+ *   (ex, ey, ez) is the trilinear image of [-1,1]^3 through its 8 lattice
+ *   vertices (Section 3).  The vertices are copied.
+ * p: polynomial degree 1..6.  quad: SEM_QUAD_LG or SEM_QUAD_LGL.
+ * device: CUDA device ordinal; the context uses it for every call.
+ * Tissue defaults to sigma_l = 0.12, sigma_t = 0.03 mm^2/ms, theta = 0.
+ * Errors: SEM_ERR_ARG, SEM_ERR_BAD_MESH (det J <= 0), SEM_ERR_CUDA, SEM_ERR_NOMEM.
+ * On failure *out is NULL. */
+int sem_create(sem_ctx** out, int nx, int ny, int nz, const double* vertices, int p, int quad,
+               int device);
+
+/* Release every resource of the context (waits for its work to finish). */
+int sem_destroy(sem_ctx* ctx);
+
+/* Message of the last failing call on ctx (or of the last failed creation when
+ * ctx is NULL).  Static/ctx-owned storage, valid until the next call. */
+const char* sem_last_error(const sem_ctx* ctx);
+
+int sem_num_dofs(const sem_ctx* ctx, int64_t* ndofs);
+int sem_num_elements(const sem_ctx* ctx, int64_t* nelem);
+
+/* Physical coordinates of the global nodes: device double xyz[3 * ndofs] laid
+ * out as x[ndofs], y[ndofs], z[ndofs]. */
+int sem_dof_coords(sem_ctx* ctx, double* xyz, void* stream);
+
+/* Per-element conductivities and fibre angle (device double arrays of length
+ * nelem; theta in radians).  Recomputes the quadrature-point metric terms
+ * G = w |det J| J^{-1} D J^{-T} (Eq. diffusiontensor evaluated at every
+ * quadrature point, Section 4.2) of every precision in use. */
+int sem_set_tissue(sem_ctx* ctx, const double* sigma_l, const double* sigma_t,
+                   const double* theta, void* stream);
+
+/* y = alpha M u + beta K u (Algorithm 1, cell loop with sum factorization).
+ * precision SEM_PREC_FP64: u, y are device double[ndofs].
+ * precision SEM_PREC_FP32 / SEM_PREC_FP32_BF16: u, y are device float[ndofs].
+ * y is overwritten; u and y must not overlap. */
+int sem_apply(sem_ctx* ctx, double alpha, double beta, const void* u, void* y, int precision,
+              void* stream);
+
+/* Diagonal of alpha M + beta K: device double d[ndofs]. */
+int sem_diagonal(sem_ctx* ctx, double alpha, double beta, double* d, void* stream);
+
+/* Solve (alpha M + K) x = b by preconditioned CG (Section 4), warm-started
+ * from the x passed in.  Stops when ||r||_2 <= max(rtol ||b||_2, atol).
+ * precond: SEM_PC_NONE or SEM_PC_JACOBI (SEM_PC_GMG: SEM_ERR_UNSUPPORTED until
+ * built).  b, x: device double[ndofs].  iters / final_res may be NULL.
+ * Returns SEM_ERR_NOT_CONVERGED after maxit iterations (x = last iterate) and
+ * SEM_ERR_NONFINITE when an inner product is NaN or Inf.  Synchronises stream. */
+int sem_cg_solve(sem_ctx* ctx, double alpha, const double* b, double* x, double rtol,
+                 double atol, int maxit, int precond, int* iters, double* final_res,
+                 void* stream);
+
+/* Ionic model parameters (copied). */
+int sem_set_ionic(sem_ctx* ctx, const sem_ionic_params* prm);
+
+/* Applied current I_app = amplitude on the nodes inside the region, for
+ * t_on < t <= t_off (Section 5: a cuboid or a sphere of stimulation).
+ * params: host double[6] (box) or double[4] (sphere). */
+int sem_set_stimulus(sem_ctx* ctx, int region, const double* params, double amplitude,
+                     double t_on, double t_off, void* stream);
+
+/* Time-stepping state: u^n, u^{n-1}, h^n, h^{n-1} and the step counter n,
+ * device memory owned by the state. */
+int sem_state_create(sem_ctx* ctx, sem_state** out);
+int sem_state_destroy(sem_state* st);
+
+/* Set u^0 = u0 and h^0 = h0 (device double[ndofs]) and n = 0. */
+int sem_state_set(sem_state* st, const double* u0, const double* h0, void* stream);
+
+/* Copy the BDF2 state into device arrays: u^n -> u, u^{n-1} -> u_prev,
+ * h^n -> h, h^{n-1} -> h_prev (each may be NULL); *n_out (may be NULL)
+ * receives the number of steps taken.  With sem_state_restore this is a
+ * checkpoint of the full time-stepping state. */
+int sem_state_get(sem_state* st, double* u, double* u_prev, double* h, double* h_prev,
+                  int64_t* n_out, void* stream);
+
+/* Restore a full BDF2 state (device arrays of length ndofs) and its step count n
+ * (n = 0 makes the next step BDF1 and ignores u_prev / h_prev). */
+int sem_state_restore(sem_state* st, const double* u, const double* u_prev, const double* h,
+                      const double* h_prev, int64_t n, void* stream);
+
+/* Advance the state by nsteps time steps of size dt (ms): the first step from
+ * n = 0 is BDF1 (u* = u^0, A = M/dt + K), the following ones BDF2
+ * (u* = 2u^n - u^{n-1}, A = 3/(2 dt) M + K), each one
+ *   gate update and I_ion per node (Eq. ionic_discr),
+ *   b = M(history) - M I_ion + M I_app(t^{n+1})   (Eqs. algebraic_ionic, matrix_rhs),
+ *   CG solve warm-started from u^n to ||r|| <= max(rtol ||b||, atol).
+ * stats may be NULL.  Synchronises stream. */
+int sem_step(sem_ctx* ctx, sem_state* st, double dt, int nsteps, double rtol, double atol,
+             int maxit, int precond, sem_stats* stats, void* stream);
+
+/* One time step on HOST arrays of length ndofs: the state (u^n, u^{n-1},
+ * h^n, h^{n-1}, n) is copied to the device, advanced by one step as
+ * sem_step does, and the new state is written back in place (u_prev <- u,
+ * u <- u^{n+1}, h_prev <- h, h <- h^{n+1}).  Page-locked host memory makes
+ * the copies asynchronous.  Synchronises stream. */
+int sem_step_host(sem_ctx* ctx, double* u, double* u_prev, double* h, double* h_prev, int64_t n,
+                  double dt, double rtol, double atol, int maxit, int precond, sem_stats* stats,
+                  void* stream);
+
+/* Enable (1) or disable (0) CUDA-event timing of the operator-apply kernels
+ * inside sem_step / sem_cg_solve (reported in sem_stats). */
+int sem_set_timing(sem_ctx* ctx, int enable);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SEM_H */

@@ -1,0 +1,502 @@
+// C ABI of libsem (declared in include/sem.h): argument checking, context and
+// state management, and dispatch to the setup, apply and solver layers.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sem_context.cuh"
+
+using namespace sem;
+
+namespace sem {
+int apply_fp32(sem_ctx* ctx, double alpha, double beta, const float* u, float* y, bool bf16,
+               cudaStream_t s);
+}
+
+namespace {
+
+thread_local std::string g_create_err;
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int d) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != d) cudaSetDevice(d);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Device memory of the context's device (or managed memory); host pointers are rejected.
+bool is_device_ptr(const sem_ctx* ctx, const void* p) {
+  if (p == nullptr) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == ctx->device;
+}
+
+bool is_host_ptr(const void* p) {
+  if (p == nullptr) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return true;  // unregistered host memory
+  }
+  return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
+}
+
+#define CK_CTX(ctx)                                      \
+  do {                                                   \
+    if ((ctx) == nullptr) return SEM_ERR_ARG;            \
+  } while (0)
+
+#define CK_DEV(ptr, name)                                                                 \
+  do {                                                                                    \
+    if (!is_device_ptr(ctx, (ptr)))                                                       \
+      return fail(ctx, SEM_ERR_ARG, std::string(name) + " must be device memory of the context's device"); \
+  } while (0)
+
+#define SEM_CK(call)                                         \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+void free_level(Level& L) {
+  cudaFree(L.map);
+  cudaFree(L.evert);
+  cudaFree(L.metric);
+  cudaFree(L.metric32);
+  cudaFree(L.metric16);
+  cudaFree(L.mdiag);
+  cudaFree(L.kdiag);
+  cudaFree(L.xyz);
+  L = Level();
+}
+
+void free_ctx(sem_ctx* ctx) {
+  free_level(ctx->L);
+  cudaFree(ctx->sigma_l);
+  cudaFree(ctx->sigma_t);
+  cudaFree(ctx->theta);
+  cudaFree(ctx->d_flag);
+  cudaFree(ctx->stim_mask);
+  Workspace& w = ctx->ws;
+  cudaFree(w.r); cudaFree(w.z); cudaFree(w.p); cudaFree(w.Ap); cudaFree(w.invdiag);
+  cudaFree(w.b); cudaFree(w.g);
+  cudaFree(w.cg);
+  if (w.cg_host) cudaFreeHost(w.cg_host);
+  cudaFree(w.vec_partials);
+  cudaFree(w.tickets);
+  cudaFree(w.apply_partials);
+  cudaFree(w.dot_result);
+}
+
+__global__ void k_fill(int64_t n, double v, double* x) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = v;
+}
+
+__global__ void k_axpby(int64_t n, double a, const double* __restrict__ x, double b,
+                        const double* __restrict__ y, double* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = a * x[i] + b * y[i];
+}
+
+int grid_for(int64_t n) {
+  const int64_t g = (n + 255) / 256;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 8));
+}
+
+// Builds the structured numbering and element vertex arrays, uploads them and
+// computes metric, node coordinates and diagonals.
+int build_level(sem_ctx* ctx, int nx, int ny, int nz, const double* vertices, int p, int quad,
+                cudaStream_t s) {
+  Level& L = ctx->L;
+  L.p = p; L.quad = quad; L.n = p + 1;
+  L.nx = nx; L.ny = ny; L.nz = nz;
+  L.nelem = nx * ny * nz;
+  const int64_t NX = (int64_t)p * nx + 1, NY = (int64_t)p * ny + 1, NZ = (int64_t)p * nz + 1;
+  L.ndofs = NX * NY * NZ;
+  build_tables(p, quad, &L.tab);
+  const int n = L.n, n3 = n * n * n;
+  std::vector<int> map((size_t)L.nelem * n3);
+  std::vector<double> ev((size_t)L.nelem * 24);
+  for (int ez = 0; ez < nz; ++ez)
+    for (int ey = 0; ey < ny; ++ey)
+      for (int ex = 0; ex < nx; ++ex) {
+        const size_t e = (size_t)ex + (size_t)nx * (ey + (size_t)ny * ez);
+        for (int k = 0; k < n; ++k)
+          for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) {
+              const int64_t g = (ex * (int64_t)p + i) + NX * ((ey * (int64_t)p + j) + NY * (ez * (int64_t)p + k));
+              map[e * n3 + i + n * (j + n * k)] = (int)g;
+            }
+        for (int c = 0; c < 2; ++c)
+          for (int b = 0; b < 2; ++b)
+            for (int a = 0; a < 2; ++a) {
+              const size_t v = (size_t)(ex + a) + (size_t)(nx + 1) * ((ey + b) + (size_t)(ny + 1) * (ez + c));
+              for (int d = 0; d < 3; ++d) ev[e * 24 + (a + 2 * b + 4 * c) * 3 + d] = vertices[v * 3 + d];
+            }
+      }
+  const size_t nm = (size_t)L.nelem * kMetricComps * n3;
+  SEM_CK(cudaMalloc(&L.map, sizeof(int) * map.size()));
+  SEM_CK(cudaMalloc(&L.evert, sizeof(double) * ev.size()));
+  SEM_CK(cudaMalloc(&L.metric, sizeof(double) * nm));
+  SEM_CK(cudaMalloc(&L.mdiag, sizeof(double) * L.ndofs));
+  SEM_CK(cudaMalloc(&L.kdiag, sizeof(double) * L.ndofs));
+  SEM_CK(cudaMalloc(&L.xyz, sizeof(double) * 3 * L.ndofs));
+  SEM_CK(cudaMemcpyAsync(L.map, map.data(), sizeof(int) * map.size(), cudaMemcpyHostToDevice, s));
+  SEM_CK(cudaMemcpyAsync(L.evert, ev.data(), sizeof(double) * ev.size(), cudaMemcpyHostToDevice, s));
+  SEM_CK(cudaMalloc(&ctx->sigma_l, sizeof(double) * L.nelem));
+  SEM_CK(cudaMalloc(&ctx->sigma_t, sizeof(double) * L.nelem));
+  SEM_CK(cudaMalloc(&ctx->theta, sizeof(double) * L.nelem));
+  k_fill<<<grid_for(L.nelem), 256, 0, s>>>(L.nelem, 0.12, ctx->sigma_l);
+  k_fill<<<grid_for(L.nelem), 256, 0, s>>>(L.nelem, 0.03, ctx->sigma_t);
+  k_fill<<<grid_for(L.nelem), 256, 0, s>>>(L.nelem, 0.0, ctx->theta);
+  SEM_CK(cudaGetLastError());
+  SEM_CK(cudaMalloc(&ctx->d_flag, sizeof(int)));
+  SEM_CK(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), s));
+  SEM_CK(setup_geometry(L, ctx->sigma_l, ctx->sigma_t, ctx->theta, ctx->d_flag, s));
+  int bad = 0;
+  SEM_CK(cudaMemcpyAsync(&bad, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  SEM_CK(cudaStreamSynchronize(s));
+  if (bad) return fail(ctx, SEM_ERR_BAD_MESH, "non-positive Jacobian determinant at a quadrature point");
+  SEM_CK(setup_node_coords(L, s));
+  SEM_CK(setup_diagonals(L, s));
+  SEM_CK(cudaStreamSynchronize(s));
+  return SEM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sem_version(void) { return "libsem 0.1 (sm_103a)"; }
+
+const char* sem_last_error(const sem_ctx* ctx) {
+  if (ctx == nullptr) return g_create_err.c_str();
+  return ctx->err.c_str();
+}
+
+int sem_create(sem_ctx** out, int nx, int ny, int nz, const double* vertices, int p, int quad,
+               int device) {
+  if (out == nullptr) { g_create_err = "out is NULL"; return SEM_ERR_ARG; }
+  *out = nullptr;
+  if (nx < 1 || ny < 1 || nz < 1) { g_create_err = "nx, ny, nz must be >= 1"; return SEM_ERR_ARG; }
+  if (p < 1 || p > kMaxP) { g_create_err = "p must be in 1..6"; return SEM_ERR_ARG; }
+  if (quad != SEM_QUAD_LG && quad != SEM_QUAD_LGL) { g_create_err = "bad quadrature"; return SEM_ERR_ARG; }
+  if (vertices == nullptr) { g_create_err = "vertices is NULL"; return SEM_ERR_ARG; }
+  const double ndofs = (double(p) * nx + 1) * (double(p) * ny + 1) * (double(p) * nz + 1);
+  const double nel = double(nx) * ny * nz;
+  if (ndofs >= 2147483647.0 || nel * (p + 1) * (p + 1) * (p + 1) >= 2147483647.0) {
+    g_create_err = "mesh too large for 32-bit node indices";
+    return SEM_ERR_ARG;
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    g_create_err = "invalid CUDA device";
+    return SEM_ERR_ARG;
+  }
+  DeviceGuard guard(device);
+  sem_ctx* ctx = new (std::nothrow) sem_ctx();
+  if (!ctx) { g_create_err = "host allocation failed"; return SEM_ERR_NOMEM; }
+  ctx->device = device;
+  ctx->ionic = sem_ionic_params{-85.0, 100.0, 0.3, 6.0, 120.0, 150.0, 0.13, 0.01};
+  cudaStream_t s = nullptr;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+    g_create_err = "cudaStreamCreate failed";
+    delete ctx;
+    return SEM_ERR_CUDA;
+  }
+  int rc = build_level(ctx, nx, ny, nz, vertices, p, quad, s);
+  cudaStreamSynchronize(s);
+  cudaStreamDestroy(s);
+  if (rc != SEM_OK) {
+    g_create_err = ctx->err;
+    free_ctx(ctx);
+    delete ctx;
+    return rc;
+  }
+  *out = ctx;
+  return SEM_OK;
+}
+
+int sem_destroy(sem_ctx* ctx) {
+  if (ctx == nullptr) return SEM_OK;
+  DeviceGuard guard(ctx->device);
+  cudaDeviceSynchronize();
+  if (ctx->host_state) sem_state_destroy(ctx->host_state);
+  ctx->host_state = nullptr;
+  if (ctx->timing.start) cudaEventDestroy(ctx->timing.start);
+  if (ctx->timing.stop) cudaEventDestroy(ctx->timing.stop);
+  free_ctx(ctx);
+  delete ctx;
+  return SEM_OK;
+}
+
+int sem_num_dofs(const sem_ctx* ctx, int64_t* ndofs) {
+  if (ctx == nullptr || ndofs == nullptr) return SEM_ERR_ARG;
+  *ndofs = ctx->L.ndofs;
+  return SEM_OK;
+}
+
+int sem_num_elements(const sem_ctx* ctx, int64_t* nelem) {
+  if (ctx == nullptr || nelem == nullptr) return SEM_ERR_ARG;
+  *nelem = ctx->L.nelem;
+  return SEM_OK;
+}
+
+int sem_dof_coords(sem_ctx* ctx, double* xyz, void* stream) {
+  CK_CTX(ctx);
+  DeviceGuard guard(ctx->device);
+  CK_DEV(xyz, "xyz");
+  SEM_CK(cudaMemcpyAsync(xyz, ctx->L.xyz, sizeof(double) * 3 * ctx->L.ndofs,
+                         cudaMemcpyDeviceToDevice, as_stream(stream)));
+  return SEM_OK;
+}
+
+int sem_set_tissue(sem_ctx* ctx, const double* sigma_l, const double* sigma_t,
+                   const double* theta, void* stream) {
+  CK_CTX(ctx);
+  DeviceGuard guard(ctx->device);
+  CK_DEV(sigma_l, "sigma_l");
+  CK_DEV(sigma_t, "sigma_t");
+  CK_DEV(theta, "theta");
+  cudaStream_t s = as_stream(stream);
+  const size_t bytes = sizeof(double) * ctx->L.nelem;
+  SEM_CK(cudaMemcpyAsync(ctx->sigma_l, sigma_l, bytes, cudaMemcpyDeviceToDevice, s));
+  SEM_CK(cudaMemcpyAsync(ctx->sigma_t, sigma_t, bytes, cudaMemcpyDeviceToDevice, s));
+  SEM_CK(cudaMemcpyAsync(ctx->theta, theta, bytes, cudaMemcpyDeviceToDevice, s));
+  SEM_CK(setup_geometry(ctx->L, ctx->sigma_l, ctx->sigma_t, ctx->theta, ctx->d_flag, s));
+  SEM_CK(setup_diagonals(ctx->L, s));
+  ctx->ws.inv_alpha = -1.0;
+  return SEM_OK;
+}
+
+int sem_apply(sem_ctx* ctx, double alpha, double beta, const void* u, void* y, int precision,
+              void* stream) {
+  CK_CTX(ctx);
+  DeviceGuard guard(ctx->device);
+  CK_DEV(u, "u");
+  CK_DEV(y, "y");
+  if (u == y) return fail(ctx, SEM_ERR_ARG, "u and y must not overlap");
+  if (!std::isfinite(alpha) || !std::isfinite(beta)) return fail(ctx, SEM_ERR_ARG, "alpha and beta must be finite");
+  cudaStream_t s = as_stream(stream);
+  switch (precision) {
+    case SEM_PREC_FP64:
+      return apply_fp64(ctx, alpha, beta, static_cast<const double*>(u), static_cast<double*>(y), s);
+    case SEM_PREC_FP32:
+      return apply_fp32(ctx, alpha, beta, static_cast<const float*>(u), static_cast<float*>(y), false, s);
+    case SEM_PREC_FP32_BF16:
+      return apply_fp32(ctx, alpha, beta, static_cast<const float*>(u), static_cast<float*>(y), true, s);
+    default:
+      return fail(ctx, SEM_ERR_ARG, "unknown precision");
+  }
+}
+
+int sem_diagonal(sem_ctx* ctx, double alpha, double beta, double* d, void* stream) {
+  CK_CTX(ctx);
+  DeviceGuard guard(ctx->device);
+  CK_DEV(d, "d");
+  const int64_t n = ctx->L.ndofs;
+  k_axpby<<<grid_for(n), 256, 0, as_stream(stream)>>>(n, alpha, ctx->L.mdiag, beta, ctx->L.kdiag, d);
+  SEM_CK(cudaGetLastError());
+  return SEM_OK;
+}
+
+int sem_cg_solve(sem_ctx* ctx, double alpha, const double* b, double* x, double rtol,
+                 double atol, int maxit, int precond, int* iters, double* final_res,
+                 void* stream) {
+  CK_CTX(ctx);
+  DeviceGuard guard(ctx->device);
+  CK_DEV(b, "b");
+  CK_DEV(x, "x");
+  if (b == x) return fail(ctx, SEM_ERR_ARG, "b and x must not overlap");
+  if (maxit < 0 || !(rtol >= 0.0) || !(atol >= 0.0) || !std::isfinite(alpha))
+    return fail(ctx, SEM_ERR_ARG, "bad solver parameters");
+  return cg_solve(ctx, alpha, b, x, rtol, atol, maxit, precond, iters, final_res, nullptr,
+                  as_stream(stream));
+}
+
+int sem_set_ionic(sem_ctx* ctx, const sem_ionic_params* prm) {
+  CK_CTX(ctx);
+  if (prm == nullptr) return fail(ctx, SEM_ERR_ARG, "prm is NULL");
+  if (!(prm->tau_in > 0) || !(prm->tau_out > 0) || !(prm->tau_open > 0) ||
+      !(prm->tau_close > 0) || !(prm->kappa > 0) || !(prm->u_amp != 0))
+    return fail(ctx, SEM_ERR_ARG, "time constants, kappa and u_amp must be positive");
+  ctx->ionic = *prm;
+  return SEM_OK;
+}
+
+int sem_set_stimulus(sem_ctx* ctx, int region, const double* params, double amplitude,
+                     double t_on, double t_off, void* stream) {
+  CK_CTX(ctx);
+  DeviceGuard guard(ctx->device);
+  if (params == nullptr) return fail(ctx, SEM_ERR_ARG, "params is NULL");
+  if (region != SEM_REGION_BOX && region != SEM_REGION_SPHERE)
+    return fail(ctx, SEM_ERR_ARG, "unknown region");
+  if (!ctx->stim_mask) SEM_CK(cudaMalloc(&ctx->stim_mask, sizeof(double) * ctx->L.ndofs));
+  SEM_CK(setup_region_mask(ctx->L, region, params, ctx->stim_mask, as_stream(stream)));
+  ctx->stim_amp = amplitude;
+  ctx->stim_on = t_on;
+  ctx->stim_off = t_off;
+  return SEM_OK;
+}
+
+int sem_state_create(sem_ctx* ctx, sem_state** out) {
+  CK_CTX(ctx);
+  if (out == nullptr) return fail(ctx, SEM_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  DeviceGuard guard(ctx->device);
+  sem_state* st = new (std::nothrow) sem_state();
+  if (!st) return fail(ctx, SEM_ERR_NOMEM, "host allocation failed");
+  st->ctx = ctx;
+  for (int i = 0; i < 3; ++i) {
+    if (cudaMalloc(&st->U[i], sizeof(double) * ctx->L.ndofs) != cudaSuccess ||
+        cudaMalloc(&st->H[i], sizeof(double) * ctx->L.ndofs) != cudaSuccess) {
+      cudaGetLastError();
+      for (int j = 0; j < 3; ++j) { cudaFree(st->U[j]); cudaFree(st->H[j]); }
+      delete st;
+      return fail(ctx, SEM_ERR_NOMEM, "state allocation failed");
+    }
+  }
+  *out = st;
+  return SEM_OK;
+}
+
+int sem_state_destroy(sem_state* st) {
+  if (st == nullptr) return SEM_OK;
+  DeviceGuard guard(st->ctx->device);
+  cudaDeviceSynchronize();
+  for (int j = 0; j < 3; ++j) { cudaFree(st->U[j]); cudaFree(st->H[j]); }
+  delete st;
+  return SEM_OK;
+}
+
+int sem_state_set(sem_state* st, const double* u0, const double* h0, void* stream) {
+  if (st == nullptr) return SEM_ERR_ARG;
+  sem_ctx* ctx = st->ctx;
+  DeviceGuard guard(ctx->device);
+  CK_DEV(u0, "u0");
+  CK_DEV(h0, "h0");
+  cudaStream_t s = as_stream(stream);
+  const size_t bytes = sizeof(double) * ctx->L.ndofs;
+  st->cur = 0; st->prev = 1; st->next = 2; st->n = 0;
+  SEM_CK(cudaMemcpyAsync(st->U[0], u0, bytes, cudaMemcpyDeviceToDevice, s));
+  SEM_CK(cudaMemcpyAsync(st->U[1], u0, bytes, cudaMemcpyDeviceToDevice, s));
+  SEM_CK(cudaMemcpyAsync(st->H[0], h0, bytes, cudaMemcpyDeviceToDevice, s));
+  SEM_CK(cudaMemcpyAsync(st->H[1], h0, bytes, cudaMemcpyDeviceToDevice, s));
+  return SEM_OK;
+}
+
+int sem_state_get(sem_state* st, double* u, double* u_prev, double* h, double* h_prev,
+                  int64_t* n_out, void* stream) {
+  if (st == nullptr) return SEM_ERR_ARG;
+  sem_ctx* ctx = st->ctx;
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = as_stream(stream);
+  const size_t bytes = sizeof(double) * ctx->L.ndofs;
+  double* dst[4] = {u, u_prev, h, h_prev};
+  const double* src[4] = {st->U[st->cur], st->U[st->prev], st->H[st->cur], st->H[st->prev]};
+  const char* names[4] = {"u", "u_prev", "h", "h_prev"};
+  for (int i = 0; i < 4; ++i) {
+    if (dst[i] == nullptr) continue;
+    CK_DEV(dst[i], names[i]);
+    SEM_CK(cudaMemcpyAsync(dst[i], src[i], bytes, cudaMemcpyDeviceToDevice, s));
+  }
+  if (n_out) *n_out = st->n;
+  return SEM_OK;
+}
+
+int sem_state_restore(sem_state* st, const double* u, const double* u_prev, const double* h,
+                      const double* h_prev, int64_t n, void* stream) {
+  if (st == nullptr) return SEM_ERR_ARG;
+  sem_ctx* ctx = st->ctx;
+  DeviceGuard guard(ctx->device);
+  if (n < 0) return fail(ctx, SEM_ERR_ARG, "n must be >= 0");
+  CK_DEV(u, "u");
+  CK_DEV(h, "h");
+  if (n > 0) {
+    CK_DEV(u_prev, "u_prev");
+    CK_DEV(h_prev, "h_prev");
+  }
+  cudaStream_t s = as_stream(stream);
+  const size_t bytes = sizeof(double) * ctx->L.ndofs;
+  st->cur = 0; st->prev = 1; st->next = 2; st->n = n;
+  SEM_CK(cudaMemcpyAsync(st->U[0], u, bytes, cudaMemcpyDeviceToDevice, s));
+  SEM_CK(cudaMemcpyAsync(st->U[1], n > 0 ? u_prev : u, bytes, cudaMemcpyDeviceToDevice, s));
+  SEM_CK(cudaMemcpyAsync(st->H[0], h, bytes, cudaMemcpyDeviceToDevice, s));
+  SEM_CK(cudaMemcpyAsync(st->H[1], n > 0 ? h_prev : h, bytes, cudaMemcpyDeviceToDevice, s));
+  return SEM_OK;
+}
+
+int sem_step(sem_ctx* ctx, sem_state* st, double dt, int nsteps, double rtol, double atol,
+             int maxit, int precond, sem_stats* stats, void* stream) {
+  CK_CTX(ctx);
+  if (st == nullptr || st->ctx != ctx) return fail(ctx, SEM_ERR_ARG, "state does not belong to ctx");
+  if (!(dt > 0.0) || nsteps < 0 || maxit < 0 || !(rtol >= 0.0) || !(atol >= 0.0))
+    return fail(ctx, SEM_ERR_ARG, "bad step parameters");
+  DeviceGuard guard(ctx->device);
+  sem_stats local{};
+  sem_stats* sp = stats ? stats : &local;
+  std::memset(sp, 0, sizeof(*sp));
+  const double ms0 = ctx->timing.ms;
+  const int64_t c0 = ctx->timing.count;
+  const int64_t l0 = ctx->launches;
+  const int rc = time_steps(ctx, st, dt, nsteps, rtol, atol, maxit, precond, sp, as_stream(stream));
+  sp->apply_ms = ctx->timing.ms - ms0;
+  sp->n_apply = ctx->timing.count - c0;
+  sp->kernel_launches = ctx->launches - l0;
+  return rc;
+}
+
+int sem_step_host(sem_ctx* ctx, double* u, double* u_prev, double* h, double* h_prev, int64_t n,
+                  double dt, double rtol, double atol, int maxit, int precond, sem_stats* stats,
+                  void* stream) {
+  CK_CTX(ctx);
+  DeviceGuard guard(ctx->device);
+  if (!is_host_ptr(u) || !is_host_ptr(u_prev) || !is_host_ptr(h) || !is_host_ptr(h_prev))
+    return fail(ctx, SEM_ERR_ARG, "u, u_prev, h, h_prev must be host memory");
+  if (n < 0) return fail(ctx, SEM_ERR_ARG, "n must be >= 0");
+  if (ctx->host_state == nullptr) {
+    int rc = sem_state_create(ctx, &ctx->host_state);
+    if (rc != SEM_OK) return rc;
+  }
+  sem_state* st = ctx->host_state;
+  cudaStream_t s = as_stream(stream);
+  const size_t bytes = sizeof(double) * ctx->L.ndofs;
+  st->cur = 0; st->prev = 1; st->next = 2; st->n = n;
+  SEM_CK(cudaMemcpyAsync(st->U[0], u, bytes, cudaMemcpyHostToDevice, s));
+  SEM_CK(cudaMemcpyAsync(st->U[1], u_prev, bytes, cudaMemcpyHostToDevice, s));
+  SEM_CK(cudaMemcpyAsync(st->H[0], h, bytes, cudaMemcpyHostToDevice, s));
+  SEM_CK(cudaMemcpyAsync(st->H[1], h_prev, bytes, cudaMemcpyHostToDevice, s));
+  int rc = sem_step(ctx, st, dt, 1, rtol, atol, maxit, precond, stats, stream);
+  if (rc != SEM_OK) return rc;
+  SEM_CK(cudaMemcpyAsync(u_prev, st->U[st->prev], bytes, cudaMemcpyDeviceToHost, s));
+  SEM_CK(cudaMemcpyAsync(h_prev, st->H[st->prev], bytes, cudaMemcpyDeviceToHost, s));
+  SEM_CK(cudaMemcpyAsync(u, st->U[st->cur], bytes, cudaMemcpyDeviceToHost, s));
+  SEM_CK(cudaMemcpyAsync(h, st->H[st->cur], bytes, cudaMemcpyDeviceToHost, s));
+  SEM_CK(cudaStreamSynchronize(s));
+  return SEM_OK;
+}
+
+int sem_set_timing(sem_ctx* ctx, int enable) {
+  CK_CTX(ctx);
+  ctx->timing.enabled = enable != 0;
+  return SEM_OK;
+}
+
+}  // extern "C"

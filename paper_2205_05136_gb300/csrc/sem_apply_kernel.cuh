@@ -1,0 +1,332 @@
+// Matrix-free element kernel of the SEM / SEM-NI operator (Algorithm 1's
+// vectorized cell loop, Section 4) with sum factorization (Section 4.1):
+//
+//   y += sum_e  P_e^T (mass_coef M_e + K_e) P_e u          (P_e: gather through the map)
+//
+// per element, with n = p + 1 points per direction:
+//   SEM-NI (LGL quadrature on the nodes):
+//     g_d   = D along direction d of u_e                    3 sweeps
+//     q     = G g,  m = mass_coef W u                       per quadrature point
+//     y_e   = m + sum_d D^T along d of q_d                  3 sweeps
+//   SEM (LG quadrature):
+//     u_q   = Bi (x) Bi (x) Bi u_e                          3 sweeps to the Gauss points
+//     g_d   = Dg along d of u_q  (collocation derivative on the Gauss points)
+//     q, m  as above at the Gauss points
+//     y_e   = Bi^T (x) Bi^T (x) Bi^T (m + sum_d Dg^T along d of q_d)
+//
+// GPU mapping: one CTA holds E elements in shared memory (three n^3 tiles per
+// element).  A sweep along x or y gives each thread one 1-D line of n values
+// (n^2 FMAs on registers, matrix entries read from the kernel-parameter bank);
+// the z-sweep, the quadrature-point stage and the transposed z-sweep run on
+// the (i, j) columns in registers.  The result is scatter-added with
+// atomicAdd (RED) through the element-to-DOF map.
+#pragma once
+
+#include "sem_internal.cuh"
+
+namespace sem {
+
+constexpr int kApplyThreads = 256;
+
+// Elements per CTA: E * n^2 close to the 256 threads of the CTA.
+template <int P> struct ApplyCfg;
+template <> struct ApplyCfg<1> { static constexpr int E = 64; };
+template <> struct ApplyCfg<2> { static constexpr int E = 28; };
+template <> struct ApplyCfg<3> { static constexpr int E = 16; };
+template <> struct ApplyCfg<4> { static constexpr int E = 10; };
+template <> struct ApplyCfg<5> { static constexpr int E = 7; };
+template <> struct ApplyCfg<6> { static constexpr int E = 5; };
+
+__device__ __forceinline__ double ldmetric(const double* p) { return __ldg(p); }
+__device__ __forceinline__ float ldmetric(const float* p) { return __ldg(p); }
+__device__ __forceinline__ float ldmetric(const __nv_bfloat16* p) {
+  return __bfloat162float(__ldg(p));
+}
+
+// Base offset and stride of line l of an n^3 tile along direction DIR
+// (0: x-line (j,k), l = j + n k; 1: y-line (i,k), l = i + n k; 2: z-line (i,j), l = i + n j).
+template <int N, int DIR>
+__device__ __forceinline__ void line_geom(int l, int& base, int& stride) {
+  if (DIR == 0) { base = l * N; stride = 1; }
+  else if (DIR == 1) { const int i = l % N, k = l / N; base = k * N * N + i; stride = N; }
+  else { base = l; stride = N * N; }
+}
+
+// out[q] = sum_l M[q][l] in[l]
+template <int N, typename T>
+__device__ __forceinline__ void mat_line(const T (&M)[N][N], const T (&in)[N], T (&out)[N]) {
+#pragma unroll
+  for (int q = 0; q < N; ++q) {
+    T acc = M[q][0] * in[0];
+#pragma unroll
+    for (int l = 1; l < N; ++l) acc = fma(M[q][l], in[l], acc);
+    out[q] = acc;
+  }
+}
+
+// out[l] = sum_q M[q][l] in[q]  (ACC: out[l] += ...)
+template <int N, bool ACC, typename T>
+__device__ __forceinline__ void matT_line(const T (&M)[N][N], const T (&in)[N], T (&out)[N]) {
+#pragma unroll
+  for (int l = 0; l < N; ++l) {
+    T acc;
+    if (ACC) {
+      acc = out[l];
+#pragma unroll
+      for (int q = 0; q < N; ++q) acc = fma(M[q][l], in[q], acc);
+    } else {
+      acc = M[0][l] * in[0];
+#pragma unroll
+      for (int q = 1; q < N; ++q) acc = fma(M[q][l], in[q], acc);
+    }
+    out[l] = acc;
+  }
+}
+
+// dst = M along DIR of src, for every line of the E element tiles.
+template <int N, int E, int DIR, typename T>
+__device__ __forceinline__ void sweep(const T (&M)[N][N], const T* src, T* dst) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  for (int w = threadIdx.x; w < E * N2; w += blockDim.x) {
+    const int s = w / N2, l = w - s * N2;
+    int base, stride;
+    line_geom<N, DIR>(l, base, stride);
+    const T* ps = src + s * N3 + base;
+    T* pd = dst + s * N3 + base;
+    T in[N], out[N];
+#pragma unroll
+    for (int t = 0; t < N; ++t) in[t] = ps[t * stride];
+    mat_line<N>(M, in, out);
+#pragma unroll
+    for (int t = 0; t < N; ++t) pd[t * stride] = out[t];
+  }
+}
+
+// dst = M^T along DIR of src (ACC: dst += M^T src).  src may equal dst.
+template <int N, int E, int DIR, bool ACC, typename T>
+__device__ __forceinline__ void sweepT(const T (&M)[N][N], const T* src, T* dst) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  for (int w = threadIdx.x; w < E * N2; w += blockDim.x) {
+    const int s = w / N2, l = w - s * N2;
+    int base, stride;
+    line_geom<N, DIR>(l, base, stride);
+    const T* ps = src + s * N3 + base;
+    T* pd = dst + s * N3 + base;
+    T in[N], out[N];
+#pragma unroll
+    for (int t = 0; t < N; ++t) in[t] = ps[t * stride];
+    if (ACC) {
+#pragma unroll
+      for (int t = 0; t < N; ++t) out[t] = pd[t * stride];
+    }
+    matT_line<N, ACC>(M, in, out);
+#pragma unroll
+    for (int t = 0; t < N; ++t) pd[t * stride] = out[t];
+  }
+}
+
+// Block-wide sum of v (all threads must call); result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  v = 0.0;
+  if (warp == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    v = (lane < nw) ? red[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  }
+  return v;
+}
+
+// Writes this block's partial; the last block to arrive sums all partials in
+// block order (deterministic) and returns true in its thread 0 with *total set.
+__device__ __forceinline__ bool finish_reduction(double partial, double* partials,
+                                                 unsigned int* ticket, double* total,
+                                                 double* red) {
+  __shared__ bool is_last;
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = partial;
+    __threadfence();
+    const unsigned int t = atomicAdd(ticket, 1u);
+    is_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+  double v = 0.0;
+  // fixed assignment of partials to threads, then a fixed-shape tree
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+    v += ((volatile double*)partials)[b];
+  v = block_sum(v, red);
+  if (threadIdx.x == 0) {
+    *total = v;
+    *ticket = 0u;
+  }
+  return threadIdx.x == 0;
+}
+
+template <int P, int QUAD, typename T, typename MT, bool DOT, bool MASS_ONLY>
+__global__ void __launch_bounds__(kApplyThreads)
+    sem_apply_kernel(const ApplyArgs<T, MT> a, const __grid_constant__ KTab<P + 1, T> tab) {
+  constexpr int N = P + 1, N2 = N * N, N3 = N2 * N;
+  constexpr int E = ApplyCfg<P>::E;
+  __shared__ T sA[E * N3];
+  __shared__ T sB[E * N3];
+  __shared__ T sC[E * N3];
+  __shared__ double red[32];
+
+  if (a.done != nullptr && *a.done) return;
+  const int e0 = blockIdx.x * E;
+
+  // gather u_e = P_e u
+  for (int idx = threadIdx.x; idx < E * N3; idx += blockDim.x) {
+    const int s = idx / N3, loc = idx - s * N3, e = e0 + s;
+    sA[idx] = (e < a.nelem) ? a.u[__ldg(a.map + (size_t)e * N3 + loc)] : T(0);
+  }
+  __syncthreads();
+
+  if (QUAD == SEM_QUAD_LG) {  // values at the Gauss points
+    sweep<N, E, 0>(tab.Bi, sA, sB);
+    __syncthreads();
+    sweep<N, E, 1>(tab.Bi, sB, sC);
+    __syncthreads();
+    sweep<N, E, 2>(tab.Bi, sC, sA);
+    __syncthreads();
+  }
+
+  if (MASS_ONLY) {
+    for (int idx = threadIdx.x; idx < E * N3; idx += blockDim.x) {
+      const int s = idx / N3, loc = idx - s * N3, e = e0 + s;
+      if (e < a.nelem) {
+        const T W = ldmetric(a.metric + ((size_t)e * kMetricComps + 6) * N3 + loc);
+        sA[idx] = (a.mass_coef * W) * sA[idx];
+      }
+    }
+    __syncthreads();
+  } else {
+    // reference gradient along x and y (into sB, sC)
+    sweep<N, E, 0>(tab.D, sA, sB);
+    sweep<N, E, 1>(tab.D, sA, sC);
+    __syncthreads();
+    // z-gradient, quadrature-point stage and transposed z-sweep on the columns
+    for (int w = threadIdx.x; w < E * N2; w += blockDim.x) {
+      const int s = w / N2, c = w - s * N2, e = e0 + s;
+      if (e >= a.nelem) continue;
+      T* pa = sA + s * N3 + c;
+      T* pb = sB + s * N3 + c;
+      T* pc = sC + s * N3 + c;
+      T uz[N], g3[N], q3[N], m[N];
+#pragma unroll
+      for (int k = 0; k < N; ++k) uz[k] = pa[k * N2];
+      mat_line<N>(tab.D, uz, g3);
+      const MT* mp = a.metric + (size_t)e * kMetricComps * N3 + c;
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const T g1 = pb[k * N2], g2 = pc[k * N2];
+        const T G00 = ldmetric(mp + 0 * N3 + k * N2);
+        const T G01 = ldmetric(mp + 1 * N3 + k * N2);
+        const T G02 = ldmetric(mp + 2 * N3 + k * N2);
+        const T G11 = ldmetric(mp + 3 * N3 + k * N2);
+        const T G12 = ldmetric(mp + 4 * N3 + k * N2);
+        const T G22 = ldmetric(mp + 5 * N3 + k * N2);
+        const T W = ldmetric(mp + 6 * N3 + k * N2);
+        pb[k * N2] = fma(G02, g3[k], fma(G01, g2, G00 * g1));
+        pc[k * N2] = fma(G12, g3[k], fma(G11, g2, G01 * g1));
+        q3[k] = fma(G22, g3[k], fma(G12, g2, G02 * g1));
+        m[k] = (a.mass_coef * W) * uz[k];
+      }
+      matT_line<N, true>(tab.D, q3, m);
+#pragma unroll
+      for (int k = 0; k < N; ++k) pa[k * N2] = m[k];
+    }
+    __syncthreads();
+    sweepT<N, E, 1, true>(tab.D, sC, sA);
+    __syncthreads();
+    sweepT<N, E, 0, true>(tab.D, sB, sA);
+    __syncthreads();
+  }
+
+  if (QUAD == SEM_QUAD_LG) {  // back from the Gauss points to the nodes
+    sweepT<N, E, 0, false>(tab.Bi, sA, sB);
+    __syncthreads();
+    sweepT<N, E, 1, false>(tab.Bi, sB, sC);
+    __syncthreads();
+    sweepT<N, E, 2, false>(tab.Bi, sC, sA);
+    __syncthreads();
+  }
+
+  // scatter-add y += P_e^T y_e
+  double dot = 0.0;
+  for (int idx = threadIdx.x; idx < E * N3; idx += blockDim.x) {
+    const int s = idx / N3, loc = idx - s * N3, e = e0 + s;
+    if (e < a.nelem) {
+      const int g = __ldg(a.map + (size_t)e * N3 + loc);
+      T v = sA[idx];
+      if (a.scale_out) v *= a.out_scale;
+      atomicAdd(a.y + g, v);
+      if (DOT) dot = fma((double)a.u[g], (double)v, dot);
+    }
+  }
+  if (DOT) {
+    double bs = block_sum(dot, red);
+    double total;
+    if (finish_reduction(bs, a.dot_partials, a.dot_ticket, &total, red)) {
+      if (a.cg != nullptr) {
+        a.cg->pAp = total;
+        a.cg->alpha = a.cg->rz / total;
+      } else if (a.dot_out != nullptr) {
+        *a.dot_out = total;
+      }
+    }
+  }
+}
+
+// Launch helper shared by the precision-specific translation units.
+template <int P, int QUAD, typename T, typename MT>
+cudaError_t launch_apply_t(const Level& L, const ApplyArgs<T, MT>& a, bool mass_only, bool dot,
+                           cudaStream_t s) {
+  constexpr int N = P + 1;
+  KTab<N, T> tab;
+  for (int q = 0; q < N; ++q)
+    for (int l = 0; l < N; ++l) {
+      tab.D[q][l] = (T)(QUAD == SEM_QUAD_LG ? L.tab.Dg[q][l] : L.tab.D[q][l]);
+      tab.Bi[q][l] = (T)L.tab.Bi[q][l];
+    }
+  const int E = ApplyCfg<P>::E;
+  const int grid = (L.nelem + E - 1) / E;
+  if (grid == 0) return cudaSuccess;
+  if (mass_only) {
+    sem_apply_kernel<P, QUAD, T, MT, false, true><<<grid, kApplyThreads, 0, s>>>(a, tab);
+  } else if (dot) {
+    sem_apply_kernel<P, QUAD, T, MT, true, false><<<grid, kApplyThreads, 0, s>>>(a, tab);
+  } else {
+    sem_apply_kernel<P, QUAD, T, MT, false, false><<<grid, kApplyThreads, 0, s>>>(a, tab);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T, typename MT>
+cudaError_t dispatch_apply(const Level& L, const ApplyArgs<T, MT>& a, bool mass_only, bool dot,
+                           cudaStream_t s) {
+#define SEM_CASE(PP)                                                                  \
+  case PP:                                                                            \
+    return L.quad == SEM_QUAD_LG ? launch_apply_t<PP, SEM_QUAD_LG, T, MT>(L, a, mass_only, dot, s) \
+                                 : launch_apply_t<PP, SEM_QUAD_LGL, T, MT>(L, a, mass_only, dot, s);
+  switch (L.p) {
+    SEM_CASE(1)
+    SEM_CASE(2)
+    SEM_CASE(3)
+    SEM_CASE(4)
+    SEM_CASE(5)
+    SEM_CASE(6)
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef SEM_CASE
+}
+
+}  // namespace sem

@@ -1,0 +1,72 @@
+// Context and state objects behind the opaque sem_ctx / sem_state handles.
+#pragma once
+
+#include <string>
+
+#include "sem_internal.cuh"
+
+namespace sem {
+
+// Work vectors and device scalars of the solver (allocated on first use).
+struct Workspace {
+  bool ready = false;
+  double *r = nullptr, *z = nullptr, *p = nullptr, *Ap = nullptr, *invdiag = nullptr;
+  double *b = nullptr, *g = nullptr;
+  double inv_alpha = -1.0;   // alpha for which invdiag holds 1 / diag(alpha M + K)
+  CgScalars* cg = nullptr;   // device
+  CgScalars* cg_host = nullptr;  // page-locked mirror
+  double* vec_partials = nullptr;     // [kReduceSlots][kVecBlocksMax]
+  unsigned int* tickets = nullptr;    // [4]: vec, apply, spare
+  double* apply_partials = nullptr;   // [apply grid]
+  double* dot_result = nullptr;       // 1 double
+};
+
+struct Timing {
+  bool enabled = false;
+  cudaEvent_t start = nullptr, stop = nullptr;
+  double ms = 0.0;
+  int64_t count = 0;
+};
+
+}  // namespace sem
+
+struct sem_ctx {
+  int device = 0;
+  sem::Level L;
+  double* sigma_l = nullptr;  // per element
+  double* sigma_t = nullptr;
+  double* theta = nullptr;
+  int* d_flag = nullptr;      // setup error flag
+  sem_ionic_params ionic{};
+  double* stim_mask = nullptr;
+  double stim_amp = 0.0, stim_on = 0.0, stim_off = -1.0;
+  sem::Workspace ws;
+  sem::Timing timing;
+  int64_t launches = 0;             // libsem kernels launched so far
+  sem_state* host_state = nullptr;  // device copy of the state for sem_step_host
+  std::string err;
+};
+
+struct sem_state {
+  sem_ctx* ctx = nullptr;
+  double* U[3] = {nullptr, nullptr, nullptr};
+  double* H[3] = {nullptr, nullptr, nullptr};
+  int cur = 0, prev = 1, next = 2;
+  int64_t n = 0;
+};
+
+namespace sem {
+
+// Solver entry points (sem_solver.cu); return SEM_* codes and set ctx->err.
+int ensure_workspace(sem_ctx* ctx);
+int apply_fp64(sem_ctx* ctx, double alpha, double beta, const double* u, double* y,
+               cudaStream_t s);
+int cg_solve(sem_ctx* ctx, double alpha, const double* b, double* x, double rtol, double atol,
+             int maxit, int precond, int* iters, double* final_res, sem_stats* stats,
+             cudaStream_t s);
+int time_steps(sem_ctx* ctx, sem_state* st, double dt, int nsteps, double rtol, double atol,
+               int maxit, int precond, sem_stats* stats, cudaStream_t s);
+int fail(sem_ctx* ctx, int code, const std::string& msg);
+int cuda_fail(sem_ctx* ctx, cudaError_t e, const char* what);
+
+}  // namespace sem

@@ -1,0 +1,134 @@
+// Internal declarations of libsem (not part of the C ABI).
+//
+// Layout of the data in HBM (one context = one slab, one device):
+//   map      int32  [nelem][n^3]   local node a = i + n j + n^2 k -> global node
+//   metric   double [nelem][7][n^3] per quadrature point: G00 G01 G02 G11 G12 G22 W,
+//            G = w |det J| J^{-1} D J^{-T}, W = w |det J|  (element-blocked SoA)
+//   metric32 float / bf16 copies of the same array for the mixed-precision applies
+//   mdiag    double [ndofs]  diagonal of the assembled mass matrix
+//   kdiag    double [ndofs]  diagonal of the assembled stiffness matrix
+//   xyz      double [3][ndofs] node coordinates
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "sem.h"
+
+namespace sem {
+
+constexpr int kMaxP = 6;
+constexpr int kMaxN = kMaxP + 1;
+constexpr int kMetricComps = 7;
+
+// 1-D tables of one degree p and one quadrature kind (host side, double).
+struct Tables1D {
+  int p = 0, n = 0, quad = 0;
+  double xg[kMaxN] = {}, wg[kMaxN] = {};  // LGL nodes / weights
+  double xq[kMaxN] = {}, wq[kMaxN] = {};  // quadrature nodes / weights
+  double D[kMaxN][kMaxN] = {};   // D[q][l] = l_l'(xg_q)  (GLL collocation derivative)
+  double Bi[kMaxN][kMaxN] = {};  // Bi[q][l] = l_l(xq_q)   (GLL basis at quadrature points)
+  double Dg[kMaxN][kMaxN] = {};  // Dg[q][m] = g_m'(xq_q)  (collocation derivative on the quadrature points)
+};
+
+// Builds the tables of degree p (1..kMaxP) for quad SEM_QUAD_LG / SEM_QUAD_LGL.
+void build_tables(int p, int quad, Tables1D* t);
+
+// Tables in the kernel's arithmetic type, passed to kernels by value (kernel
+// parameter space): accesses with compile-time indices become constant-bank
+// operands of the FMA instructions.
+template <int N, typename T>
+struct KTab {
+  T D[N][N];   // derivative matrix used for the gradient (D for SEM-NI, Dg for SEM)
+  T Bi[N][N];  // interpolation GLL -> quadrature points (SEM only)
+};
+
+// Deterministic grid reductions: every block writes a partial, the last block
+// to finish (atomic ticket) sums the partials in block order.
+// Partials of the vector kernels: kVecBlocksMax per reduction slot.
+constexpr int kVecBlocksMax = 2048;
+constexpr int kReduceSlots = 4;
+
+// Device scalars of one CG solve.
+struct CgScalars {
+  double rz;      // r . z of the current iterate
+  double rr;      // r . r
+  double bb;      // b . b
+  double pAp;     // p . A p
+  double alpha;   // step length
+  double beta;    // conjugation coefficient
+  double tol2;    // squared stopping threshold on ||r||
+  int done;       // 1 when converged or failed
+  int iters;      // iterations taken
+  int status;     // 0 ok, SEM_ERR_NONFINITE
+  int pad;
+};
+
+struct Level {
+  int p = 0, quad = 0, n = 0;
+  int nx = 0, ny = 0, nz = 0;
+  int nelem = 0;
+  int64_t ndofs = 0;
+  Tables1D tab;
+  int* map = nullptr;
+  double* evert = nullptr;   // [nelem][8][3] element vertices
+  double* metric = nullptr;  // [nelem][7][n^3]
+  float* metric32 = nullptr;
+  __nv_bfloat16* metric16 = nullptr;
+  bool metric32_valid = false, metric16_valid = false;
+  double* mdiag = nullptr;
+  double* kdiag = nullptr;
+  double* xyz = nullptr;
+};
+
+// Arguments of the element kernel y += A_e u_e (scatter-add into y).
+template <typename T, typename MT>
+struct ApplyArgs {
+  const int* map;
+  const MT* metric;
+  const T* u;
+  T* y;
+  int nelem;
+  T mass_coef;        // coefficient of the mass term inside the element kernel
+  T out_scale;        // factor applied to the element result before the scatter
+  int scale_out;      // out_scale != 1
+  const int* done;    // optional: skip all work when *done != 0
+  // optional fused u . (A u) (CG's p . A p), finished by the last block;
+  // dot_partials holds one double per CTA of the launch
+  double* dot_partials;
+  unsigned int* dot_ticket;
+  CgScalars* cg;      // when set, the finishing block writes pAp and alpha = rz / pAp
+  double* dot_out;    // otherwise the total goes here
+};
+using ApplyArgs64 = ApplyArgs<double, double>;
+
+// Kernel launchers (sem_apply_fp64.cu, sem_apply_fp32.cu).
+cudaError_t launch_apply_fp64(const Level& L, const ApplyArgs64& a, bool mass_only, cudaStream_t s);
+cudaError_t launch_apply_fp32(const Level& L, const ApplyArgs<float, float>& a, bool mass_only,
+                              cudaStream_t s);
+cudaError_t launch_apply_bf16(const Level& L, const ApplyArgs<float, __nv_bfloat16>& a,
+                              bool mass_only, cudaStream_t s);
+int apply_grid_blocks(const Level& L);
+
+// Setup kernels (sem_setup.cu).
+cudaError_t setup_geometry(Level& L, const double* sigma_l, const double* sigma_t,
+                           const double* theta, int* d_bad, cudaStream_t s);
+cudaError_t setup_diagonals(Level& L, cudaStream_t s);
+cudaError_t setup_metric_lowp(Level& L, bool bf16, cudaStream_t s);
+cudaError_t setup_node_coords(Level& L, cudaStream_t s);
+cudaError_t setup_region_mask(const Level& L, int region, const double* prm, double* mask,
+                              cudaStream_t s);
+
+// Vector kernels (sem_solver.cu).
+int vec_blocks(int64_t n);
+cudaError_t vec_axpby_diag(int64_t n, double a, const double* x, double b, const double* y,
+                           double* out, cudaStream_t s);  // out = a x + b y
+cudaError_t vec_inv_diag(int64_t n, double alpha, const double* mdiag, const double* kdiag,
+                         double* inv, cudaStream_t s);     // inv = 1/(alpha m + k)
+cudaError_t vec_scale_mul(int64_t n, double a, const double* d, const double* x, double* y,
+                          cudaStream_t s);                 // y = a d x
+
+}  // namespace sem

@@ -1,0 +1,476 @@
+// Solver layer: fused CG vector kernels, the preconditioned CG driver
+// (Section 4: A is SPD, CG / PCG; one matrix-free apply per iteration), and
+// the partitioned BDF time step (Section 3, Eqs. ionic_discr - matrix_rhs,
+// Algorithm 1).
+//
+// One CG iteration is three kernels on the caller's stream:
+//   apply   Ap += A p (element kernel) and p . Ap; its last CTA sets
+//           alpha = (r . z) / (p . Ap)
+//   xr      x += alpha p, r -= alpha Ap, z = Jacobi(r), r . z, r . r; its last
+//           CTA sets beta, the iteration count and the convergence flag
+//   p       p = z + beta p, Ap = 0
+// Every reduction is deterministic (per-CTA partials summed in CTA order by
+// the last CTA).  Scalars stay on the device; the host reads them once per
+// chunk of iterations, and kernels of a finished solve return at once.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "sem_apply_kernel.cuh"
+#include "sem_context.cuh"
+
+namespace sem {
+namespace {
+
+constexpr int kVecThreads = 256;
+
+int vec_grid(int64_t n) {
+  const int64_t want = (n + kVecThreads - 1) / kVecThreads;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(want, 152 * 8));
+}
+
+// Sum K values over the grid; the last CTA gets the totals (thread 0 returns true).
+template <int K>
+__device__ __forceinline__ bool grid_sums(double (&v)[K], double* partials, unsigned int* ticket,
+                                          double (&tot)[K]) {
+  __shared__ double red[K][32];
+  __shared__ bool is_last;
+  double bs[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    bs[k] = block_sum(v[k], red[k]);
+  }
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) partials[k * kVecBlocksMax + blockIdx.x] = bs[k];
+    __threadfence();
+    const unsigned int t = atomicAdd(ticket, 1u);
+    is_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+      s += ((volatile double*)partials)[k * kVecBlocksMax + b];
+    tot[k] = block_sum(s, red[k]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *ticket = 0u;
+  return threadIdx.x == 0;
+}
+
+__global__ void k_inv_diag(int64_t n, double alpha, const double* __restrict__ m,
+                           const double* __restrict__ k, double* __restrict__ inv) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    inv[i] = 1.0 / fma(alpha, m[i], k[i]);
+}
+
+__global__ void k_scale_mul(int64_t n, double a, const double* __restrict__ d,
+                            const double* __restrict__ x, double* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = a * d[i] * x[i];
+}
+
+__global__ void k_scale_mul32(int64_t n, float a, const double* __restrict__ d,
+                              const float* __restrict__ x, float* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = a * (float)d[i] * x[i];
+}
+
+// r = b - Ap, z = Jacobi(r), p = z, Ap = 0; r.z, r.r, b.b; convergence test.
+__global__ void __launch_bounds__(kVecThreads)
+    k_cg_init(int64_t n, const double* __restrict__ b, double* __restrict__ Ap,
+              const double* __restrict__ inv, double* __restrict__ r, double* __restrict__ z,
+              double* __restrict__ p, CgScalars* cg, double* partials, unsigned int* ticket,
+              double rtol, double atol) {
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double bi = b[i];
+    const double ri = bi - Ap[i];
+    const double zi = inv ? inv[i] * ri : ri;
+    r[i] = ri;
+    z[i] = zi;
+    p[i] = zi;
+    Ap[i] = 0.0;
+    v[0] = fma(ri, zi, v[0]);
+    v[1] = fma(ri, ri, v[1]);
+    v[2] = fma(bi, bi, v[2]);
+  }
+  double tot[3];
+  if (grid_sums<3>(v, partials, ticket, tot)) {
+    cg->rz = tot[0];
+    cg->rr = tot[1];
+    cg->bb = tot[2];
+    cg->tol2 = fmax(rtol * rtol * tot[2], atol * atol);
+    cg->iters = 0;
+    cg->status = 0;
+    cg->beta = 0.0;
+    const bool finite = isfinite(tot[0]) && isfinite(tot[1]) && isfinite(tot[2]);
+    if (!finite) cg->status = SEM_ERR_NONFINITE;
+    cg->done = (!finite || tot[1] <= cg->tol2) ? 1 : 0;
+  }
+}
+
+// x += alpha p, r -= alpha Ap, z = Jacobi(r); r.z, r.r; beta, convergence.
+__global__ void __launch_bounds__(kVecThreads)
+    k_cg_xr(int64_t n, double* __restrict__ x, const double* __restrict__ p,
+            const double* __restrict__ Ap, double* __restrict__ r, const double* __restrict__ inv,
+            double* __restrict__ z, CgScalars* cg, double* partials, unsigned int* ticket) {
+  if (cg->done) return;
+  const double alpha = cg->alpha;
+  double v[2] = {0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] = fma(alpha, p[i], x[i]);
+    const double ri = fma(-alpha, Ap[i], r[i]);
+    const double zi = inv ? inv[i] * ri : ri;
+    r[i] = ri;
+    z[i] = zi;
+    v[0] = fma(ri, zi, v[0]);
+    v[1] = fma(ri, ri, v[1]);
+  }
+  double tot[2];
+  if (grid_sums<2>(v, partials, ticket, tot)) {
+    cg->beta = tot[0] / cg->rz;
+    cg->rz = tot[0];
+    cg->rr = tot[1];
+    cg->iters += 1;
+    const bool finite = isfinite(tot[0]) && isfinite(tot[1]) && isfinite(alpha);
+    if (!finite) {
+      cg->status = SEM_ERR_NONFINITE;
+      cg->done = 1;
+    } else if (tot[1] <= cg->tol2) {
+      cg->done = 1;
+    }
+  }
+}
+
+// p = z + beta p, Ap = 0.
+__global__ void __launch_bounds__(kVecThreads)
+    k_cg_p(int64_t n, const double* __restrict__ z, double* __restrict__ p,
+           double* __restrict__ Ap, const CgScalars* cg) {
+  if (cg->done) return;
+  const double beta = cg->beta;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    p[i] = fma(beta, p[i], z[i]);
+    Ap[i] = 0.0;
+  }
+}
+
+struct IonicArgs {
+  double u_rest, inv_amp, u_amp, inv_tau_in, inv_tau_out, inv_tau_open, inv_tau_close, v_gate,
+      inv_kappa;
+};
+
+// Per node (Algorithm 1, DOF loop; Eq. ionic_discr):
+//   u* = u^n (first step) or 2 u^n - u^{n-1}
+//   gate: BDF1 / BDF2 equation, affine in h^{n+1}, solved in closed form
+//   I_ion(u*, h^{n+1}); g = history/dt terms - I_ion + I_app
+//   out = mdiag * g (SEM-NI: M diagonal) or g (SEM: M g applied afterwards)
+//   x0 = u^n (warm start of CG)
+__global__ void __launch_bounds__(kVecThreads)
+    k_ionic_rhs(int64_t n, const double* __restrict__ un, const double* __restrict__ unm1,
+                const double* __restrict__ hn, const double* __restrict__ hnm1,
+                double* __restrict__ hnext, double* __restrict__ x0, double* __restrict__ out,
+                const double* __restrict__ mdiag, const double* __restrict__ mask, double iapp,
+                const IonicArgs prm, double dt, int first) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double u0 = un[i];
+    const double u1 = first ? u0 : unm1[i];
+    const double us = first ? u0 : 2.0 * u0 - u1;
+    const double v = (us - prm.u_rest) * prm.inv_amp;
+    const double sw = 1.0 / (1.0 + exp(-(v - prm.v_gate) * prm.inv_kappa));
+    const double ra = (1.0 - sw) * prm.inv_tau_open;
+    const double rb = sw * prm.inv_tau_close;
+    double h, hist;
+    if (first) {
+      h = (hn[i] + dt * ra) / (1.0 + dt * (ra + rb));
+      hist = u0 / dt;
+    } else {
+      h = (4.0 * hn[i] - hnm1[i] + 2.0 * dt * ra) / (3.0 + 2.0 * dt * (ra + rb));
+      hist = (4.0 * u0 - u1) / (2.0 * dt);
+    }
+    const double iion = -prm.u_amp * (h * v * v * (1.0 - v) * prm.inv_tau_in - v * prm.inv_tau_out);
+    double g = hist - iion;
+    if (mask != nullptr) g += iapp * mask[i];
+    hnext[i] = h;
+    x0[i] = u0;
+    out[i] = mdiag ? mdiag[i] * g : g;
+  }
+}
+
+}  // namespace
+
+int vec_blocks(int64_t n) { return vec_grid(n); }
+
+int fail(sem_ctx* ctx, int code, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+int cuda_fail(sem_ctx* ctx, cudaError_t e, const char* what) {
+  return fail(ctx, e == cudaErrorMemoryAllocation ? SEM_ERR_NOMEM : SEM_ERR_CUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define SEM_CK(call)                                      \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+int ensure_workspace(sem_ctx* ctx) {
+  Workspace& w = ctx->ws;
+  if (w.ready) return SEM_OK;
+  const size_t n = (size_t)ctx->L.ndofs;
+  double** vecs[] = {&w.r, &w.z, &w.p, &w.Ap, &w.invdiag, &w.b, &w.g};
+  for (double** v : vecs) SEM_CK(cudaMalloc(v, sizeof(double) * n));
+  SEM_CK(cudaMalloc(&w.cg, sizeof(CgScalars)));
+  SEM_CK(cudaMemset(w.cg, 0, sizeof(CgScalars)));
+  SEM_CK(cudaMallocHost(&w.cg_host, sizeof(CgScalars)));
+  SEM_CK(cudaMalloc(&w.vec_partials, sizeof(double) * kReduceSlots * kVecBlocksMax));
+  SEM_CK(cudaMalloc(&w.tickets, sizeof(unsigned int) * 4));
+  SEM_CK(cudaMemset(w.tickets, 0, sizeof(unsigned int) * 4));
+  const int ag = std::max(1, apply_grid_blocks(ctx->L));
+  SEM_CK(cudaMalloc(&w.apply_partials, sizeof(double) * ag));
+  SEM_CK(cudaMalloc(&w.dot_result, sizeof(double)));
+  w.inv_alpha = -1.0;
+  w.ready = true;
+  return SEM_OK;
+}
+
+namespace {
+
+ApplyArgs64 base_args(sem_ctx* ctx, double alpha, double beta, const double* u, double* y) {
+  ApplyArgs64 a{};
+  a.map = ctx->L.map;
+  a.metric = ctx->L.metric;
+  a.u = u;
+  a.y = y;
+  a.nelem = ctx->L.nelem;
+  a.mass_coef = alpha / beta;
+  a.out_scale = beta;
+  a.scale_out = beta != 1.0;
+  return a;
+}
+
+}  // namespace
+
+int apply_fp64(sem_ctx* ctx, double alpha, double beta, const double* u, double* y,
+               cudaStream_t s) {
+  const Level& L = ctx->L;
+  if (beta == 0.0) {
+    if (L.quad == SEM_QUAD_LGL) {
+      k_scale_mul<<<vec_grid(L.ndofs), kVecThreads, 0, s>>>(L.ndofs, alpha, L.mdiag, u, y);
+      ctx->launches += 1;
+      SEM_CK(cudaGetLastError());
+      return SEM_OK;
+    }
+    SEM_CK(cudaMemsetAsync(y, 0, sizeof(double) * L.ndofs, s));
+    ApplyArgs64 a = base_args(ctx, alpha, 1.0, u, y);
+    SEM_CK(launch_apply_fp64(L, a, true, s));
+    ctx->launches += 1;
+    return SEM_OK;
+  }
+  SEM_CK(cudaMemsetAsync(y, 0, sizeof(double) * L.ndofs, s));
+  ApplyArgs64 a = base_args(ctx, alpha, beta, u, y);
+  SEM_CK(launch_apply_fp64(L, a, false, s));
+  ctx->launches += 1;
+  return SEM_OK;
+}
+
+int apply_fp32(sem_ctx* ctx, double alpha, double beta, const float* u, float* y, bool bf16,
+               cudaStream_t s) {
+  Level& L = ctx->L;
+  if (bf16 && !L.metric16_valid) {
+    if (!L.metric16)
+      SEM_CK(cudaMalloc(&L.metric16, sizeof(__nv_bfloat16) * (size_t)L.nelem * kMetricComps *
+                                         L.n * L.n * L.n));
+    SEM_CK(setup_metric_lowp(L, true, s));
+  }
+  if (!bf16 && !L.metric32_valid) {
+    if (!L.metric32)
+      SEM_CK(cudaMalloc(&L.metric32, sizeof(float) * (size_t)L.nelem * kMetricComps * L.n * L.n * L.n));
+    SEM_CK(setup_metric_lowp(L, false, s));
+  }
+  if (beta == 0.0 && L.quad == SEM_QUAD_LGL) {
+    k_scale_mul32<<<vec_grid(L.ndofs), kVecThreads, 0, s>>>(L.ndofs, (float)alpha, L.mdiag, u, y);
+    SEM_CK(cudaGetLastError());
+    return SEM_OK;
+  }
+  SEM_CK(cudaMemsetAsync(y, 0, sizeof(float) * L.ndofs, s));
+  const bool mass_only = beta == 0.0;
+  const double bb = mass_only ? 1.0 : beta;
+  if (bf16) {
+    ApplyArgs<float, __nv_bfloat16> a{};
+    a.map = L.map; a.metric = L.metric16; a.u = u; a.y = y; a.nelem = L.nelem;
+    a.mass_coef = (float)(alpha / bb); a.out_scale = (float)bb; a.scale_out = bb != 1.0;
+    SEM_CK(launch_apply_bf16(L, a, mass_only, s));
+  } else {
+    ApplyArgs<float, float> a{};
+    a.map = L.map; a.metric = L.metric32; a.u = u; a.y = y; a.nelem = L.nelem;
+    a.mass_coef = (float)(alpha / bb); a.out_scale = (float)bb; a.scale_out = bb != 1.0;
+    SEM_CK(launch_apply_fp32(L, a, mass_only, s));
+  }
+  return SEM_OK;
+}
+
+int cg_solve(sem_ctx* ctx, double alpha, const double* b, double* x, double rtol, double atol,
+             int maxit, int precond, int* iters, double* final_res, sem_stats* stats,
+             cudaStream_t s) {
+  int rc = ensure_workspace(ctx);
+  if (rc != SEM_OK) return rc;
+  Level& L = ctx->L;
+  Workspace& w = ctx->ws;
+  const int64_t n = L.ndofs;
+  const int vg = vec_grid(n);
+  const double* inv = nullptr;
+  if (precond == SEM_PC_JACOBI) {
+    if (w.inv_alpha != alpha) {
+      k_inv_diag<<<vg, kVecThreads, 0, s>>>(n, alpha, L.mdiag, L.kdiag, w.invdiag);
+      ctx->launches += 1;
+      SEM_CK(cudaGetLastError());
+      w.inv_alpha = alpha;
+    }
+    inv = w.invdiag;
+  } else if (precond == SEM_PC_GMG) {
+    return fail(ctx, SEM_ERR_UNSUPPORTED, "geometric multigrid preconditioner not available");
+  } else if (precond != SEM_PC_NONE) {
+    return fail(ctx, SEM_ERR_ARG, "unknown preconditioner");
+  }
+  // Ap = A x, then the initial residual
+  SEM_CK(cudaMemsetAsync(w.Ap, 0, sizeof(double) * n, s));
+  {
+    ApplyArgs64 a = base_args(ctx, alpha, 1.0, x, w.Ap);
+    SEM_CK(launch_apply_fp64(L, a, false, s));
+  }
+  ctx->launches += 2;
+  k_cg_init<<<vg, kVecThreads, 0, s>>>(n, b, w.Ap, inv, w.r, w.z, w.p, w.cg, w.vec_partials,
+                                       w.tickets + 0, rtol, atol);
+  SEM_CK(cudaGetLastError());
+
+  ApplyArgs64 ap = base_args(ctx, alpha, 1.0, w.p, w.Ap);
+  ap.done = &w.cg->done;
+  ap.dot_partials = w.apply_partials;
+  ap.dot_ticket = w.tickets + 1;
+  ap.cg = w.cg;
+
+  Timing& tm = ctx->timing;
+  constexpr int kChunkMax = 16;
+  std::vector<cudaEvent_t> evs;
+  if (tm.enabled) {
+    evs.resize(2 * kChunkMax);
+    for (auto& e : evs) SEM_CK(cudaEventCreate(&e));
+  }
+  int launched = 0;
+  int prev_iters = 0;
+  int chunk = 4;
+  bool done = false;
+  int rc_out = SEM_OK;
+  while (true) {
+    const int this_chunk = std::min(chunk, maxit - launched);
+    if (this_chunk > 0) {
+      for (int c = 0; c < this_chunk; ++c) {
+        if (tm.enabled) SEM_CK(cudaEventRecord(evs[2 * c], s));
+        SEM_CK(launch_apply_fp64(L, ap, false, s));
+        if (tm.enabled) SEM_CK(cudaEventRecord(evs[2 * c + 1], s));
+        k_cg_xr<<<vg, kVecThreads, 0, s>>>(n, x, w.p, w.Ap, w.r, inv, w.z, w.cg, w.vec_partials,
+                                           w.tickets + 0);
+        k_cg_p<<<vg, kVecThreads, 0, s>>>(n, w.z, w.p, w.Ap, w.cg);
+      }
+      SEM_CK(cudaGetLastError());
+      launched += this_chunk;
+      ctx->launches += 3 * this_chunk;
+    }
+    SEM_CK(cudaMemcpyAsync(w.cg_host, w.cg, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+    SEM_CK(cudaStreamSynchronize(s));
+    const CgScalars& h = *w.cg_host;
+    if (tm.enabled && this_chunk > 0) {
+      const int worked = std::min(this_chunk, h.iters - prev_iters);
+      for (int c = 0; c < worked; ++c) {
+        float ms = 0.f;
+        SEM_CK(cudaEventElapsedTime(&ms, evs[2 * c], evs[2 * c + 1]));
+        tm.ms += ms;
+        tm.count += 1;
+      }
+    }
+    prev_iters = h.iters;
+    if (h.done) { done = true; break; }
+    if (launched >= maxit) break;
+    chunk = std::min(kChunkMax, chunk * 2);
+  }
+  for (auto& e : evs) cudaEventDestroy(e);
+  const CgScalars& h = *w.cg_host;
+  if (iters) *iters = h.iters;
+  if (final_res) *final_res = std::sqrt(h.rr);
+  if (stats) {
+    stats->cg_iters += h.iters;
+    stats->last_residual = std::sqrt(h.rr);
+  }
+  if (h.status == SEM_ERR_NONFINITE)
+    rc_out = fail(ctx, SEM_ERR_NONFINITE, "non-finite value in a CG inner product");
+  else if (!done)
+    rc_out = fail(ctx, SEM_ERR_NOT_CONVERGED,
+                  "CG did not converge in " + std::to_string(maxit) + " iterations (|r| = " +
+                      std::to_string(std::sqrt(h.rr)) + ")");
+  return rc_out;
+}
+
+int time_steps(sem_ctx* ctx, sem_state* st, double dt, int nsteps, double rtol, double atol,
+               int maxit, int precond, sem_stats* stats, cudaStream_t s) {
+  int rc = ensure_workspace(ctx);
+  if (rc != SEM_OK) return rc;
+  Level& L = ctx->L;
+  Workspace& w = ctx->ws;
+  const int64_t n = L.ndofs;
+  const int vg = vec_grid(n);
+  const sem_ionic_params& ip = ctx->ionic;
+  IonicArgs ia;
+  ia.u_rest = ip.u_rest;
+  ia.u_amp = ip.u_amp;
+  ia.inv_amp = 1.0 / ip.u_amp;
+  ia.inv_tau_in = 1.0 / ip.tau_in;
+  ia.inv_tau_out = 1.0 / ip.tau_out;
+  ia.inv_tau_open = 1.0 / ip.tau_open;
+  ia.inv_tau_close = 1.0 / ip.tau_close;
+  ia.v_gate = ip.v_gate;
+  ia.inv_kappa = 1.0 / ip.kappa;
+  for (int k = 0; k < nsteps; ++k) {
+    const int first = st->n == 0 ? 1 : 0;
+    const double t1 = (double)(st->n + 1) * dt;
+    const bool on = ctx->stim_mask != nullptr && t1 > ctx->stim_on && t1 <= ctx->stim_off;
+    double* out = L.quad == SEM_QUAD_LGL ? w.b : w.g;
+    k_ionic_rhs<<<vg, kVecThreads, 0, s>>>(
+        n, st->U[st->cur], st->U[st->prev], st->H[st->cur], st->H[st->prev], st->H[st->next],
+        st->U[st->next], out, L.quad == SEM_QUAD_LGL ? L.mdiag : nullptr,
+        on ? ctx->stim_mask : nullptr, on ? ctx->stim_amp : 0.0, ia, dt, first);
+    SEM_CK(cudaGetLastError());
+    ctx->launches += 1;
+    if (L.quad == SEM_QUAD_LG) {
+      rc = apply_fp64(ctx, 1.0, 0.0, w.g, w.b, s);
+      if (rc != SEM_OK) return rc;
+    }
+    const double alpha = first ? 1.0 / dt : 1.5 / dt;
+    rc = cg_solve(ctx, alpha, w.b, st->U[st->next], rtol, atol, maxit, precond, nullptr, nullptr,
+                  stats, s);
+    if (rc != SEM_OK) return rc;
+    const int old_prev = st->prev;
+    st->prev = st->cur;
+    st->cur = st->next;
+    st->next = old_prev;
+    st->n += 1;
+    if (stats) stats->steps += 1;
+  }
+  return SEM_OK;
+}
+
+}  // namespace sem

@@ -1,0 +1,190 @@
+"""GPU parity of the CG solve and of the monodomain time step against the oracle,
+plus the solver's error reporting.
+
+Time steps: the oracle solves each linear system exactly (sparse LU); the
+GPU runs Jacobi-CG to ||r|| <= 1e-13 ||b|| so that the solution tolerance of
+1e-10 (relative, 2-norm) is not consumed by the iteration.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import ionic
+from oracle import mesh as Mh
+from oracle import monodomain as MD
+
+pytestmark = pytest.mark.gpu
+
+gb = pytest.importorskip("paper_2205_05136_gb300")
+capi = gb.capi
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _small(p=2, quad="LGL", perturb=0.0, dims=(8, 4, 2)):
+    s = W.slab(*dims, (20.0, 7.0, 3.0), perturb=perturb, seed=1)
+    tissue = W.constant_tissue(s, 0.12, 0.03, 0.0)
+    g = gb.Slab(s.flat_vertices(), s.nx, s.ny, s.nz, p, quad)
+    g.set_tissue(*tissue)
+    o = Mh.SlabSpace(s.flat_vertices(), s.nx, s.ny, s.nz, p, quad)
+    return s, tissue, g, o
+
+
+def test_small_slab_dof_count():
+    """8 x 4 x 2 elements at p = 2: 17 x 9 x 5 = 765 nodes (the small slab workload)."""
+    _, _, g, o = _small()
+    assert g.ndofs == o.ndofs == 765
+
+
+@pytest.mark.parametrize("quad", ["LG", "LGL"])
+@pytest.mark.parametrize("precond", [capi.SEM_PC_JACOBI, capi.SEM_PC_NONE])
+def test_cg_solve_matches_direct_solve(quad, precond):
+    s, tissue, g, o = _small(3, quad, perturb=0.1, dims=(4, 3, 2))
+    alpha = 1.5 / 0.05
+    A = Mh.assemble(o, tissue, alpha, 1.0)
+    b = W.uniform_vector(o.ndofs, -1.0, 1.0, seed=3)
+    import scipy.sparse.linalg as spla
+    xref = spla.spsolve(A.tocsc(), b)
+    x = torch.zeros(o.ndofs, dtype=torch.float64, device="cuda")
+    it, res = g.cg_solve(alpha, torch.tensor(b, device="cuda"), x, rtol=1e-13, maxit=5000,
+                         precond=precond)
+    assert it > 0
+    assert res <= 1e-13 * np.linalg.norm(b) * 1.0000001
+    assert rel(x.cpu().numpy(), xref) < 1e-11
+
+
+def test_cg_reports_not_converged_and_nonfinite():
+    _, _, g, o = _small()
+    b = torch.tensor(W.uniform_vector(o.ndofs, seed=3), device="cuda")
+    x = torch.zeros_like(b)
+    rc, it, res = capi.sem_cg_solve(g.ctx, 30.0, b, x, 1e-14, 0.0, 3, capi.SEM_PC_JACOBI,
+                                    raise_on_error=False)
+    assert rc == capi.SEM_ERR_NOT_CONVERGED and it == 3
+    assert "did not converge" in capi.sem_last_error(g.ctx)
+    b[5] = float("nan")
+    x.zero_()
+    rc, _, _ = capi.sem_cg_solve(g.ctx, 30.0, b, x, 1e-10, 0.0, 50, capi.SEM_PC_JACOBI,
+                                 raise_on_error=False)
+    assert rc == capi.SEM_ERR_NONFINITE
+
+
+def test_argument_errors_on_gpu():
+    _, _, g, o = _small()
+    u_host = torch.zeros(o.ndofs, dtype=torch.float64)
+    y = torch.zeros(o.ndofs, dtype=torch.float64, device="cuda")
+    L = capi.lib()
+    import ctypes
+    rc = L.sem_apply(g.ctx, 1.0, 1.0, ctypes.c_void_p(u_host.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                     capi.SEM_PREC_FP64, None)
+    assert rc == capi.SEM_ERR_ARG
+    rc = L.sem_apply(g.ctx, 1.0, 1.0, ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                     capi.SEM_PREC_FP64, None)
+    assert rc == capi.SEM_ERR_ARG
+    with pytest.raises(capi.SemError):
+        g.cg_solve(30.0, y, y.clone(), precond=capi.SEM_PC_GMG + 5)
+
+
+def test_bad_mesh_is_rejected():
+    s = W.slab(2, 1, 1, (2.0, 1.0, 1.0))
+    v = s.flat_vertices().copy()
+    v[1, 0] = 2.5  # pull the middle bottom vertex past its right neighbour: inverted cell
+    with pytest.raises(capi.SemError) as ei:
+        gb.Slab(v, 2, 1, 1, 2, "LGL")
+    assert ei.value.code == capi.SEM_ERR_BAD_MESH
+
+
+def _oracle_run(o, tissue, dt, nsteps, region, amp, t_off, u0=None):
+    md = MD.Monodomain(o, tissue, dt, region=region, amplitude=amp, t_on=0.0, t_off=t_off)
+    st = MD.rest_state(o.ndofs)
+    if u0 is not None:
+        st = dict(u=u0.copy(), u_prev=u0.copy(), h=st["h"], h_prev=st["h_prev"], n=0)
+    return md.run(st, nsteps)
+
+
+@pytest.mark.parametrize("quad", ["LGL", "LG"])
+def test_one_step_and_first_bdf2_step(quad):
+    s, tissue, g, o = _small(2, quad, perturb=0.1)
+    u0 = W.uniform_vector(o.ndofs, -85.0, 20.0, seed=W.SEED_U)
+    dt = 0.05
+    box = (0.0, 0.0, 0.0, 1.5, 1.5, 1.5)
+    g.set_ionic()
+    g.set_stimulus("box", box, 50.0, 0.0, 1.0)
+    st = g.new_state(torch.tensor(u0, device="cuda"), 1.0)
+    for k in (1, 2):
+        st.step(dt, 1, rtol=1e-13, maxit=5000)
+        u, h, n = st.get()
+        ref = _oracle_run(o, tissue, dt, k, ("box", box), 50.0, 1.0, u0=u0)
+        assert n == k
+        assert rel(u.cpu().numpy(), ref["u"]) < 1e-10
+        assert rel(h.cpu().numpy(), ref["h"]) < 1e-12
+
+
+@pytest.mark.parametrize("quad", ["LGL", "LG"])
+def test_hundred_steps_small_slab(quad):
+    """The small-slab workload: 20 x 7 x 3 mm, 8 x 4 x 2 elements, p = 2, rest
+    state, 50 mV/ms corner stimulus for 1 ms, dt = 0.05 ms, 100 steps."""
+    s, tissue, g, o = _small(2, quad)
+    dt = 0.05
+    box = (0.0, 0.0, 0.0, 1.5, 1.5, 1.5)
+    g.set_ionic()
+    g.set_stimulus("box", box, 50.0, 0.0, 1.0)
+    st = g.new_state(-85.0, 1.0)
+    stats = st.step(dt, 100, rtol=1e-13, maxit=5000)
+    assert stats.steps == 100 and stats.cg_iters > 100
+    u, h, n = st.get()
+    ref = _oracle_run(o, tissue, dt, 100, ("box", box), 50.0, 1.0)
+    assert rel(u.cpu().numpy(), ref["u"]) < 1e-10
+    assert rel(h.cpu().numpy(), ref["h"]) < 1e-10
+    # the stimulus excited the corner
+    assert ref["u"].max() > 0.0
+
+
+def test_step_host_matches_device_step():
+    s, tissue, g, o = _small(2, "LGL")
+    g.set_ionic()
+    g.set_stimulus("box", (0, 0, 0, 1.5, 1.5, 1.5), 50.0, 0.0, 1.0)
+    st = g.new_state(-85.0, 1.0)
+    st.step(0.05, 3, rtol=1e-12)
+    ud, hd, _ = st.get()
+    u = torch.full((o.ndofs,), -85.0, dtype=torch.float64).pin_memory()
+    up = u.clone().pin_memory()
+    h = torch.ones(o.ndofs, dtype=torch.float64).pin_memory()
+    hp = h.clone().pin_memory()
+    for n in range(3):
+        capi.sem_step_host(g.ctx, u, up, h, hp, n, 0.05, 1e-12, 0.0, 1000)
+    torch.cuda.synchronize()
+    # same kernels; only the order of the scatter atomics may differ
+    assert rel(u.numpy(), ud.cpu().numpy()) < 1e-13 and rel(h.numpy(), hd.cpu().numpy()) < 1e-13
+
+
+def test_checkpoint_restore_resumes_identically():
+    s, tissue, g, o = _small(2, "LGL")
+    g.set_ionic()
+    g.set_stimulus("box", (0, 0, 0, 1.5, 1.5, 1.5), 50.0, 0.0, 1.0)
+    st = g.new_state(-85.0, 1.0)
+    st.step(0.05, 4, rtol=1e-13)
+    ck = st.checkpoint()
+    assert ck["n"] == 4
+    st.step(0.05, 3, rtol=1e-13)
+    ua, ha, na = st.get()
+    st2 = g.new_state(0.0, 0.0)
+    st2.restore(ck)
+    st2.step(0.05, 3, rtol=1e-13)
+    ub, hb, nb = st2.get()
+    assert na == nb == 7
+    assert rel(ub.cpu().numpy(), ua.cpu().numpy()) < 1e-13
+
+
+def test_ionic_parameters_reach_the_kernel():
+    prm = dict(ionic.DEFAULT_PARAMS)
+    prm["tau_out"] = 3.0
+    s, tissue, g, o = _small(1, "LGL", dims=(2, 2, 1))
+    g.set_ionic(**prm)
+    st = g.new_state(-60.0, 0.8)
+    st.step(0.05, 5, rtol=1e-13)
+    u, h, _ = st.get()
+    ref = ionic.single_cell_semi_implicit(-60.0, 0.8, 0.25, 0.05, prm)
+    assert np.abs(u.cpu().numpy() - ref[0]).max() < 1e-10 * abs(ref[0])
