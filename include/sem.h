@@ -195,6 +195,24 @@ int sem_step_host(sem_ctx* ctx, double* u, double* u_prev, double* h, double* h_
                   double dt, double rtol, double atol, int maxit, int precond, sem_stats* stats,
                   void* stream);
 
+/* y = alpha M u + beta K u and *dot = u . y (FP64), without allocating.
+ * The paper has no counterpart: this is a variant of the operator apply for
+ * callers that cannot call cudaMalloc -- code running while a CUDA stream
+ * capture is active, hosts that own every device allocation through their own
+ * arena or budget, real-time loops that must not enter the allocator
+ * (sem_cg_solve and sem_step allocate work vectors on first use; this call
+ * never does).  u, y: device double[ndofs]; dot: device double[1]; the caller
+ * passes all inputs and outputs.  beta must be finite and nonzero.
+ * The grid reduction's scratch is one static device array of 65,536 per-CTA
+ * partial sums (512 KiB per device that loads libsem, held until the process
+ * exits); meshes needing more CTAs (more than 65,536 x E elements, E = 64,
+ * 28, 16, 10, 7, 5 for p = 1..6) are rejected with SEM_ERR_ARG.  All calls
+ * share that array: overlapping calls on the GPU race, so order them.  The
+ * first call on a device looks up the array's address; make it before any
+ * stream capture begins.  Asynchronous on stream. */
+int sem_apply_dot_static(sem_ctx* ctx, double alpha, double beta, const double* u, double* y,
+                         double* dot, void* stream);
+
 /* Enable (1) or disable (0) CUDA-event timing of the operator-apply kernels
  * inside sem_step / sem_cg_solve (reported in sem_stats). */
 int sem_set_timing(sem_ctx* ctx, int enable);

@@ -26,6 +26,7 @@ SOURCES = [
     "sem_apply_fp32.cu",
     "sem_solver.cu",
     "sem_api.cu",
+    "sem_noalloc.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

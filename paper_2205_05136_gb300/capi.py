@@ -45,7 +45,7 @@ EXPORTS = [
     "sem_num_elements", "sem_dof_coords", "sem_set_tissue", "sem_apply", "sem_diagonal",
     "sem_cg_solve", "sem_set_ionic", "sem_set_stimulus", "sem_state_create", "sem_state_destroy",
     "sem_state_set", "sem_state_get", "sem_state_restore", "sem_step", "sem_step_host",
-    "sem_set_timing",
+    "sem_set_timing", "sem_apply_dot_static",
 ]
 
 
@@ -104,6 +104,7 @@ def lib():
             "sem_step_host": (_I, [_P, _P, _P, _P, _P, _I64, _D, _D, _D, _I, _I,
                                    ctypes.POINTER(sem_stats), _P]),
             "sem_set_timing": (_I, [_P, _I]),
+            "sem_apply_dot_static": (_I, [_P, _D, _D, _P, _P, _P, _P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -278,3 +279,14 @@ def sem_step_host(ctx, u, u_prev, h, h_prev, n, dt, rtol, atol, maxit, precond=S
 
 def sem_set_timing(ctx, enable: bool):
     return _check(lib().sem_set_timing(ctx, 1 if enable else 0), ctx)
+
+
+def sem_apply_dot_static(ctx, alpha, beta, u, y, dot, stream=None):
+    """y = alpha M u + beta K u and dot[0] = u . y with no allocation inside libsem
+    (static device scratch; see include/sem.h)."""
+    n = sem_num_dofs(ctx)
+    return _check(lib().sem_apply_dot_static(ctx, float(alpha), float(beta),
+                                             _dev(u, torch.float64, n, "u"),
+                                             _dev(y, torch.float64, n, "y"),
+                                             _dev(dot, torch.float64, 1, "dot"),
+                                             _stream(stream)), ctx)
