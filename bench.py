@@ -45,6 +45,10 @@ STIM_AMP = 50.0      # mV/ms
 STIM_T_OFF = 1.0     # ms
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64: 152 SMs x 2 DFMA/clk x 2 flop x ~2.06 GHz
 
+# DRAM bytes (read + write) per launch of the CG apply kernel from one ncu capture
+# (profiles/sem_apply_fp64_p4_semni_2M.md); an entry is removed whenever that kernel changes.
+NCU_TRAFFIC = {(4, "LGL"): 267.783424e6 + 12.869632e6}
+
 
 def peaks():
     try:
@@ -306,7 +310,7 @@ def run_gpu(args):
             "peak": FP64_PEAK_TFLOPS,
             "unit": "TFLOP/s",
             "frac": achieved_tf / FP64_PEAK_TFLOPS,
-            "traffic": args.traffic,
+            "traffic": args.traffic if args.traffic is not None else NCU_TRAFFIC.get((p, quad)),
             "kernel": f"sem_apply_kernel<P={p},{quad},f64,dot>",
             "algorithmic_flops_per_launch": flops,
             "algorithmic_bytes_per_launch": algo_bytes,
