@@ -139,13 +139,35 @@ int sem_diagonal(sem_ctx* ctx, double alpha, double beta, double* d, void* strea
 
 /* Solve (alpha M + K) x = b by preconditioned CG (Section 4), warm-started
  * from the x passed in.  Stops when ||r||_2 <= max(rtol ||b||_2, atol).
- * precond: SEM_PC_NONE or SEM_PC_JACOBI (SEM_PC_GMG: SEM_ERR_UNSUPPORTED until
- * built).  b, x: device double[ndofs].  iters / final_res may be NULL.
+ * precond: SEM_PC_NONE, SEM_PC_JACOBI or SEM_PC_GMG (flexible PCG with one
+ * V-cycle per iteration, see sem_set_gmg).  b, x: device double[ndofs].  iters / final_res may be NULL.
  * Returns SEM_ERR_NOT_CONVERGED after maxit iterations (x = last iterate) and
  * SEM_ERR_NONFINITE when an inner product is NaN or Inf.  Synchronises stream. */
 int sem_cg_solve(sem_ctx* ctx, double alpha, const double* b, double* x, double rtol,
                  double atol, int maxit, int precond, int* iters, double* final_res,
                  void* stream);
+
+/* Geometric multigrid preconditioner (Section 4.3), used by sem_cg_solve and
+ * sem_step with precond = SEM_PC_GMG.  Levels: the fine Q_p level, p-coarsened
+ * levels on the same mesh (p -> p/2 -> ... -> 1), then 2:1 h-coarsened Q_1
+ * levels until a level has at most min_coarse_dofs nodes; operators are
+ * rediscretised per level.  Smoother: Chebyshev-Jacobi of the given degree on
+ * [0.08, 1.2] x lambda_max(D^{-1} A), lambda_max from 10 Lanczos (CG) steps;
+ * coarse_degree Chebyshev steps on the coarsest level.  precision: the
+ * V-cycle's arithmetic -- SEM_PREC_FP32 (FP32 metric), SEM_PREC_FP32_BF16
+ * (bf16 metric) or SEM_PREC_FP64; the outer CG is flexible and stays FP64.
+ * Defaults: degree 3, coarse_degree 10, min_coarse_dofs 2000, FP32.  The
+ * hierarchy is (re)built on first use after this call or sem_set_tissue. */
+int sem_set_gmg(sem_ctx* ctx, int degree, int coarse_degree, int min_coarse_dofs, int precision);
+
+/* z = one V-cycle applied to r for the operator alpha M + K (device double[ndofs]). */
+int sem_vcycle(sem_ctx* ctx, double alpha, const double* r, double* z, void* stream);
+
+/* Hierarchy description for alpha (builds it if needed): number of levels, and
+ * for the first max_levels levels their degree p, element counts dims[3 l ..
+ * 3 l + 2], node counts and lambda_max estimates (any output may be NULL). */
+int sem_gmg_info(sem_ctx* ctx, double alpha, int max_levels, int* nlevels, int* p, int* dims,
+                 int64_t* ndofs, double* lambda_max, void* stream);
 
 /* Ionic model parameters (copied). */
 int sem_set_ionic(sem_ctx* ctx, const sem_ionic_params* prm);

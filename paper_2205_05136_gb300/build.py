@@ -27,6 +27,7 @@ SOURCES = [
     "sem_solver.cu",
     "sem_api.cu",
     "sem_noalloc.cu",
+    "sem_gmg.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

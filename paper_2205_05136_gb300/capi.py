@@ -45,7 +45,7 @@ EXPORTS = [
     "sem_num_elements", "sem_dof_coords", "sem_set_tissue", "sem_apply", "sem_diagonal",
     "sem_cg_solve", "sem_set_ionic", "sem_set_stimulus", "sem_state_create", "sem_state_destroy",
     "sem_state_set", "sem_state_get", "sem_state_restore", "sem_step", "sem_step_host",
-    "sem_set_timing", "sem_apply_dot_static",
+    "sem_set_timing", "sem_apply_dot_static", "sem_set_gmg", "sem_vcycle", "sem_gmg_info",
 ]
 
 
@@ -105,6 +105,10 @@ def lib():
                                    ctypes.POINTER(sem_stats), _P]),
             "sem_set_timing": (_I, [_P, _I]),
             "sem_apply_dot_static": (_I, [_P, _D, _D, _P, _P, _P, _P]),
+            "sem_set_gmg": (_I, [_P, _I, _I, _I, _I]),
+            "sem_vcycle": (_I, [_P, _D, _P, _P, _P]),
+            "sem_gmg_info": (_I, [_P, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
+                                  ctypes.POINTER(_I), ctypes.POINTER(_I64), _DP, _P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -290,3 +294,28 @@ def sem_apply_dot_static(ctx, alpha, beta, u, y, dot, stream=None):
                                              _dev(y, torch.float64, n, "y"),
                                              _dev(dot, torch.float64, 1, "dot"),
                                              _stream(stream)), ctx)
+
+
+def sem_set_gmg(ctx, degree=3, coarse_degree=10, min_coarse_dofs=2000, precision=SEM_PREC_FP32):
+    return _check(lib().sem_set_gmg(ctx, int(degree), int(coarse_degree), int(min_coarse_dofs),
+                                    int(precision)), ctx)
+
+
+def sem_vcycle(ctx, alpha, r, z, stream=None):
+    n = sem_num_dofs(ctx)
+    return _check(lib().sem_vcycle(ctx, float(alpha), _dev(r, torch.float64, n, "r"),
+                                   _dev(z, torch.float64, n, "z"), _stream(stream)), ctx)
+
+
+def sem_gmg_info(ctx, alpha, max_levels=32, stream=None):
+    """dict(nlevels, p, dims, ndofs, lambda_max) of the multigrid hierarchy for alpha."""
+    nl = _I()
+    p = (_I * max_levels)()
+    dims = (_I * (3 * max_levels))()
+    nd = (_I64 * max_levels)()
+    lam = (_D * max_levels)()
+    _check(lib().sem_gmg_info(ctx, float(alpha), int(max_levels), ctypes.byref(nl), p, dims, nd,
+                              lam, _stream(stream)), ctx)
+    k = min(nl.value, max_levels)
+    return dict(nlevels=nl.value, p=list(p[:k]), dims=[tuple(dims[3 * i:3 * i + 3]) for i in range(k)],
+                ndofs=list(nd[:k]), lambda_max=list(lam[:k]))

@@ -71,20 +71,9 @@ bool is_host_ptr(const void* p) {
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
   } while (0)
 
-void free_level(Level& L) {
-  cudaFree(L.map);
-  cudaFree(L.evert);
-  cudaFree(L.metric);
-  cudaFree(L.metric32);
-  cudaFree(L.metric16);
-  cudaFree(L.mdiag);
-  cudaFree(L.kdiag);
-  cudaFree(L.xyz);
-  L = Level();
-}
-
 void free_ctx(sem_ctx* ctx) {
-  free_level(ctx->L);
+  gmg_free(ctx);
+  level_free(ctx->L);
   cudaFree(ctx->sigma_l);
   cudaFree(ctx->sigma_t);
   cudaFree(ctx->theta);
@@ -119,46 +108,13 @@ int grid_for(int64_t n) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 8));
 }
 
-// Builds the structured numbering and element vertex arrays, uploads them and
-// computes metric, node coordinates and diagonals.
+// Builds the fine level (numbering, vertices, metric, node coordinates,
+// diagonals) with the default tissue.
 int build_level(sem_ctx* ctx, int nx, int ny, int nz, const double* vertices, int p, int quad,
                 cudaStream_t s) {
   Level& L = ctx->L;
-  L.p = p; L.quad = quad; L.n = p + 1;
-  L.nx = nx; L.ny = ny; L.nz = nz;
-  L.nelem = nx * ny * nz;
-  const int64_t NX = (int64_t)p * nx + 1, NY = (int64_t)p * ny + 1, NZ = (int64_t)p * nz + 1;
-  L.ndofs = NX * NY * NZ;
-  build_tables(p, quad, &L.tab);
-  const int n = L.n, n3 = n * n * n;
-  std::vector<int> map((size_t)L.nelem * n3);
-  std::vector<double> ev((size_t)L.nelem * 24);
-  for (int ez = 0; ez < nz; ++ez)
-    for (int ey = 0; ey < ny; ++ey)
-      for (int ex = 0; ex < nx; ++ex) {
-        const size_t e = (size_t)ex + (size_t)nx * (ey + (size_t)ny * ez);
-        for (int k = 0; k < n; ++k)
-          for (int j = 0; j < n; ++j)
-            for (int i = 0; i < n; ++i) {
-              const int64_t g = (ex * (int64_t)p + i) + NX * ((ey * (int64_t)p + j) + NY * (ez * (int64_t)p + k));
-              map[e * n3 + i + n * (j + n * k)] = (int)g;
-            }
-        for (int c = 0; c < 2; ++c)
-          for (int b = 0; b < 2; ++b)
-            for (int a = 0; a < 2; ++a) {
-              const size_t v = (size_t)(ex + a) + (size_t)(nx + 1) * ((ey + b) + (size_t)(ny + 1) * (ez + c));
-              for (int d = 0; d < 3; ++d) ev[e * 24 + (a + 2 * b + 4 * c) * 3 + d] = vertices[v * 3 + d];
-            }
-      }
-  const size_t nm = (size_t)L.nelem * kMetricComps * n3;
-  SEM_CK(cudaMalloc(&L.map, sizeof(int) * map.size()));
-  SEM_CK(cudaMalloc(&L.evert, sizeof(double) * ev.size()));
-  SEM_CK(cudaMalloc(&L.metric, sizeof(double) * nm));
-  SEM_CK(cudaMalloc(&L.mdiag, sizeof(double) * L.ndofs));
-  SEM_CK(cudaMalloc(&L.kdiag, sizeof(double) * L.ndofs));
-  SEM_CK(cudaMalloc(&L.xyz, sizeof(double) * 3 * L.ndofs));
-  SEM_CK(cudaMemcpyAsync(L.map, map.data(), sizeof(int) * map.size(), cudaMemcpyHostToDevice, s));
-  SEM_CK(cudaMemcpyAsync(L.evert, ev.data(), sizeof(double) * ev.size(), cudaMemcpyHostToDevice, s));
+  ctx->vertices.assign(vertices, vertices + (size_t)(nx + 1) * (ny + 1) * (nz + 1) * 3);
+  SEM_CK(level_create(L, nx, ny, nz, vertices, p, quad, true, s));
   SEM_CK(cudaMalloc(&ctx->sigma_l, sizeof(double) * L.nelem));
   SEM_CK(cudaMalloc(&ctx->sigma_t, sizeof(double) * L.nelem));
   SEM_CK(cudaMalloc(&ctx->theta, sizeof(double) * L.nelem));
@@ -283,6 +239,7 @@ int sem_set_tissue(sem_ctx* ctx, const double* sigma_l, const double* sigma_t,
   SEM_CK(setup_geometry(ctx->L, ctx->sigma_l, ctx->sigma_t, ctx->theta, ctx->d_flag, s));
   SEM_CK(setup_diagonals(ctx->L, s));
   ctx->ws.inv_alpha = -1.0;
+  gmg_free(ctx);  // coarse levels inherit the tissue: rebuilt on next use
   return SEM_OK;
 }
 
@@ -491,6 +448,39 @@ int sem_step_host(sem_ctx* ctx, double* u, double* u_prev, double* h, double* h_
   SEM_CK(cudaMemcpyAsync(h, st->H[st->cur], bytes, cudaMemcpyDeviceToHost, s));
   SEM_CK(cudaStreamSynchronize(s));
   return SEM_OK;
+}
+
+int sem_set_gmg(sem_ctx* ctx, int degree, int coarse_degree, int min_coarse_dofs, int precision) {
+  CK_CTX(ctx);
+  if (degree < 1 || degree > 20 || coarse_degree < 1 || coarse_degree > 200 || min_coarse_dofs < 1)
+    return fail(ctx, SEM_ERR_ARG, "bad multigrid parameters");
+  if (precision != SEM_PREC_FP64 && precision != SEM_PREC_FP32 && precision != SEM_PREC_FP32_BF16)
+    return fail(ctx, SEM_ERR_ARG, "unknown precision");
+  DeviceGuard guard(ctx->device);
+  cudaDeviceSynchronize();
+  gmg_free(ctx);
+  ctx->gmg_degree = degree;
+  ctx->gmg_coarse_degree = coarse_degree;
+  ctx->gmg_min_coarse_dofs = min_coarse_dofs;
+  ctx->gmg_precision = precision;
+  return SEM_OK;
+}
+
+int sem_vcycle(sem_ctx* ctx, double alpha, const double* r, double* z, void* stream) {
+  CK_CTX(ctx);
+  DeviceGuard guard(ctx->device);
+  CK_DEV(r, "r");
+  CK_DEV(z, "z");
+  if (!(alpha >= 0.0) || !std::isfinite(alpha)) return fail(ctx, SEM_ERR_ARG, "alpha must be finite and >= 0");
+  return gmg_vcycle(ctx, alpha, r, z, as_stream(stream));
+}
+
+int sem_gmg_info(sem_ctx* ctx, double alpha, int max_levels, int* nlevels, int* p, int* dims,
+                 int64_t* ndofs, double* lambda_max, void* stream) {
+  CK_CTX(ctx);
+  if (max_levels < 0) return fail(ctx, SEM_ERR_ARG, "max_levels must be >= 0");
+  DeviceGuard guard(ctx->device);
+  return gmg_info(ctx, alpha, max_levels, nlevels, p, dims, ndofs, lambda_max, as_stream(stream));
 }
 
 int sem_set_timing(sem_ctx* ctx, int enable) {

@@ -1,7 +1,9 @@
 // Context and state objects behind the opaque sem_ctx / sem_state handles.
 #pragma once
 
+#include <memory>
 #include <string>
+#include <vector>
 
 #include "sem_internal.cuh"
 
@@ -21,6 +23,8 @@ struct Workspace {
   double* dot_result = nullptr;       // 1 double
 };
 
+struct Gmg;  // geometric multigrid hierarchy (sem_gmg.cu)
+
 struct Timing {
   bool enabled = false;
   cudaEvent_t start = nullptr, stop = nullptr;
@@ -33,6 +37,7 @@ struct Timing {
 struct sem_ctx {
   int device = 0;
   sem::Level L;
+  std::vector<double> vertices;  // host copy of the slab's vertex lattice
   double* sigma_l = nullptr;  // per element
   double* sigma_t = nullptr;
   double* theta = nullptr;
@@ -43,6 +48,9 @@ struct sem_ctx {
   sem::Workspace ws;
   sem::Timing timing;
   int64_t launches = 0;             // libsem kernels launched so far
+  sem::Gmg* gmg = nullptr;          // built on first use of the multigrid preconditioner
+  int gmg_degree = 3, gmg_coarse_degree = 10, gmg_min_coarse_dofs = 2000;
+  int gmg_precision = SEM_PREC_FP32;
   sem_state* host_state = nullptr;  // device copy of the state for sem_step_host
   std::string err;
 };
@@ -67,6 +75,16 @@ int cg_solve(sem_ctx* ctx, double alpha, const double* b, double* x, double rtol
 int time_steps(sem_ctx* ctx, sem_state* st, double dt, int nsteps, double rtol, double atol,
                int maxit, int precond, sem_stats* stats, cudaStream_t s);
 int fail(sem_ctx* ctx, int code, const std::string& msg);
+int apply_fp32(sem_ctx* ctx, double alpha, double beta, const float* u, float* y, bool bf16,
+               cudaStream_t s);
+
+// Geometric multigrid (sem_gmg.cu).
+void gmg_free(sem_ctx* ctx);
+int gmg_vcycle(sem_ctx* ctx, double alpha, const double* r, double* z, cudaStream_t s);
+int gmg_pcg(sem_ctx* ctx, double alpha, const double* b, double* x, double rtol, double atol,
+            int maxit, int* iters, double* final_res, sem_stats* stats, cudaStream_t s);
+int gmg_info(sem_ctx* ctx, double alpha, int max_levels, int* nlevels, int* p, int* dims,
+             int64_t* ndofs, double* lambda_max, cudaStream_t s);
 int cuda_fail(sem_ctx* ctx, cudaError_t e, const char* what);
 
 }  // namespace sem

@@ -1,0 +1,1001 @@
+// Geometric multigrid preconditioner (Section 4.3) and the flexible PCG it drives.
+//
+// Levels: the fine Q_p level, then p-coarsened levels on the same mesh
+// (p -> max(1, p/2) -> ... -> 1), then 2:1 h-coarsened Q_1 levels (each
+// direction's n elements -> ceil(n/2) elements built from every other vertex)
+// until a level has at most `min_coarse_dofs` nodes.  Every level
+// rediscretises alpha M + K with its own metric; a coarse element takes the
+// tissue of its first fine child.
+//
+// Transfers (matrix-vector products, Section 4.3):
+//   p-levels: per element, nodal interpolation Q_pc -> Q_pf by three 1-D
+//     sweeps; restriction is its transpose, with each fine node's residual
+//     divided by the number of elements sharing it so that the element-wise
+//     sum equals P^T r;
+//   h-levels: per fine vertex, the coarse trilinear function evaluated at the
+//     reference coordinates -1, 0, +1 of the coarse element (a trailing odd
+//     element spans one fine element: -1, +1); restriction by the transpose.
+// Smoother: Chebyshev semi-iteration with point-Jacobi on [0.08, 1.2] x the
+//   largest eigenvalue of D^{-1} A, estimated by 10 preconditioned CG
+//   (Lanczos) steps from a fixed start vector; degree `degree` before and after
+//   the coarse correction, degree `coarse_degree` on the coarsest level.
+// Precision: the V-cycle runs in FP32 with an FP32 or bf16 metric, or in FP64;
+//   the outer CG, its inner products and residual stay in FP64.  A V-cycle in
+//   FP32 is not exactly symmetric, so the outer iteration is the flexible
+//   (Polak-Ribiere) PCG: beta = r_{k+1} . (z_{k+1} - z_k) / (r_k . z_k).
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "sem_apply_kernel.cuh"
+#include "sem_context.cuh"
+
+namespace sem {
+
+struct GmgLevel {
+  Level* L = nullptr;
+  bool owned = false;
+  int to_next = 0;  // 0: p-transfer to the next level, 1: h-transfer
+  double *sl = nullptr, *st = nullptr, *th = nullptr;
+  bool owns_tissue = false;
+  void *b = nullptr, *x = nullptr, *t = nullptr, *d = nullptr, *invd = nullptr;
+  double* dinv64 = nullptr;
+  double lam = 0.0;
+};
+
+struct Gmg {
+  std::vector<GmgLevel> lv;
+  double alpha = -1.0;
+  int precision = SEM_PREC_FP32;
+  int degree = 3, coarse_degree = 10;
+  double *z0 = nullptr, *z1 = nullptr;                 // outer PCG: z_k, z_{k-1}
+  double *lr = nullptr, *lz = nullptr, *lp = nullptr, *lAp = nullptr;  // Lanczos
+  double* dots = nullptr;                              // device scalars
+  double* partials = nullptr;
+  unsigned int* tickets = nullptr;
+  int partial_len = 0;
+};
+
+namespace {
+
+constexpr int kThreads = 256;
+
+int grid1d(int64_t n) {
+  const int64_t g = (n + kThreads - 1) / kThreads;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 8));
+}
+
+#define GRID_LOOP(i, n)                                                          \
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); \
+       i += (int64_t)gridDim.x * blockDim.x)
+
+__device__ __forceinline__ bool skip(const int* done) { return done != nullptr && *done; }
+
+// ---------------------------------------------------------------- vectors
+template <typename T>
+__global__ void k_zero(int64_t n, T* x, const int* done) {
+  if (skip(done)) return;
+  GRID_LOOP(i, n) x[i] = T(0);
+}
+
+template <typename T>
+__global__ void k_level_inv_diag(int64_t n, double alpha, const double* m, const double* k,
+                                 T* inv, double* inv64) {
+  GRID_LOOP(i, n) {
+    const double v = 1.0 / fma(alpha, m[i], k[i]);
+    inv[i] = (T)v;
+    inv64[i] = v;
+  }
+}
+
+// Chebyshev step 0 from a zero start: d = D^{-1} b / theta, x = d, t = 0.
+template <typename T>
+__global__ void k_cheb_zero_start(int64_t n, const T* __restrict__ b, const T* __restrict__ invd,
+                                  T* __restrict__ x, T* __restrict__ d, T* __restrict__ t,
+                                  T inv_theta, const int* done) {
+  if (skip(done)) return;
+  GRID_LOOP(i, n) {
+    const T di = invd[i] * b[i] * inv_theta;
+    d[i] = di;
+    x[i] = di;
+    t[i] = T(0);
+  }
+}
+
+// Chebyshev step with t = A x: d = c1 d + c2 D^{-1}(b - t), x += d, t = 0
+// (first: d = c2 D^{-1}(b - t)).
+template <typename T>
+__global__ void k_cheb_step(int64_t n, const T* __restrict__ b, const T* __restrict__ invd,
+                            T* __restrict__ x, T* __restrict__ d, T* __restrict__ t, T c1, T c2,
+                            int first, const int* done) {
+  if (skip(done)) return;
+  GRID_LOOP(i, n) {
+    const T ri = b[i] - t[i];
+    const T di = first ? c2 * invd[i] * ri : fma(c1, d[i], c2 * invd[i] * ri);
+    d[i] = di;
+    x[i] += di;
+    t[i] = T(0);
+  }
+}
+
+// ---------------------------------------------------------------- transfers
+struct PTab {
+  int nf, nc;
+  double P[kMaxN][kMaxN];  // P[i][a] = l^c_a(x^f_i)
+};
+
+// x_f += P x_c on the elements; each fine node is written by one element (the
+// highest-index element holding it), which also clears t_f there.
+template <typename T>
+__global__ void k_prolong_p(int nelem, int nx, int ny, int nz, const int* __restrict__ map_c,
+                            const int* __restrict__ map_f, const __grid_constant__ PTab tab,
+                            const T* __restrict__ xc, T* __restrict__ xf, T* __restrict__ tf,
+                            const int* done) {
+  if (skip(done)) return;
+  const int e = blockIdx.x;
+  if (e >= nelem) return;
+  const int nf = tab.nf, nc = tab.nc, pf = nf - 1;
+  const int nf3 = nf * nf * nf, nc3 = nc * nc * nc;
+  __shared__ T cv[kMaxN * kMaxN * kMaxN];
+  __shared__ T s1[kMaxN * kMaxN * kMaxN];
+  __shared__ T s2[kMaxN * kMaxN * kMaxN];
+  for (int a = threadIdx.x; a < nc3; a += blockDim.x) cv[a] = xc[map_c[(size_t)e * nc3 + a]];
+  __syncthreads();
+  for (int w = threadIdx.x; w < nc * nc * nf; w += blockDim.x) {  // [k_c][j_c][i_f]
+    const int i = w % nf, kj = w / nf;
+    T s = T(0);
+    for (int a = 0; a < nc; ++a) s += (T)tab.P[i][a] * cv[kj * nc + a];
+    s1[w] = s;
+  }
+  __syncthreads();
+  for (int w = threadIdx.x; w < nc * nf * nf; w += blockDim.x) {  // [k_c][j_f][i_f]
+    const int i = w % nf, j = (w / nf) % nf, k = w / (nf * nf);
+    T s = T(0);
+    for (int b = 0; b < nc; ++b) s += (T)tab.P[j][b] * s1[(k * nc + b) * nf + i];
+    s2[w] = s;
+  }
+  __syncthreads();
+  const int ex = e % nx, ey = (e / nx) % ny, ez = e / (nx * ny);
+  for (int w = threadIdx.x; w < nf3; w += blockDim.x) {  // [k_f][j_f][i_f]
+    const int i = w % nf, j = (w / nf) % nf, k = w / (nf * nf);
+    const bool own = (i < pf || ex == nx - 1) && (j < pf || ey == ny - 1) && (k < pf || ez == nz - 1);
+    if (!own) continue;
+    T s = T(0);
+    for (int c = 0; c < nc; ++c) s += (T)tab.P[k][c] * s2[(c * nf + j) * nf + i];
+    const int g = map_f[(size_t)e * nf3 + w];
+    xf[g] += s;
+    tf[g] = T(0);
+  }
+}
+
+// b_c += P^T (b_f - t_f) on the elements, fine residuals divided by the number
+// of elements sharing the node.
+template <typename T>
+__global__ void k_restrict_p(int nelem, int nx, int ny, int nz, const int* __restrict__ map_c,
+                             const int* __restrict__ map_f, const __grid_constant__ PTab tab,
+                             const T* __restrict__ bf, const T* __restrict__ tf,
+                             T* __restrict__ bc, const int* done) {
+  if (skip(done)) return;
+  const int e = blockIdx.x;
+  if (e >= nelem) return;
+  const int nf = tab.nf, nc = tab.nc, pf = nf - 1;
+  const int nf3 = nf * nf * nf, nc3 = nc * nc * nc;
+  __shared__ T fv[kMaxN * kMaxN * kMaxN];
+  __shared__ T s1[kMaxN * kMaxN * kMaxN];
+  __shared__ T s2[kMaxN * kMaxN * kMaxN];
+  const int ex = e % nx, ey = (e / nx) % ny, ez = e / (nx * ny);
+  for (int w = threadIdx.x; w < nf3; w += blockDim.x) {
+    const int i = w % nf, j = (w / nf) % nf, k = w / (nf * nf);
+    const int m = (((i == 0 && ex > 0) || (i == pf && ex < nx - 1)) ? 2 : 1) *
+                  (((j == 0 && ey > 0) || (j == pf && ey < ny - 1)) ? 2 : 1) *
+                  (((k == 0 && ez > 0) || (k == pf && ez < nz - 1)) ? 2 : 1);
+    const int g = map_f[(size_t)e * nf3 + w];
+    fv[w] = (bf[g] - tf[g]) / (T)m;
+  }
+  __syncthreads();
+  for (int w = threadIdx.x; w < nf * nf * nc; w += blockDim.x) {  // [k_f][j_f][a]
+    const int a = w % nc, kj = w / nc;
+    T s = T(0);
+    for (int i = 0; i < nf; ++i) s += (T)tab.P[i][a] * fv[kj * nf + i];
+    s1[w] = s;
+  }
+  __syncthreads();
+  for (int w = threadIdx.x; w < nf * nc * nc; w += blockDim.x) {  // [k_f][b][a]
+    const int a = w % nc, b = (w / nc) % nc, k = w / (nc * nc);
+    T s = T(0);
+    for (int j = 0; j < nf; ++j) s += (T)tab.P[j][b] * s1[(k * nf + j) * nc + a];
+    s2[w] = s;
+  }
+  __syncthreads();
+  for (int w = threadIdx.x; w < nc3; w += blockDim.x) {  // [c][b][a]
+    const int a = w % nc, b = (w / nc) % nc, c = w / (nc * nc);
+    T s = T(0);
+    for (int k = 0; k < nf; ++k) s += (T)tab.P[k][c] * s2[(k * nc + b) * nc + a];
+    atomicAdd(bc + map_c[(size_t)e * nc3 + w], s);
+  }
+}
+
+// Coarse vertex k (and k+1) and weights of fine vertex I along one direction.
+__device__ __forceinline__ void hweights(int I, int nf, int nc, int& k, double& w0, double& w1) {
+  k = min(I / 2, nc - 1);
+  const int t = I - 2 * k;
+  if (2 * k + 2 <= nf) {  // coarse element made of two fine elements
+    w0 = t == 0 ? 1.0 : (t == 1 ? 0.5 : 0.0);
+  } else {                // trailing single fine element
+    w0 = t == 0 ? 1.0 : 0.0;
+  }
+  w1 = 1.0 - w0;
+}
+
+template <typename T>
+__global__ void k_prolong_h(int nfx, int nfy, int nfz, int ncx, int ncy, int ncz,
+                            const T* __restrict__ xc, T* __restrict__ xf, T* __restrict__ tf,
+                            const int* done) {
+  if (skip(done)) return;
+  const int64_t NX = nfx + 1, NY = nfy + 1, n = NX * NY * (nfz + 1);
+  const int64_t CX = ncx + 1, CY = ncy + 1;
+  GRID_LOOP(g, n) {
+    const int I = (int)(g % NX), J = (int)((g / NX) % NY), K = (int)(g / (NX * NY));
+    int kx, ky, kz;
+    double wx[2], wy[2], wz[2];
+    hweights(I, nfx, ncx, kx, wx[0], wx[1]);
+    hweights(J, nfy, ncy, ky, wy[0], wy[1]);
+    hweights(K, nfz, ncz, kz, wz[0], wz[1]);
+    T s = T(0);
+    for (int c = 0; c < 2; ++c)
+      for (int b = 0; b < 2; ++b)
+        for (int a = 0; a < 2; ++a) {
+          const double w = wx[a] * wy[b] * wz[c];
+          if (w != 0.0) s += (T)w * xc[(kx + a) + CX * ((ky + b) + CY * (kz + c))];
+        }
+    xf[g] += s;
+    tf[g] = T(0);
+  }
+}
+
+template <typename T>
+__global__ void k_restrict_h(int nfx, int nfy, int nfz, int ncx, int ncy, int ncz,
+                             const T* __restrict__ bf, const T* __restrict__ tf,
+                             T* __restrict__ bc, const int* done) {
+  if (skip(done)) return;
+  const int64_t NX = nfx + 1, NY = nfy + 1, n = NX * NY * (nfz + 1);
+  const int64_t CX = ncx + 1, CY = ncy + 1;
+  GRID_LOOP(g, n) {
+    const int I = (int)(g % NX), J = (int)((g / NX) % NY), K = (int)(g / (NX * NY));
+    int kx, ky, kz;
+    double wx[2], wy[2], wz[2];
+    hweights(I, nfx, ncx, kx, wx[0], wx[1]);
+    hweights(J, nfy, ncy, ky, wy[0], wy[1]);
+    hweights(K, nfz, ncz, kz, wz[0], wz[1]);
+    const T r = bf[g] - tf[g];
+    for (int c = 0; c < 2; ++c)
+      for (int b = 0; b < 2; ++b)
+        for (int a = 0; a < 2; ++a) {
+          const double w = wx[a] * wy[b] * wz[c];
+          if (w != 0.0) atomicAdd(bc + (kx + a) + CX * ((ky + b) + CY * (kz + c)), (T)w * r);
+        }
+  }
+}
+
+__global__ void k_coarse_tissue(int ncx, int ncy, int ncz, int nfx, int nfy, const double* sl,
+                                const double* st, const double* th, double* csl, double* cst,
+                                double* cth) {
+  const int64_t n = (int64_t)ncx * ncy * ncz;
+  GRID_LOOP(e, n) {
+    const int kx = (int)(e % ncx), ky = (int)((e / ncx) % ncy), kz = (int)(e / ((int64_t)ncx * ncy));
+    const int64_t f = 2 * kx + (int64_t)nfx * (2 * ky + (int64_t)nfy * 2 * kz);
+    csl[e] = sl[f];
+    cst[e] = st[f];
+    cth[e] = th[f];
+  }
+}
+
+// ---------------------------------------------------------------- reductions
+// Deterministic dot product; the last CTA writes the total to *out.
+__global__ void k_dot(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
+                      double* partials, unsigned int* ticket, double* out) {
+  __shared__ double red[32];
+  double v = 0.0;
+  GRID_LOOP(i, n) v = fma(a[i], b[i], v);
+  v = block_sum(v, red);
+  double total;
+  if (finish_reduction(v, partials, ticket, &total, red)) *out = total;
+}
+
+__global__ void k_fill_start(int64_t n, double* v) {
+  GRID_LOOP(i, n) {
+    const unsigned long long h = ((unsigned long long)i * 2654435761ull) & 0xffffffffull;
+    v[i] = (double)h / 4294967296.0 - 0.5;
+  }
+}
+
+__global__ void k_lanczos_z(int64_t n, const double* dinv, const double* r, double* z) {
+  GRID_LOOP(i, n) z[i] = dinv[i] * r[i];
+}
+
+__global__ void k_lanczos_update(int64_t n, double alpha, const double* Ap, double* r,
+                                 const double* dinv, double* z) {
+  GRID_LOOP(i, n) {
+    const double ri = fma(-alpha, Ap[i], r[i]);
+    r[i] = ri;
+    z[i] = dinv[i] * ri;
+  }
+}
+
+__global__ void k_lanczos_p(int64_t n, double beta, const double* z, double* p, double* Ap) {
+  GRID_LOOP(i, n) {
+    p[i] = fma(beta, p[i], z[i]);
+    Ap[i] = 0.0;
+  }
+}
+
+// ---------------------------------------------------------------- outer flexible PCG
+template <int K>
+__device__ __forceinline__ bool grid_sums_k(double (&v)[K], double* partials, int stride,
+                                            unsigned int* ticket, double (&tot)[K]) {
+  __shared__ double red[K][32];
+  __shared__ bool is_last;
+  double bs[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) bs[k] = block_sum(v[k], red[k]);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) partials[k * stride + blockIdx.x] = bs[k];
+    __threadfence();
+    const unsigned int t = atomicAdd(ticket, 1u);
+    is_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+      s += ((volatile double*)partials)[k * stride + b];
+    tot[k] = block_sum(s, red[k]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *ticket = 0u;
+  return threadIdx.x == 0;
+}
+
+// r = b - Ap, Ap = 0, b0 = (T) r; r.r, b.b; stopping threshold.
+template <typename T>
+__global__ void k_fpcg_init(int64_t n, const double* __restrict__ b, double* __restrict__ Ap,
+                            double* __restrict__ r, T* __restrict__ b0, CgScalars* cg,
+                            double* partials, int stride, unsigned int* ticket, double rtol,
+                            double atol) {
+  double v[2] = {0.0, 0.0};
+  GRID_LOOP(i, n) {
+    const double bi = b[i];
+    const double ri = bi - Ap[i];
+    r[i] = ri;
+    Ap[i] = 0.0;
+    b0[i] = (T)ri;
+    v[0] = fma(ri, ri, v[0]);
+    v[1] = fma(bi, bi, v[1]);
+  }
+  double tot[2];
+  if (grid_sums_k<2>(v, partials, stride, ticket, tot)) {
+    cg->rr = tot[0];
+    cg->bb = tot[1];
+    cg->tol2 = fmax(rtol * rtol * tot[1], atol * atol);
+    cg->iters = 0;
+    cg->status = 0;
+    const bool finite = isfinite(tot[0]) && isfinite(tot[1]);
+    if (!finite) cg->status = SEM_ERR_NONFINITE;
+    cg->done = (!finite || tot[0] <= cg->tol2) ? 1 : 0;
+  }
+}
+
+// z = (double) x0; first: p = z, rz = r.z; else beta = (r.z - r.z_old) / rz, rz = r.z.
+template <typename T>
+__global__ void k_fpcg_z(int64_t n, const T* __restrict__ x0, double* __restrict__ z,
+                         const double* __restrict__ zold, const double* __restrict__ r,
+                         double* __restrict__ p, int first, CgScalars* cg, double* partials,
+                         int stride, unsigned int* ticket) {
+  if (cg->done) return;
+  double v[2] = {0.0, 0.0};
+  GRID_LOOP(i, n) {
+    const double zi = (double)x0[i];
+    const double ri = r[i];
+    z[i] = zi;
+    if (first) p[i] = zi;
+    v[0] = fma(ri, zi, v[0]);
+    if (!first) v[1] = fma(ri, zold[i], v[1]);
+  }
+  double tot[2];
+  if (grid_sums_k<2>(v, partials, stride, ticket, tot)) {
+    if (first) {
+      cg->beta = 0.0;
+    } else {
+      cg->beta = (tot[0] - tot[1]) / cg->rz;
+    }
+    cg->rz = tot[0];
+    if (!isfinite(tot[0]) || !isfinite(tot[1])) {
+      cg->status = SEM_ERR_NONFINITE;
+      cg->done = 1;
+    }
+  }
+}
+
+__global__ void k_fpcg_p(int64_t n, const double* __restrict__ z, double* __restrict__ p,
+                         const CgScalars* cg) {
+  if (cg->done) return;
+  const double beta = cg->beta;
+  GRID_LOOP(i, n) p[i] = fma(beta, p[i], z[i]);
+}
+
+// x += alpha p, r -= alpha Ap, Ap = 0, b0 = (T) r; r.r; convergence.
+template <typename T>
+__global__ void k_fpcg_xr(int64_t n, double* __restrict__ x, const double* __restrict__ p,
+                          double* __restrict__ Ap, double* __restrict__ r, T* __restrict__ b0,
+                          CgScalars* cg, double* partials, int stride, unsigned int* ticket) {
+  if (cg->done) return;
+  const double alpha = cg->alpha;
+  double v[1] = {0.0};
+  GRID_LOOP(i, n) {
+    x[i] = fma(alpha, p[i], x[i]);
+    const double ri = fma(-alpha, Ap[i], r[i]);
+    r[i] = ri;
+    Ap[i] = 0.0;
+    b0[i] = (T)ri;
+    v[0] = fma(ri, ri, v[0]);
+  }
+  double tot[1];
+  if (grid_sums_k<1>(v, partials, stride, ticket, tot)) {
+    cg->rr = tot[0];
+    cg->iters += 1;
+    if (!isfinite(tot[0]) || !isfinite(alpha)) {
+      cg->status = SEM_ERR_NONFINITE;
+      cg->done = 1;
+    } else if (tot[0] <= cg->tol2) {
+      cg->done = 1;
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_to_level0(int64_t n, const double* __restrict__ r, T* __restrict__ b0) {
+  GRID_LOOP(i, n) b0[i] = (T)r[i];
+}
+
+template <typename T>
+__global__ void k_from_level0(int64_t n, const T* __restrict__ x0, double* __restrict__ z) {
+  GRID_LOOP(i, n) z[i] = (double)x0[i];
+}
+
+// ---------------------------------------------------------------- host helpers
+#define GMG_CK(call)                                          \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);  \
+  } while (0)
+
+size_t elem_size(int precision) { return precision == SEM_PREC_FP64 ? sizeof(double) : sizeof(float); }
+
+// Largest eigenvalue of the symmetric tridiagonal matrix (diag a, off-diagonal e) by bisection.
+double tridiag_max_eig(const std::vector<double>& a, const std::vector<double>& e) {
+  const int m = (int)a.size();
+  double lo = 1e300, hi = -1e300;
+  for (int i = 0; i < m; ++i) {
+    const double r = (i > 0 ? std::fabs(e[i - 1]) : 0.0) + (i + 1 < m ? std::fabs(e[i]) : 0.0);
+    lo = std::min(lo, a[i] - r);
+    hi = std::max(hi, a[i] + r);
+  }
+  auto count_below = [&](double x) {
+    int c = 0;
+    double d = 1.0;
+    for (int i = 0; i < m; ++i) {
+      d = a[i] - x - (i > 0 ? e[i - 1] * e[i - 1] / d : 0.0);
+      if (d == 0.0) d = -1e-300;
+      if (d < 0.0) ++c;
+    }
+    return c;
+  };
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (count_below(mid) >= m) hi = mid; else lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+template <typename T>
+const void* level_metric(const Level& L, int precision) {
+  if (precision == SEM_PREC_FP64) return L.metric;
+  if (precision == SEM_PREC_FP32_BF16) return L.metric16;
+  return L.metric32;
+}
+
+// y += (alpha M + K) x on one level in the V-cycle's precision.
+int level_apply(sem_ctx* ctx, const Level& L, int precision, double alpha, const void* x, void* y,
+                const int* done, cudaStream_t s) {
+  cudaError_t e;
+  if (precision == SEM_PREC_FP64) {
+    ApplyArgs64 a{};
+    a.map = L.map; a.metric = L.metric; a.u = (const double*)x; a.y = (double*)y;
+    a.nelem = L.nelem; a.mass_coef = alpha; a.out_scale = 1.0; a.scale_out = 0; a.done = done;
+    e = launch_apply_fp64(L, a, false, s);
+  } else if (precision == SEM_PREC_FP32_BF16) {
+    ApplyArgs<float, __nv_bfloat16> a{};
+    a.map = L.map; a.metric = L.metric16; a.u = (const float*)x; a.y = (float*)y;
+    a.nelem = L.nelem; a.mass_coef = (float)alpha; a.out_scale = 1.f; a.scale_out = 0; a.done = done;
+    e = launch_apply_bf16(L, a, false, s);
+  } else {
+    ApplyArgs<float, float> a{};
+    a.map = L.map; a.metric = L.metric32; a.u = (const float*)x; a.y = (float*)y;
+    a.nelem = L.nelem; a.mass_coef = (float)alpha; a.out_scale = 1.f; a.scale_out = 0; a.done = done;
+    e = launch_apply_fp32(L, a, false, s);
+  }
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "level apply");
+  ctx->launches += 1;
+  return SEM_OK;
+}
+
+PTab make_ptab(const Level& fine, const Level& coarse) {
+  PTab t{};
+  t.nf = fine.n;
+  t.nc = coarse.n;
+  // l^c_a(x^f_i) by the barycentric formula on the coarse LGL nodes
+  const double* xc = coarse.tab.xg;
+  const double* xf = fine.tab.xg;
+  double lam[kMaxN];
+  for (int a = 0; a < t.nc; ++a) {
+    double prod = 1.0;
+    for (int b = 0; b < t.nc; ++b) if (b != a) prod *= (xc[a] - xc[b]);
+    lam[a] = 1.0 / prod;
+  }
+  for (int i = 0; i < t.nf; ++i) {
+    int hit = -1;
+    for (int a = 0; a < t.nc; ++a) if (std::fabs(xf[i] - xc[a]) < 1e-15) hit = a;
+    if (hit >= 0) {
+      for (int a = 0; a < t.nc; ++a) t.P[i][a] = (a == hit) ? 1.0 : 0.0;
+      continue;
+    }
+    double den = 0.0;
+    for (int a = 0; a < t.nc; ++a) den += lam[a] / (xf[i] - xc[a]);
+    for (int a = 0; a < t.nc; ++a) t.P[i][a] = (lam[a] / (xf[i] - xc[a])) / den;
+  }
+  return t;
+}
+
+int transfer_threads(const Level& f) { return f.n * f.n * f.n <= 64 ? 64 : 128; }
+
+// Restrict (b_l - t_l) into b_{l+1} (zeroed first).
+template <typename T>
+int restrict_to(sem_ctx* ctx, Gmg& g, int l, const int* done, cudaStream_t s) {
+  GmgLevel& F = g.lv[l];
+  GmgLevel& C = g.lv[l + 1];
+  k_zero<T><<<grid1d(C.L->ndofs), kThreads, 0, s>>>(C.L->ndofs, (T*)C.b, done);
+  if (F.to_next == 0) {
+    const PTab tab = make_ptab(*F.L, *C.L);
+    k_restrict_p<T><<<F.L->nelem, transfer_threads(*F.L), 0, s>>>(
+        F.L->nelem, F.L->nx, F.L->ny, F.L->nz, C.L->map, F.L->map, tab, (const T*)F.b,
+        (const T*)F.t, (T*)C.b, done);
+  } else {
+    k_restrict_h<T><<<grid1d(F.L->ndofs), kThreads, 0, s>>>(
+        F.L->nx, F.L->ny, F.L->nz, C.L->nx, C.L->ny, C.L->nz, (const T*)F.b, (const T*)F.t,
+        (T*)C.b, done);
+  }
+  GMG_CK(cudaGetLastError());
+  ctx->launches += 2;
+  return SEM_OK;
+}
+
+template <typename T>
+int prolong_from(sem_ctx* ctx, Gmg& g, int l, const int* done, cudaStream_t s) {
+  GmgLevel& F = g.lv[l];
+  GmgLevel& C = g.lv[l + 1];
+  if (F.to_next == 0) {
+    const PTab tab = make_ptab(*F.L, *C.L);
+    k_prolong_p<T><<<F.L->nelem, transfer_threads(*F.L), 0, s>>>(
+        F.L->nelem, F.L->nx, F.L->ny, F.L->nz, C.L->map, F.L->map, tab, (const T*)C.x, (T*)F.x,
+        (T*)F.t, done);
+  } else {
+    k_prolong_h<T><<<grid1d(F.L->ndofs), kThreads, 0, s>>>(
+        F.L->nx, F.L->ny, F.L->nz, C.L->nx, C.L->ny, C.L->nz, (const T*)C.x, (T*)F.x, (T*)F.t,
+        done);
+  }
+  GMG_CK(cudaGetLastError());
+  ctx->launches += 1;
+  return SEM_OK;
+}
+
+// `degree` Chebyshev steps on level l for A x = b (zero start, or from the current x
+// with t = 0).
+template <typename T>
+int chebyshev(sem_ctx* ctx, Gmg& g, int l, int degree, bool zero_start, const int* done,
+              cudaStream_t s) {
+  GmgLevel& V = g.lv[l];
+  const Level& L = *V.L;
+  const int64_t n = L.ndofs;
+  const double lo = 0.08 * V.lam, hi = 1.2 * V.lam;
+  const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
+  double rho_old = 1.0 / sigma;
+  T* b = (T*)V.b; T* x = (T*)V.x; T* t = (T*)V.t; T* d = (T*)V.d; const T* invd = (const T*)V.invd;
+  int k0 = 0;
+  if (zero_start) {
+    k_cheb_zero_start<T><<<grid1d(n), kThreads, 0, s>>>(n, b, invd, x, d, t, (T)(1.0 / theta), done);
+    GMG_CK(cudaGetLastError());
+    ctx->launches += 1;
+    k0 = 1;
+  }
+  for (int k = k0; k < degree; ++k) {
+    int rc = level_apply(ctx, L, g.precision, g.alpha, x, t, done, s);
+    if (rc != SEM_OK) return rc;
+    if (k == 0) {
+      k_cheb_step<T><<<grid1d(n), kThreads, 0, s>>>(n, b, invd, x, d, t, (T)0, (T)(1.0 / theta), 1, done);
+    } else {
+      const double rho = 1.0 / (2.0 * sigma - rho_old);
+      k_cheb_step<T><<<grid1d(n), kThreads, 0, s>>>(n, b, invd, x, d, t, (T)(rho * rho_old),
+                                                    (T)(2.0 * rho / delta), 0, done);
+      rho_old = rho;
+    }
+    GMG_CK(cudaGetLastError());
+    ctx->launches += 1;
+  }
+  return SEM_OK;
+}
+
+template <typename T>
+int vcycle_level(sem_ctx* ctx, Gmg& g, int l, const int* done, cudaStream_t s) {
+  const int last = (int)g.lv.size() - 1;
+  int rc;
+  if (l == last) return chebyshev<T>(ctx, g, l, g.coarse_degree, true, done, s);
+  if ((rc = chebyshev<T>(ctx, g, l, g.degree, true, done, s)) != SEM_OK) return rc;
+  GmgLevel& V = g.lv[l];
+  // t = A x (t is zero after the smoother), then b_{l+1} = R (b - t)
+  if ((rc = level_apply(ctx, *V.L, g.precision, g.alpha, V.x, V.t, done, s)) != SEM_OK) return rc;
+  if ((rc = restrict_to<T>(ctx, g, l, done, s)) != SEM_OK) return rc;
+  if ((rc = vcycle_level<T>(ctx, g, l + 1, done, s)) != SEM_OK) return rc;
+  if ((rc = prolong_from<T>(ctx, g, l, done, s)) != SEM_OK) return rc;  // also clears t
+  return chebyshev<T>(ctx, g, l, g.degree, false, done, s);
+}
+
+int vcycle(sem_ctx* ctx, Gmg& g, const int* done, cudaStream_t s) {
+  if (g.precision == SEM_PREC_FP64) return vcycle_level<double>(ctx, g, 0, done, s);
+  return vcycle_level<float>(ctx, g, 0, done, s);
+}
+
+// 10 Jacobi-PCG steps on level V from the fixed start vector; largest Lanczos eigenvalue.
+int estimate_lambda(sem_ctx* ctx, Gmg& g, GmgLevel& V, double alpha, cudaStream_t s) {
+  const Level& L = *V.L;
+  const int64_t n = L.ndofs;
+  const int gr = grid1d(n);
+  k_fill_start<<<gr, kThreads, 0, s>>>(n, g.lr);
+  k_lanczos_z<<<gr, kThreads, 0, s>>>(n, V.dinv64, g.lr, g.lz);
+  GMG_CK(cudaMemcpyAsync(g.lp, g.lz, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  GMG_CK(cudaMemsetAsync(g.lAp, 0, sizeof(double) * n, s));
+  k_dot<<<gr, kThreads, 0, s>>>(n, g.lr, g.lz, g.partials, g.tickets, g.dots + 0);
+  GMG_CK(cudaGetLastError());
+  double h[2];
+  GMG_CK(cudaMemcpyAsync(h, g.dots, sizeof(double), cudaMemcpyDeviceToHost, s));
+  GMG_CK(cudaStreamSynchronize(s));
+  double rz = h[0];
+  std::vector<double> alphas, betas;
+  const int iters = (int)std::min<int64_t>(10, n);
+  for (int it = 0; it < iters; ++it) {
+    ApplyArgs64 a{};
+    a.map = L.map; a.metric = L.metric; a.u = g.lp; a.y = g.lAp; a.nelem = L.nelem;
+    a.mass_coef = alpha; a.out_scale = 1.0; a.scale_out = 0;
+    GMG_CK(launch_apply_fp64(L, a, false, s));
+    k_dot<<<gr, kThreads, 0, s>>>(n, g.lp, g.lAp, g.partials, g.tickets, g.dots + 1);
+    GMG_CK(cudaMemcpyAsync(h, g.dots + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+    GMG_CK(cudaStreamSynchronize(s));
+    const double pAp = h[0];
+    if (!(pAp > 0.0) || !(rz > 0.0)) break;
+    const double al = rz / pAp;
+    k_lanczos_update<<<gr, kThreads, 0, s>>>(n, al, g.lAp, g.lr, V.dinv64, g.lz);
+    k_dot<<<gr, kThreads, 0, s>>>(n, g.lr, g.lz, g.partials, g.tickets, g.dots + 2);
+    GMG_CK(cudaMemcpyAsync(h, g.dots + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
+    GMG_CK(cudaStreamSynchronize(s));
+    const double rz_new = h[0];
+    const double be = rz_new / rz;
+    alphas.push_back(al);
+    betas.push_back(be);
+    rz = rz_new;
+    k_lanczos_p<<<gr, kThreads, 0, s>>>(n, be, g.lz, g.lp, g.lAp);
+    GMG_CK(cudaGetLastError());
+    if (!(rz > 0.0)) break;
+  }
+  const int m = (int)alphas.size();
+  if (m == 0) return fail(ctx, SEM_ERR_NONFINITE, "eigenvalue estimate failed on a multigrid level");
+  std::vector<double> d(m), e(std::max(0, m - 1));
+  for (int j = 0; j < m; ++j) {
+    d[j] = 1.0 / alphas[j] + (j > 0 ? betas[j - 1] / alphas[j - 1] : 0.0);
+    if (j + 1 < m) e[j] = std::sqrt(betas[j]) / alphas[j];
+  }
+  V.lam = tridiag_max_eig(d, e);
+  return SEM_OK;
+}
+
+int set_alpha(sem_ctx* ctx, Gmg& g, double alpha, cudaStream_t s) {
+  if (g.alpha == alpha) return SEM_OK;
+  for (GmgLevel& V : g.lv) {
+    const Level& L = *V.L;
+    if (g.precision == SEM_PREC_FP64)
+      k_level_inv_diag<double><<<grid1d(L.ndofs), kThreads, 0, s>>>(L.ndofs, alpha, L.mdiag, L.kdiag,
+                                                                   (double*)V.invd, V.dinv64);
+    else
+      k_level_inv_diag<float><<<grid1d(L.ndofs), kThreads, 0, s>>>(L.ndofs, alpha, L.mdiag, L.kdiag,
+                                                                  (float*)V.invd, V.dinv64);
+    GMG_CK(cudaGetLastError());
+    int rc = estimate_lambda(ctx, g, V, alpha, s);
+    if (rc != SEM_OK) return rc;
+  }
+  g.alpha = alpha;
+  return SEM_OK;
+}
+
+void free_gmg_struct(Gmg* g) {
+  if (!g) return;
+  for (GmgLevel& V : g->lv) {
+    if (V.owned && V.L) {
+      level_free(*V.L);
+      delete V.L;
+    }
+    if (V.owns_tissue) {
+      cudaFree(V.sl); cudaFree(V.st); cudaFree(V.th);
+    }
+    cudaFree(V.b); cudaFree(V.x); cudaFree(V.t); cudaFree(V.d); cudaFree(V.invd);
+    cudaFree(V.dinv64);
+  }
+  cudaFree(g->z0); cudaFree(g->z1);
+  cudaFree(g->lr); cudaFree(g->lz); cudaFree(g->lp); cudaFree(g->lAp);
+  cudaFree(g->dots); cudaFree(g->partials); cudaFree(g->tickets);
+  delete g;
+}
+
+int build(sem_ctx* ctx, cudaStream_t s) {
+  if (ctx->gmg) return SEM_OK;
+  Gmg* g = new Gmg();
+  g->precision = ctx->gmg_precision;
+  g->degree = ctx->gmg_degree;
+  g->coarse_degree = ctx->gmg_coarse_degree;
+  struct Guard {
+    Gmg*& g;
+    ~Guard() { if (g) free_gmg_struct(g); }
+  } guard{g};
+  GmgLevel top;
+  top.L = &ctx->L;
+  top.sl = ctx->sigma_l; top.st = ctx->sigma_t; top.th = ctx->theta;
+  g->lv.push_back(top);
+  std::vector<double> verts = ctx->vertices;
+  int nx = ctx->L.nx, ny = ctx->L.ny, nz = ctx->L.nz, p = ctx->L.p;
+  const int quad = ctx->L.quad;
+  GMG_CK(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), s));
+  while (p > 1) {  // p-coarsening on the fine mesh
+    const int pc = std::max(1, p / 2);
+    GmgLevel V;
+    V.L = new Level();
+    V.owned = true;
+    V.sl = ctx->sigma_l; V.st = ctx->sigma_t; V.th = ctx->theta;
+    g->lv.back().to_next = 0;
+    g->lv.push_back(V);
+    GMG_CK(level_create(*g->lv.back().L, nx, ny, nz, verts.data(), pc, quad, false, s));
+    GMG_CK(setup_geometry(*g->lv.back().L, V.sl, V.st, V.th, ctx->d_flag, s));
+    GMG_CK(setup_diagonals(*g->lv.back().L, s));
+    p = pc;
+  }
+  while (g->lv.back().L->ndofs > ctx->gmg_min_coarse_dofs && std::max(nx, std::max(ny, nz)) > 1) {
+    const int cx = (nx + 1) / 2, cy = (ny + 1) / 2, cz = (nz + 1) / 2;
+    std::vector<double> cv((size_t)(cx + 1) * (cy + 1) * (cz + 1) * 3);
+    for (int K = 0; K <= cz; ++K)
+      for (int J = 0; J <= cy; ++J)
+        for (int I = 0; I <= cx; ++I) {
+          const size_t f = (size_t)std::min(2 * I, nx) +
+                           (size_t)(nx + 1) * (std::min(2 * J, ny) + (size_t)(ny + 1) * std::min(2 * K, nz));
+          const size_t c = (size_t)I + (size_t)(cx + 1) * (J + (size_t)(cy + 1) * K);
+          for (int d = 0; d < 3; ++d) cv[c * 3 + d] = verts[f * 3 + d];
+        }
+    GmgLevel& F = g->lv.back();
+    GmgLevel V;
+    V.L = new Level();
+    V.owned = true;
+    V.owns_tissue = true;
+    const size_t ne = (size_t)cx * cy * cz;
+    GMG_CK(cudaMalloc(&V.sl, sizeof(double) * ne));
+    GMG_CK(cudaMalloc(&V.st, sizeof(double) * ne));
+    GMG_CK(cudaMalloc(&V.th, sizeof(double) * ne));
+    k_coarse_tissue<<<grid1d((int64_t)ne), kThreads, 0, s>>>(cx, cy, cz, nx, ny, F.sl, F.st, F.th,
+                                                              V.sl, V.st, V.th);
+    GMG_CK(cudaGetLastError());
+    F.to_next = 1;
+    g->lv.push_back(V);
+    GMG_CK(level_create(*g->lv.back().L, cx, cy, cz, cv.data(), 1, quad, false, s));
+    GMG_CK(setup_geometry(*g->lv.back().L, V.sl, V.st, V.th, ctx->d_flag, s));
+    GMG_CK(setup_diagonals(*g->lv.back().L, s));
+    verts.swap(cv);
+    nx = cx; ny = cy; nz = cz;
+  }
+  int bad = 0;
+  GMG_CK(cudaMemcpyAsync(&bad, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  GMG_CK(cudaStreamSynchronize(s));
+  if (bad) return fail(ctx, SEM_ERR_BAD_MESH, "a coarsened multigrid level has an inverted element");
+  const size_t es = elem_size(g->precision);
+  int64_t nmax = 0;
+  for (GmgLevel& V : g->lv) {
+    Level& L = *V.L;
+    nmax = std::max(nmax, L.ndofs);
+    if (g->precision == SEM_PREC_FP32 && !L.metric32_valid) {
+      if (!L.metric32) GMG_CK(cudaMalloc(&L.metric32, sizeof(float) * (size_t)L.nelem * kMetricComps * L.n * L.n * L.n));
+      GMG_CK(setup_metric_lowp(L, false, s));
+    }
+    if (g->precision == SEM_PREC_FP32_BF16 && !L.metric16_valid) {
+      if (!L.metric16) GMG_CK(cudaMalloc(&L.metric16, sizeof(__nv_bfloat16) * (size_t)L.nelem * kMetricComps * L.n * L.n * L.n));
+      GMG_CK(setup_metric_lowp(L, true, s));
+    }
+    void** vecs[] = {&V.b, &V.x, &V.t, &V.d, &V.invd};
+    for (void** v : vecs) GMG_CK(cudaMalloc(v, es * L.ndofs));
+    GMG_CK(cudaMemsetAsync(V.t, 0, es * L.ndofs, s));
+    GMG_CK(cudaMalloc(&V.dinv64, sizeof(double) * L.ndofs));
+  }
+  const int64_t nf = ctx->L.ndofs;
+  GMG_CK(cudaMalloc(&g->z0, sizeof(double) * nf));
+  GMG_CK(cudaMalloc(&g->z1, sizeof(double) * nf));
+  double** lv4[] = {&g->lr, &g->lz, &g->lp, &g->lAp};
+  for (double** v : lv4) GMG_CK(cudaMalloc(v, sizeof(double) * nmax));
+  GMG_CK(cudaMalloc(&g->dots, sizeof(double) * 8));
+  g->partial_len = 2048;
+  GMG_CK(cudaMalloc(&g->partials, sizeof(double) * 4 * g->partial_len));
+  GMG_CK(cudaMalloc(&g->tickets, sizeof(unsigned int) * 4));
+  GMG_CK(cudaMemsetAsync(g->tickets, 0, sizeof(unsigned int) * 4, s));
+  GMG_CK(cudaStreamSynchronize(s));
+  ctx->gmg = g;
+  g = nullptr;  // ownership moved to the context
+  return SEM_OK;
+}
+
+template <typename T>
+int pcg_t(sem_ctx* ctx, Gmg& g, double alpha, const double* b, double* x, double rtol,
+          double atol, int maxit, int* iters, double* final_res, sem_stats* stats, cudaStream_t s) {
+  Workspace& w = ctx->ws;
+  Level& L = ctx->L;
+  const int64_t n = L.ndofs;
+  const int gr = grid1d(n);
+  T* b0 = (T*)g.lv[0].b;
+  T* x0 = (T*)g.lv[0].x;
+  const int stride = g.partial_len;
+  // Ap = A x, r = b - Ap
+  GMG_CK(cudaMemsetAsync(w.Ap, 0, sizeof(double) * n, s));
+  {
+    ApplyArgs64 a{};
+    a.map = L.map; a.metric = L.metric; a.u = x; a.y = w.Ap; a.nelem = L.nelem;
+    a.mass_coef = alpha; a.out_scale = 1.0; a.scale_out = 0;
+    GMG_CK(launch_apply_fp64(L, a, false, s));
+  }
+  k_fpcg_init<T><<<gr, kThreads, 0, s>>>(n, b, w.Ap, w.r, b0, w.cg, g.partials, stride, g.tickets,
+                                         rtol, atol);
+  GMG_CK(cudaGetLastError());
+  ctx->launches += 2;
+  const int* done = &w.cg->done;
+  int rc = vcycle(ctx, g, done, s);
+  if (rc != SEM_OK) return rc;
+  double* zc = g.z0;
+  double* zo = g.z1;
+  k_fpcg_z<T><<<gr, kThreads, 0, s>>>(n, x0, zc, nullptr, w.r, w.p, 1, w.cg, g.partials, stride,
+                                      g.tickets + 1);
+  GMG_CK(cudaGetLastError());
+  ctx->launches += 1;
+
+  ApplyArgs64 ap{};
+  ap.map = L.map; ap.metric = L.metric; ap.u = w.p; ap.y = w.Ap; ap.nelem = L.nelem;
+  ap.mass_coef = alpha; ap.out_scale = 1.0; ap.scale_out = 0; ap.done = done;
+  ap.dot_partials = w.apply_partials; ap.dot_ticket = w.tickets + 1; ap.cg = w.cg;
+
+  Timing& tm = ctx->timing;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  if (tm.enabled) {
+    GMG_CK(cudaEventCreate(&ev0));
+    GMG_CK(cudaEventCreate(&ev1));
+  }
+  bool done_h = false;
+  int launched = 0;
+  while (true) {
+    GMG_CK(cudaMemcpyAsync(w.cg_host, w.cg, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+    GMG_CK(cudaStreamSynchronize(s));
+    if (tm.enabled && launched > 0 && w.cg_host->iters == launched) {
+      float ms = 0.f;
+      GMG_CK(cudaEventElapsedTime(&ms, ev0, ev1));
+      tm.ms += ms;
+      tm.count += 1;
+    }
+    if (w.cg_host->done) { done_h = true; break; }
+    if (launched >= maxit) break;
+    if (tm.enabled) GMG_CK(cudaEventRecord(ev0, s));
+    GMG_CK(launch_apply_fp64(L, ap, false, s));
+    if (tm.enabled) GMG_CK(cudaEventRecord(ev1, s));
+    k_fpcg_xr<T><<<gr, kThreads, 0, s>>>(n, x, w.p, w.Ap, w.r, b0, w.cg, g.partials, stride,
+                                         g.tickets + 2);
+    GMG_CK(cudaGetLastError());
+    ctx->launches += 2;
+    if ((rc = vcycle(ctx, g, done, s)) != SEM_OK) break;
+    std::swap(zc, zo);
+    k_fpcg_z<T><<<gr, kThreads, 0, s>>>(n, x0, zc, zo, w.r, nullptr, 0, w.cg, g.partials, stride,
+                                        g.tickets + 1);
+    k_fpcg_p<<<gr, kThreads, 0, s>>>(n, zc, w.p, w.cg);
+    GMG_CK(cudaGetLastError());
+    ctx->launches += 2;
+    ++launched;
+  }
+  if (ev0) cudaEventDestroy(ev0);
+  if (ev1) cudaEventDestroy(ev1);
+  if (rc != SEM_OK) return rc;
+  const CgScalars& h = *w.cg_host;
+  if (iters) *iters = h.iters;
+  if (final_res) *final_res = std::sqrt(h.rr);
+  if (stats) {
+    stats->cg_iters += h.iters;
+    stats->last_residual = std::sqrt(h.rr);
+  }
+  if (h.status == SEM_ERR_NONFINITE)
+    return fail(ctx, SEM_ERR_NONFINITE, "non-finite value in a CG inner product");
+  if (!done_h)
+    return fail(ctx, SEM_ERR_NOT_CONVERGED,
+                "multigrid PCG did not converge in " + std::to_string(maxit) + " iterations");
+  return SEM_OK;
+}
+
+}  // namespace
+
+void gmg_free(sem_ctx* ctx) {
+  if (ctx->gmg) {
+    free_gmg_struct(ctx->gmg);
+    ctx->gmg = nullptr;
+  }
+}
+
+int gmg_pcg(sem_ctx* ctx, double alpha, const double* b, double* x, double rtol, double atol,
+            int maxit, int* iters, double* final_res, sem_stats* stats, cudaStream_t s) {
+  int rc = ensure_workspace(ctx);
+  if (rc != SEM_OK) return rc;
+  if ((rc = build(ctx, s)) != SEM_OK) return rc;
+  Gmg& g = *ctx->gmg;
+  if ((rc = set_alpha(ctx, g, alpha, s)) != SEM_OK) return rc;
+  if (g.precision == SEM_PREC_FP64)
+    return pcg_t<double>(ctx, g, alpha, b, x, rtol, atol, maxit, iters, final_res, stats, s);
+  return pcg_t<float>(ctx, g, alpha, b, x, rtol, atol, maxit, iters, final_res, stats, s);
+}
+
+int gmg_vcycle(sem_ctx* ctx, double alpha, const double* r, double* z, cudaStream_t s) {
+  int rc = build(ctx, s);
+  if (rc != SEM_OK) return rc;
+  Gmg& g = *ctx->gmg;
+  if ((rc = set_alpha(ctx, g, alpha, s)) != SEM_OK) return rc;
+  const int64_t n = ctx->L.ndofs;
+  if (g.precision == SEM_PREC_FP64)
+    k_to_level0<double><<<grid1d(n), kThreads, 0, s>>>(n, r, (double*)g.lv[0].b);
+  else
+    k_to_level0<float><<<grid1d(n), kThreads, 0, s>>>(n, r, (float*)g.lv[0].b);
+  GMG_CK(cudaGetLastError());
+  if ((rc = vcycle(ctx, g, nullptr, s)) != SEM_OK) return rc;
+  if (g.precision == SEM_PREC_FP64)
+    k_from_level0<double><<<grid1d(n), kThreads, 0, s>>>(n, (const double*)g.lv[0].x, z);
+  else
+    k_from_level0<float><<<grid1d(n), kThreads, 0, s>>>(n, (const float*)g.lv[0].x, z);
+  GMG_CK(cudaGetLastError());
+  return SEM_OK;
+}
+
+int gmg_info(sem_ctx* ctx, double alpha, int max_levels, int* nlevels, int* p, int* dims,
+             int64_t* ndofs, double* lambda_max, cudaStream_t s) {
+  int rc = build(ctx, s);
+  if (rc != SEM_OK) return rc;
+  Gmg& g = *ctx->gmg;
+  if ((rc = set_alpha(ctx, g, alpha, s)) != SEM_OK) return rc;
+  const int nl = (int)g.lv.size();
+  if (nlevels) *nlevels = nl;
+  for (int l = 0; l < std::min(nl, max_levels); ++l) {
+    const Level& L = *g.lv[l].L;
+    if (p) p[l] = L.p;
+    if (dims) { dims[3 * l] = L.nx; dims[3 * l + 1] = L.ny; dims[3 * l + 2] = L.nz; }
+    if (ndofs) ndofs[l] = L.ndofs;
+    if (lambda_max) lambda_max[l] = g.lv[l].lam;
+  }
+  return SEM_OK;
+}
+
+}  // namespace sem

@@ -113,6 +113,14 @@ cudaError_t launch_apply_bf16(const Level& L, const ApplyArgs<float, __nv_bfloat
                               bool mass_only, cudaStream_t s);
 int apply_grid_blocks(const Level& L);
 
+// Level construction (sem_setup.cu): structured numbering of an nx x ny x nz
+// slab with host vertices, device allocation of map, element vertices, metric,
+// diagonals (and node coordinates when `coords`).  Metric and diagonals are
+// filled by setup_geometry / setup_diagonals.
+cudaError_t level_create(Level& L, int nx, int ny, int nz, const double* vertices, int p, int quad,
+                         bool coords, cudaStream_t s);
+void level_free(Level& L);
+
 // Setup kernels (sem_setup.cu).
 cudaError_t setup_geometry(Level& L, const double* sigma_l, const double* sigma_t,
                            const double* theta, int* d_bad, cudaStream_t s);

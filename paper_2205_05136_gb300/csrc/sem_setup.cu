@@ -10,7 +10,9 @@
 //   collocation derivative),
 //   D_e = sigma_t I + (sigma_l - sigma_t) f f^T,  f = (cos theta, sin theta, 0),
 //   G   = w |det J| J^{-1} D_e J^{-T}  (6 entries),  W = w |det J|.
+#include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "sem_internal.cuh"
 
@@ -249,6 +251,60 @@ __global__ void k_convert<__nv_bfloat16>(int64_t n, const double* __restrict__ i
 int setup_threads(int n3) { return n3 <= 64 ? 64 : (n3 <= 128 ? 128 : 256); }
 
 }  // namespace
+
+cudaError_t level_create(Level& L, int nx, int ny, int nz, const double* vertices, int p, int quad,
+                         bool coords, cudaStream_t s) {
+  L.p = p; L.quad = quad; L.n = p + 1;
+  L.nx = nx; L.ny = ny; L.nz = nz;
+  L.nelem = nx * ny * nz;
+  const int64_t NX = (int64_t)p * nx + 1, NY = (int64_t)p * ny + 1, NZ = (int64_t)p * nz + 1;
+  L.ndofs = NX * NY * NZ;
+  build_tables(p, quad, &L.tab);
+  const int n = L.n, n3 = n * n * n;
+  std::vector<int> map((size_t)L.nelem * n3);
+  std::vector<double> ev((size_t)L.nelem * 24);
+  for (int ez = 0; ez < nz; ++ez)
+    for (int ey = 0; ey < ny; ++ey)
+      for (int ex = 0; ex < nx; ++ex) {
+        const size_t e = (size_t)ex + (size_t)nx * (ey + (size_t)ny * ez);
+        for (int k = 0; k < n; ++k)
+          for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) {
+              const int64_t g = (ex * (int64_t)p + i) + NX * ((ey * (int64_t)p + j) + NY * (ez * (int64_t)p + k));
+              map[e * n3 + i + n * (j + n * k)] = (int)g;
+            }
+        for (int c = 0; c < 2; ++c)
+          for (int b = 0; b < 2; ++b)
+            for (int a = 0; a < 2; ++a) {
+              const size_t v = (size_t)(ex + a) + (size_t)(nx + 1) * ((ey + b) + (size_t)(ny + 1) * (ez + c));
+              for (int d = 0; d < 3; ++d) ev[e * 24 + (a + 2 * b + 4 * c) * 3 + d] = vertices[v * 3 + d];
+            }
+      }
+  const size_t nm = (size_t)L.nelem * kMetricComps * n3;
+  cudaError_t e;
+  if ((e = cudaMalloc(&L.map, sizeof(int) * map.size())) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&L.evert, sizeof(double) * ev.size())) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&L.metric, sizeof(double) * nm)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&L.mdiag, sizeof(double) * L.ndofs)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&L.kdiag, sizeof(double) * L.ndofs)) != cudaSuccess) return e;
+  if (coords && (e = cudaMalloc(&L.xyz, sizeof(double) * 3 * L.ndofs)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(L.map, map.data(), sizeof(int) * map.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(L.evert, ev.data(), sizeof(double) * ev.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
+  // the host vectors must outlive the copies
+  return cudaStreamSynchronize(s);
+}
+
+void level_free(Level& L) {
+  cudaFree(L.map);
+  cudaFree(L.evert);
+  cudaFree(L.metric);
+  cudaFree(L.metric32);
+  cudaFree(L.metric16);
+  cudaFree(L.mdiag);
+  cudaFree(L.kdiag);
+  cudaFree(L.xyz);
+  L = Level();
+}
 
 cudaError_t setup_geometry(Level& L, const double* sigma_l, const double* sigma_t,
                            const double* theta, int* d_bad, cudaStream_t s) {

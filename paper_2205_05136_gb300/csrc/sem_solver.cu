@@ -343,7 +343,7 @@ int cg_solve(sem_ctx* ctx, double alpha, const double* b, double* x, double rtol
     }
     inv = w.invdiag;
   } else if (precond == SEM_PC_GMG) {
-    return fail(ctx, SEM_ERR_UNSUPPORTED, "geometric multigrid preconditioner not available");
+    return gmg_pcg(ctx, alpha, b, x, rtol, atol, maxit, iters, final_res, stats, s);
   } else if (precond != SEM_PC_NONE) {
     return fail(ctx, SEM_ERR_ARG, "unknown preconditioner");
   }
