@@ -198,6 +198,38 @@ def init_dist():
     return rank, ws, dist
 
 
+def time_arm(slab, precond, args, dist, dev, clocks=False):
+    """Warm-up, then K timed time steps from the rest state; returns
+    (ms, stats, u after the run, state, clock summary)."""
+    import torch
+    state = slab.new_state(-85.0, 1.0)
+    stream = torch.cuda.current_stream()
+    state.step(DT, args.warmup, rtol=RTOL, maxit=MAXIT, precond=precond)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    clk = ClockSampler(dev) if clocks else None
+    if clk:
+        clk.__enter__()
+    ev0.record(stream)
+    stats = state.step(DT, args.steps, rtol=RTOL, maxit=MAXIT, precond=precond)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if clk:
+        clk.__exit__(None, None, None)
+    if dist is not None:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    u, _, _ = state.get()
+    return ms, stats, u, state, (clk.summary() if clk else None)
+
+
 def run_gpu(args):
     import torch
     rank, ws, dist = init_dist()
@@ -208,6 +240,7 @@ def run_gpu(args):
     if dist is not None:
         dist.barrier()
     import paper_2205_05136_gb300 as gb
+    from paper_2205_05136_gb300 import capi
 
     p, quad = args.p, args.quad
     s, tissue, centre = workload(p)
@@ -215,37 +248,26 @@ def run_gpu(args):
     slab.set_tissue(*tissue)
     slab.set_ionic()
     slab.set_stimulus("sphere", (*centre, STIM_RADIUS), STIM_AMP, 0.0, STIM_T_OFF)
-    state = slab.new_state(-85.0, 1.0)
     slab.set_timing(True)
-    stream = torch.cuda.current_stream()
-
-    # warm-up (the first step is BDF1; BDF2 from the second on)
-    wstats = state.step(DT, args.warmup, rtol=RTOL, maxit=MAXIT)
-
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    with ClockSampler(dev) as clk:
-        ev0.record(stream)
-        stats = state.step(DT, args.steps, rtol=RTOL, maxit=MAXIT)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-    if dist is not None:
-        dist.barrier()
-    ms = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     n_d, n_e = slab.ndofs, slab.nelem
+    prec = {"fp32": gb.SEM_PREC_FP32, "bf16": gb.SEM_PREC_FP32_BF16, "fp64": gb.SEM_PREC_FP64}[args.mg_precision]
+    capi.sem_set_gmg(slab.ctx, args.mg_degree, args.mg_coarse_degree, args.mg_min_coarse_dofs, prec)
+
+    # plain FP64 path: Jacobi-CG with the FP64 operator
+    ms64, st64, u64, state64, _ = time_arm(slab, gb.SEM_PC_JACOBI, args, dist, dev)
+    state64.close()
+    # mixed-precision path: flexible FP64 CG preconditioned by the FP32 multigrid V-cycle
+    msmx, stats, umx, state, clk = time_arm(slab, gb.SEM_PC_GMG, args, dist, dev, clocks=True)
+    diff = float(torch.linalg.norm(umx - u64) / torch.linalg.norm(u64))
+
+    ms = msmx
     value = ws * n_d * args.steps / (ms * 1e-3) / 1e9
     iters = stats.cg_iters / max(args.steps, 1)
     apply_ms = stats.apply_ms / max(stats.n_apply, 1)
     flops = n_e * apply_flops_per_element(p, quad)
     achieved_tf = flops / (apply_ms * 1e-3) / 1e12
     algo_bytes = n_e * apply_bytes_per_element(p)
+    apply64_ms = st64.apply_ms / max(st64.n_apply, 1)
 
     # end to end through the public C ABI with host buffers (page-locked), one
     # step per call, continuing from the device state reached above
@@ -253,12 +275,11 @@ def run_gpu(args):
     hu, hup = ck["u"].cpu().pin_memory(), ck["u_prev"].cpu().pin_memory()
     hh, hhp = ck["h"].cpu().pin_memory(), ck["h_prev"].cpu().pin_memory()
     n2 = ck["n"]
-    from paper_2205_05136_gb300 import capi
     n_e2e = max(1, min(args.steps, 10))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(n_e2e):
-        capi.sem_step_host(slab.ctx, hu, hup, hh, hhp, n2 + k, DT, RTOL, 0.0, MAXIT)
+        capi.sem_step_host(slab.ctx, hu, hup, hh, hhp, n2 + k, DT, RTOL, 0.0, MAXIT, gb.SEM_PC_GMG)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e_value = n_d * n_e2e / e2e_s / 1e9 * ws
@@ -267,12 +288,12 @@ def run_gpu(args):
     if rank == 0 and not args.no_cpu_baseline:
         try:
             r = run_oracle_subprocess(p, quad, args.cpu_seconds)
-            applies = iters + 1.0
+            applies = st64.cg_iters / max(args.steps, 1) + 1.0
             v, step_s = cpu_equivalent(r["sec_per_element"], n_e, n_d, applies)
             cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": (f"oracle element-by-element apply (dense local matrices, numpy fp64, 1 thread) "
                               f"over {r['elements']} of {n_e} elements of this slab, "
-                              f"{r['sec_per_element'] * 1e3:.2f} ms/element; scaled to one time step of "
+                              f"{r['sec_per_element'] * 1e3:.2f} ms/element; scaled to one Jacobi-CG time step of "
                               f"{applies:.2f} applies ({step_s:.0f} s/step)")}
         except Exception as exc:  # report, never fail the GPU line
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {exc}"}
@@ -289,13 +310,14 @@ def run_gpu(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64",
+        "dtype": "f64 (outer CG, residuals, inner products, ionic exp) + f32 (multigrid V-cycle)",
         "data": "synthetic",
         "config": {
-            "workload": (f"monodomain BDF2 time step, SEM-NI Q{p} slab 20x7x3 mm, {s.nx}x{s.ny}x{s.nz} "
-                         f"hexahedra, {n_d} DOFs, +-10% vertex perturbation, fibres -60..+60 deg, "
-                         f"dt {DT} ms, Jacobi-CG rtol {RTOL}") if quad == "LGL" else
-                        (f"monodomain BDF2 time step, SEM Q{p} slab {s.nx}x{s.ny}x{s.nz}, {n_d} DOFs"),
+            "workload": (f"monodomain BDF2 time step, {'SEM-NI' if quad == 'LGL' else 'SEM'} Q{p} slab "
+                         f"20x7x3 mm, {s.nx}x{s.ny}x{s.nz} hexahedra, {n_d} DOFs, +-10% vertex perturbation, "
+                         f"fibres -60..+60 deg, dt {DT} ms, CG rtol {RTOL}"),
+            "solver": (f"flexible FP64 PCG + {args.mg_precision} GMG V-cycle (p-then-h coarsening, "
+                       f"Chebyshev({args.mg_degree}), coarse Chebyshev({args.mg_coarse_degree}))"),
             "p": p, "quadrature": quad, "ndofs": n_d, "nelem": n_e,
             "parallelism": f"replicas x{ws}",
             "l2": f"inputs larger than L2: {n_e * 7 * (p + 1) ** 3 * 8 / 1e6:.0f} MB FP64 metric streamed per apply",
@@ -304,6 +326,12 @@ def run_gpu(args):
         "cg_iters_per_step": iters,
         "apply_gdofs": n_d / (apply_ms * 1e-3) / 1e9,
         "apply_ms": apply_ms,
+        "fp64_path": {"solver": "Jacobi-CG, FP64 operator", "value": ws * n_d * args.steps / (ms64 * 1e-3) / 1e9,
+                      "unit": UNIT, "ms_per_step": ms64 / args.steps,
+                      "cg_iters_per_step": st64.cg_iters / max(args.steps, 1),
+                      "apply_ms": apply64_ms, "apply_gdofs": n_d / (apply64_ms * 1e-3) / 1e9},
+        "mixed_vs_fp64": {"speedup": ms64 / msmx, "rel_l2_u_diff": diff,
+                          "note": "u after warm-up + timed steps of both paths, same start state"},
         "roofline": {
             "bound": "alu",
             "achieved": achieved_tf,
@@ -311,7 +339,7 @@ def run_gpu(args):
             "unit": "TFLOP/s",
             "frac": achieved_tf / FP64_PEAK_TFLOPS,
             "traffic": args.traffic if args.traffic is not None else NCU_TRAFFIC.get((p, quad)),
-            "kernel": f"sem_apply_kernel<P={p},{quad},f64,dot>",
+            "kernel": f"sem_apply_kernel<P={p},{quad},f64,dot> (outer-CG operator apply)",
             "algorithmic_flops_per_launch": flops,
             "algorithmic_bytes_per_launch": algo_bytes,
             "hbm_frac_of_measured": (algo_bytes / (apply_ms * 1e-3) / 1e9) / pk.get("hbm_gbs", 6780.0),
@@ -320,12 +348,12 @@ def run_gpu(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * 8 * n_d,
                 "d2h_bytes_per_step": 4 * 8 * n_d, "steps": n_e2e},
         "gpu_launches": int(stats.kernel_launches),
-        "clocks": clk.summary(),
+        "clocks": clk,
         "cpu_baseline": cpu,
     }
-    _ = wstats
     if rank == 0:
         print(json.dumps(line), flush=True)
+    state.close()
     slab.close()
     if dist is not None:
         dist.destroy_process_group()
@@ -431,7 +459,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--traffic", type=float, default=None,
                     help="dram bytes per apply launch from an ncu capture of the current kernel")
-    ap.add_argument("--ref-applies-per-step", type=float, default=12.0)
+    ap.add_argument("--ref-applies-per-step", type=float, default=33.0)
+    ap.add_argument("--mg-precision", default="fp32", choices=["fp32", "bf16", "fp64"])
+    ap.add_argument("--mg-degree", type=int, default=3)
+    ap.add_argument("--mg-coarse-degree", type=int, default=10)
+    ap.add_argument("--mg-min-coarse-dofs", type=int, default=2000)
     ap.add_argument("--sweep", action="store_true")
     ap.add_argument("--sweep-p", type=int, nargs="*", default=[1, 2, 3, 4, 5, 6])
     args = ap.parse_args()

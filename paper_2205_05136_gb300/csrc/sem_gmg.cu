@@ -49,7 +49,21 @@ struct Gmg {
   double alpha = -1.0;
   int precision = SEM_PREC_FP32;
   int degree = 3, coarse_degree = 10;
-  double *z0 = nullptr, *z1 = nullptr;                 // outer PCG: z_k, z_{k-1}
+  double* z = nullptr;                                 // outer PCG preconditioned residual
+  // CUDA graphs of the PCG set-up and of one PCG iteration (V-cycle included),
+  // keyed by the solution pointer and alpha; captured on a private stream.
+  struct Graphs {
+    const double* x = nullptr;
+    const double* b = nullptr;
+    double alpha = 0.0;
+    double rtol = 0.0, atol = 0.0;
+    cudaGraphExec_t init = nullptr, iter = nullptr;
+    int64_t init_kernels = 0, iter_kernels = 0;
+  };
+  Graphs graphs[4];
+  int next_graph = 0;
+  cudaStream_t capture = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;           // recorded around the FP64 apply
   double *lr = nullptr, *lz = nullptr, *lp = nullptr, *lAp = nullptr;  // Lanczos
   double* dots = nullptr;                              // device scalars
   double* partials = nullptr;
@@ -390,21 +404,24 @@ __global__ void k_fpcg_init(int64_t n, const double* __restrict__ b, double* __r
   }
 }
 
-// z = (double) x0; first: p = z, rz = r.z; else beta = (r.z - r.z_old) / rz, rz = r.z.
+// z_new = (double) x0; first: p = z_new, rz = r.z_new; else
+// beta = (r.z_new - r.z_old) / rz, rz = r.z_new (z holds z_old on entry).
 template <typename T>
 __global__ void k_fpcg_z(int64_t n, const T* __restrict__ x0, double* __restrict__ z,
-                         const double* __restrict__ zold, const double* __restrict__ r,
-                         double* __restrict__ p, int first, CgScalars* cg, double* partials,
-                         int stride, unsigned int* ticket) {
+                         const double* __restrict__ r, double* __restrict__ p, int first,
+                         CgScalars* cg, double* partials, int stride, unsigned int* ticket) {
   if (cg->done) return;
   double v[2] = {0.0, 0.0};
   GRID_LOOP(i, n) {
     const double zi = (double)x0[i];
     const double ri = r[i];
+    if (first) {
+      p[i] = zi;
+    } else {
+      v[1] = fma(ri, z[i], v[1]);
+    }
     z[i] = zi;
-    if (first) p[i] = zi;
     v[0] = fma(ri, zi, v[0]);
-    if (!first) v[1] = fma(ri, zold[i], v[1]);
   }
   double tot[2];
   if (grid_sums_k<2>(v, partials, stride, ticket, tot)) {
@@ -743,7 +760,14 @@ void free_gmg_struct(Gmg* g) {
     cudaFree(V.b); cudaFree(V.x); cudaFree(V.t); cudaFree(V.d); cudaFree(V.invd);
     cudaFree(V.dinv64);
   }
-  cudaFree(g->z0); cudaFree(g->z1);
+  cudaFree(g->z);
+  for (auto& gr : g->graphs) {
+    if (gr.init) cudaGraphExecDestroy(gr.init);
+    if (gr.iter) cudaGraphExecDestroy(gr.iter);
+  }
+  if (g->capture) cudaStreamDestroy(g->capture);
+  if (g->ev0) cudaEventDestroy(g->ev0);
+  if (g->ev1) cudaEventDestroy(g->ev1);
   cudaFree(g->lr); cudaFree(g->lz); cudaFree(g->lp); cudaFree(g->lAp);
   cudaFree(g->dots); cudaFree(g->partials); cudaFree(g->tickets);
   delete g;
@@ -834,8 +858,10 @@ int build(sem_ctx* ctx, cudaStream_t s) {
     GMG_CK(cudaMalloc(&V.dinv64, sizeof(double) * L.ndofs));
   }
   const int64_t nf = ctx->L.ndofs;
-  GMG_CK(cudaMalloc(&g->z0, sizeof(double) * nf));
-  GMG_CK(cudaMalloc(&g->z1, sizeof(double) * nf));
+  GMG_CK(cudaMalloc(&g->z, sizeof(double) * nf));
+  GMG_CK(cudaStreamCreateWithFlags(&g->capture, cudaStreamNonBlocking));
+  GMG_CK(cudaEventCreate(&g->ev0));
+  GMG_CK(cudaEventCreate(&g->ev1));
   double** lv4[] = {&g->lr, &g->lz, &g->lp, &g->lAp};
   for (double** v : lv4) GMG_CK(cudaMalloc(v, sizeof(double) * nmax));
   GMG_CK(cudaMalloc(&g->dots, sizeof(double) * 8));
@@ -849,18 +875,31 @@ int build(sem_ctx* ctx, cudaStream_t s) {
   return SEM_OK;
 }
 
+// Kernel nodes of an instantiated graph's source graph.
+int64_t count_kernels(cudaGraph_t graph) {
+  size_t n = 0;
+  if (cudaGraphGetNodes(graph, nullptr, &n) != cudaSuccess) return 0;
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (cudaGraphGetNodes(graph, nodes.data(), &n) != cudaSuccess) return 0;
+  int64_t k = 0;
+  for (auto nd : nodes) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+  }
+  return k;
+}
+
+// The PCG launch sequences, issued on stream s (a capture stream when graphs are built).
 template <typename T>
-int pcg_t(sem_ctx* ctx, Gmg& g, double alpha, const double* b, double* x, double rtol,
-          double atol, int maxit, int* iters, double* final_res, sem_stats* stats, cudaStream_t s) {
+int pcg_init_seq(sem_ctx* ctx, Gmg& g, double alpha, const double* b, const double* x, double rtol,
+                 double atol, cudaStream_t s) {
   Workspace& w = ctx->ws;
   Level& L = ctx->L;
   const int64_t n = L.ndofs;
   const int gr = grid1d(n);
   T* b0 = (T*)g.lv[0].b;
-  T* x0 = (T*)g.lv[0].x;
   const int stride = g.partial_len;
-  // Ap = A x, r = b - Ap
-  GMG_CK(cudaMemsetAsync(w.Ap, 0, sizeof(double) * n, s));
+  k_zero<double><<<gr, kThreads, 0, s>>>(n, w.Ap, nullptr);
   {
     ApplyArgs64 a{};
     a.map = L.map; a.metric = L.metric; a.u = x; a.y = w.Ap; a.nelem = L.nelem;
@@ -870,28 +909,98 @@ int pcg_t(sem_ctx* ctx, Gmg& g, double alpha, const double* b, double* x, double
   k_fpcg_init<T><<<gr, kThreads, 0, s>>>(n, b, w.Ap, w.r, b0, w.cg, g.partials, stride, g.tickets,
                                          rtol, atol);
   GMG_CK(cudaGetLastError());
-  ctx->launches += 2;
   const int* done = &w.cg->done;
   int rc = vcycle(ctx, g, done, s);
   if (rc != SEM_OK) return rc;
-  double* zc = g.z0;
-  double* zo = g.z1;
-  k_fpcg_z<T><<<gr, kThreads, 0, s>>>(n, x0, zc, nullptr, w.r, w.p, 1, w.cg, g.partials, stride,
-                                      g.tickets + 1);
+  k_fpcg_z<T><<<gr, kThreads, 0, s>>>(n, (const T*)g.lv[0].x, g.z, w.r, w.p, 1, w.cg, g.partials,
+                                      stride, g.tickets + 1);
   GMG_CK(cudaGetLastError());
-  ctx->launches += 1;
+  return SEM_OK;
+}
 
+template <typename T>
+int pcg_iter_seq(sem_ctx* ctx, Gmg& g, double alpha, double* x, cudaStream_t s) {
+  Workspace& w = ctx->ws;
+  Level& L = ctx->L;
+  const int64_t n = L.ndofs;
+  const int gr = grid1d(n);
+  const int stride = g.partial_len;
+  const int* done = &w.cg->done;
   ApplyArgs64 ap{};
   ap.map = L.map; ap.metric = L.metric; ap.u = w.p; ap.y = w.Ap; ap.nelem = L.nelem;
   ap.mass_coef = alpha; ap.out_scale = 1.0; ap.scale_out = 0; ap.done = done;
   ap.dot_partials = w.apply_partials; ap.dot_ticket = w.tickets + 1; ap.cg = w.cg;
+  // external records become event nodes of the captured graph (timing of the FP64 apply)
+  GMG_CK(cudaEventRecordWithFlags(g.ev0, s, cudaEventRecordExternal));
+  GMG_CK(launch_apply_fp64(L, ap, false, s));
+  GMG_CK(cudaEventRecordWithFlags(g.ev1, s, cudaEventRecordExternal));
+  k_fpcg_xr<T><<<gr, kThreads, 0, s>>>(n, x, w.p, w.Ap, w.r, (T*)g.lv[0].b, w.cg, g.partials,
+                                       stride, g.tickets + 2);
+  GMG_CK(cudaGetLastError());
+  int rc = vcycle(ctx, g, done, s);
+  if (rc != SEM_OK) return rc;
+  k_fpcg_z<T><<<gr, kThreads, 0, s>>>(n, (const T*)g.lv[0].x, g.z, w.r, nullptr, 0, w.cg,
+                                      g.partials, stride, g.tickets + 1);
+  k_fpcg_p<<<gr, kThreads, 0, s>>>(n, g.z, w.p, w.cg);
+  GMG_CK(cudaGetLastError());
+  return SEM_OK;
+}
 
-  Timing& tm = ctx->timing;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  if (tm.enabled) {
-    GMG_CK(cudaEventCreate(&ev0));
-    GMG_CK(cudaEventCreate(&ev1));
+// Captures (once per solution pointer, right-hand side, alpha and tolerances) the
+// set-up and iteration sequences as CUDA graphs; four are cached.
+template <typename T>
+int get_graphs(sem_ctx* ctx, Gmg& g, double alpha, const double* b, double* x, double rtol,
+               double atol, Gmg::Graphs** out) {
+  for (auto& gr : g.graphs)
+    if (gr.iter && gr.x == x && gr.b == b && gr.alpha == alpha && gr.rtol == rtol && gr.atol == atol) {
+      *out = &gr;
+      return SEM_OK;
+    }
+  Gmg::Graphs& gr = g.graphs[g.next_graph];
+  g.next_graph = (g.next_graph + 1) % 4;
+  if (gr.init) { cudaGraphExecDestroy(gr.init); gr.init = nullptr; }
+  if (gr.iter) { cudaGraphExecDestroy(gr.iter); gr.iter = nullptr; }
+  cudaStream_t cs = g.capture;
+  const int64_t l0 = ctx->launches;
+  for (int which = 0; which < 2; ++which) {
+    GMG_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    int rc = which == 0 ? pcg_init_seq<T>(ctx, g, alpha, b, x, rtol, atol, cs)
+                        : pcg_iter_seq<T>(ctx, g, alpha, x, cs);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
+    if (rc != SEM_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (ec != cudaSuccess) return cuda_fail(ctx, ec, "cudaStreamEndCapture");
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    const int64_t nk = count_kernels(graph);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) return cuda_fail(ctx, ei, "cudaGraphInstantiate");
+    if (which == 0) { gr.init = exec; gr.init_kernels = nk; }
+    else { gr.iter = exec; gr.iter_kernels = nk; }
   }
+  ctx->launches = l0;  // capture launched nothing; replays are counted
+  gr.x = x;
+  gr.b = b;
+  gr.alpha = alpha;
+  gr.rtol = rtol;  // the stopping tolerances are baked into the set-up graph
+  gr.atol = atol;
+  *out = &gr;
+  return SEM_OK;
+}
+
+template <typename T>
+int pcg_t(sem_ctx* ctx, Gmg& g, double alpha, const double* b, double* x, double rtol,
+          double atol, int maxit, int* iters, double* final_res, sem_stats* stats, cudaStream_t s) {
+  Workspace& w = ctx->ws;
+  Gmg::Graphs* gr = nullptr;
+  int rc = get_graphs<T>(ctx, g, alpha, b, x, rtol, atol, &gr);
+  if (rc != SEM_OK) return rc;
+  GMG_CK(cudaGraphLaunch(gr->init, s));
+  ctx->launches += gr->init_kernels;
+  Timing& tm = ctx->timing;
   bool done_h = false;
   int launched = 0;
   while (true) {
@@ -899,31 +1008,19 @@ int pcg_t(sem_ctx* ctx, Gmg& g, double alpha, const double* b, double* x, double
     GMG_CK(cudaStreamSynchronize(s));
     if (tm.enabled && launched > 0 && w.cg_host->iters == launched) {
       float ms = 0.f;
-      GMG_CK(cudaEventElapsedTime(&ms, ev0, ev1));
-      tm.ms += ms;
-      tm.count += 1;
+      if (cudaEventElapsedTime(&ms, g.ev0, g.ev1) == cudaSuccess) {
+        tm.ms += ms;
+        tm.count += 1;
+      } else {
+        cudaGetLastError();  // timing unavailable for these event nodes: not an error
+      }
     }
     if (w.cg_host->done) { done_h = true; break; }
     if (launched >= maxit) break;
-    if (tm.enabled) GMG_CK(cudaEventRecord(ev0, s));
-    GMG_CK(launch_apply_fp64(L, ap, false, s));
-    if (tm.enabled) GMG_CK(cudaEventRecord(ev1, s));
-    k_fpcg_xr<T><<<gr, kThreads, 0, s>>>(n, x, w.p, w.Ap, w.r, b0, w.cg, g.partials, stride,
-                                         g.tickets + 2);
-    GMG_CK(cudaGetLastError());
-    ctx->launches += 2;
-    if ((rc = vcycle(ctx, g, done, s)) != SEM_OK) break;
-    std::swap(zc, zo);
-    k_fpcg_z<T><<<gr, kThreads, 0, s>>>(n, x0, zc, zo, w.r, nullptr, 0, w.cg, g.partials, stride,
-                                        g.tickets + 1);
-    k_fpcg_p<<<gr, kThreads, 0, s>>>(n, zc, w.p, w.cg);
-    GMG_CK(cudaGetLastError());
-    ctx->launches += 2;
+    GMG_CK(cudaGraphLaunch(gr->iter, s));
+    ctx->launches += gr->iter_kernels;
     ++launched;
   }
-  if (ev0) cudaEventDestroy(ev0);
-  if (ev1) cudaEventDestroy(ev1);
-  if (rc != SEM_OK) return rc;
   const CgScalars& h = *w.cg_host;
   if (iters) *iters = h.iters;
   if (final_res) *final_res = std::sqrt(h.rr);
