@@ -217,6 +217,28 @@ int sem_step_host(sem_ctx* ctx, double* u, double* u_prev, double* h, double* h_
                   double dt, double rtol, double atol, int maxit, int precond, sem_stats* stats,
                   void* stream);
 
+/* Run nsteps time steps from st as sem_step does, writing the traces
+ * traces[k * nsens + s] = u^{n0+k+1}[sensors[s]] (device double[nsteps * nsens];
+ * sensors: device int[nsens] node indices) and keeping a checkpoint of the full
+ * BDF2 state every checkpoint_every steps in the context (device memory,
+ * 4 ndofs doubles per checkpoint), for sem_adjoint_grad.  A new recording
+ * replaces the previous one. */
+int sem_forward_record(sem_ctx* ctx, sem_state* st, double dt, int nsteps, int checkpoint_every,
+                       const int* sensors, int nsens, double* traces, double rtol, double atol,
+                       int maxit, int precond, sem_stats* stats, void* stream);
+
+/* Gradient of a loss L(traces) with respect to the per-element sigma_l, sigma_t
+ * and theta of the recorded run, given trace_bar = dL/dtraces (device double,
+ * same layout as the traces).  Discrete adjoint of the partitioned scheme
+ * (Section 3): each checkpoint segment is recomputed forward, then reversed;
+ * every reversed step solves A w = ubar with the same solver settings
+ * (A is symmetric) and adds -w^T (dK/dparam) u^{n+1} per element.  The tissue
+ * and stimulus must be those of the recording.  g_*: device double[nelem],
+ * overwritten. */
+int sem_adjoint_grad(sem_ctx* ctx, const double* trace_bar, double* g_sigma_l, double* g_sigma_t,
+                     double* g_theta, double rtol, double atol, int maxit, int precond,
+                     sem_stats* stats, void* stream);
+
 /* y = alpha M u + beta K u and *dot = u . y (FP64), without allocating.
  * The paper has no counterpart: this is a variant of the operator apply for
  * callers that cannot call cudaMalloc -- code running while a CUDA stream

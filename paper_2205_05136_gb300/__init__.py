@@ -16,6 +16,7 @@ import numpy as np
 import torch
 
 from . import capi
+from .autograd import traces  # noqa: F401
 from .capi import (SEM_PC_GMG, SEM_PC_JACOBI, SEM_PC_NONE, SEM_PREC_FP32, SEM_PREC_FP32_BF16,  # noqa: F401
                    SEM_PREC_FP64, SEM_QUAD_LG, SEM_QUAD_LGL, SEM_REGION_BOX, SEM_REGION_SPHERE,
                    SemError)
@@ -152,4 +153,4 @@ class State:
             pass
 
 
-__all__ = ["Slab", "State", "capi", "SemError", "QUAD", "DEFAULT_IONIC"]
+__all__ = ["Slab", "State", "capi", "SemError", "QUAD", "DEFAULT_IONIC", "traces"]

@@ -28,6 +28,7 @@ SOURCES = [
     "sem_api.cu",
     "sem_noalloc.cu",
     "sem_gmg.cu",
+    "sem_adjoint.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

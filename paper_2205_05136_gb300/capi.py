@@ -46,6 +46,7 @@ EXPORTS = [
     "sem_cg_solve", "sem_set_ionic", "sem_set_stimulus", "sem_state_create", "sem_state_destroy",
     "sem_state_set", "sem_state_get", "sem_state_restore", "sem_step", "sem_step_host",
     "sem_set_timing", "sem_apply_dot_static", "sem_set_gmg", "sem_vcycle", "sem_gmg_info",
+    "sem_forward_record", "sem_adjoint_grad",
 ]
 
 
@@ -106,6 +107,9 @@ def lib():
             "sem_set_timing": (_I, [_P, _I]),
             "sem_apply_dot_static": (_I, [_P, _D, _D, _P, _P, _P, _P]),
             "sem_set_gmg": (_I, [_P, _I, _I, _I, _I]),
+            "sem_forward_record": (_I, [_P, _P, _D, _I, _I, _P, _I, _P, _D, _D, _I, _I,
+                                        ctypes.POINTER(sem_stats), _P]),
+            "sem_adjoint_grad": (_I, [_P, _P, _P, _P, _P, _D, _D, _I, _I, ctypes.POINTER(sem_stats), _P]),
             "sem_vcycle": (_I, [_P, _D, _P, _P, _P]),
             "sem_gmg_info": (_I, [_P, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
                                   ctypes.POINTER(_I), ctypes.POINTER(_I64), _DP, _P]),
@@ -319,3 +323,28 @@ def sem_gmg_info(ctx, alpha, max_levels=32, stream=None):
     k = min(nl.value, max_levels)
     return dict(nlevels=nl.value, p=list(p[:k]), dims=[tuple(dims[3 * i:3 * i + 3]) for i in range(k)],
                 ndofs=list(nd[:k]), lambda_max=list(lam[:k]))
+
+
+def sem_forward_record(ctx, st, dt, nsteps, checkpoint_every, sensors, traces, rtol, atol, maxit,
+                       precond=SEM_PC_JACOBI, stream=None):
+    """sensors: CUDA int32 tensor; traces: CUDA float64 tensor of nsteps * len(sensors)."""
+    ns = sensors.numel()
+    stats = sem_stats()
+    _check(lib().sem_forward_record(ctx, st, float(dt), int(nsteps), int(checkpoint_every),
+                                    _dev(sensors, torch.int32, ns, "sensors"), int(ns),
+                                    _dev(traces, torch.float64, nsteps * ns, "traces"), float(rtol),
+                                    float(atol), int(maxit), int(precond), ctypes.byref(stats),
+                                    _stream(stream)), ctx)
+    return stats
+
+
+def sem_adjoint_grad(ctx, trace_bar, g_sigma_l, g_sigma_t, g_theta, rtol, atol, maxit,
+                     precond=SEM_PC_JACOBI, stream=None):
+    ne = sem_num_elements(ctx)
+    stats = sem_stats()
+    _check(lib().sem_adjoint_grad(ctx, _dev(trace_bar, torch.float64, trace_bar.numel(), "trace_bar"),
+                                  _dev(g_sigma_l, torch.float64, ne, "g_sigma_l"),
+                                  _dev(g_sigma_t, torch.float64, ne, "g_sigma_t"),
+                                  _dev(g_theta, torch.float64, ne, "g_theta"), float(rtol), float(atol),
+                                  int(maxit), int(precond), ctypes.byref(stats), _stream(stream)), ctx)
+    return stats

@@ -73,6 +73,7 @@ bool is_host_ptr(const void* p) {
 
 void free_ctx(sem_ctx* ctx) {
   gmg_free(ctx);
+  tape_free(ctx);
   level_free(ctx->L);
   cudaFree(ctx->sigma_l);
   cudaFree(ctx->sigma_t);
@@ -481,6 +482,53 @@ int sem_gmg_info(sem_ctx* ctx, double alpha, int max_levels, int* nlevels, int* 
   if (max_levels < 0) return fail(ctx, SEM_ERR_ARG, "max_levels must be >= 0");
   DeviceGuard guard(ctx->device);
   return gmg_info(ctx, alpha, max_levels, nlevels, p, dims, ndofs, lambda_max, as_stream(stream));
+}
+
+int sem_forward_record(sem_ctx* ctx, sem_state* st, double dt, int nsteps, int checkpoint_every,
+                       const int* sensors, int nsens, double* traces, double rtol, double atol,
+                       int maxit, int precond, sem_stats* stats, void* stream) {
+  CK_CTX(ctx);
+  if (st == nullptr || st->ctx != ctx) return fail(ctx, SEM_ERR_ARG, "state does not belong to ctx");
+  if (!(dt > 0.0) || nsteps < 1 || checkpoint_every < 1 || nsens < 1 || maxit < 0 ||
+      !(rtol >= 0.0) || !(atol >= 0.0))
+    return fail(ctx, SEM_ERR_ARG, "bad recording parameters");
+  DeviceGuard guard(ctx->device);
+  CK_DEV(sensors, "sensors");
+  CK_DEV(traces, "traces");
+  {  // sensor indices must address nodes
+    std::vector<int> h(nsens);
+    SEM_CK(cudaMemcpy(h.data(), sensors, sizeof(int) * nsens, cudaMemcpyDeviceToHost));
+    for (int v : h)
+      if (v < 0 || v >= ctx->L.ndofs) return fail(ctx, SEM_ERR_ARG, "sensor index out of range");
+  }
+  sem_stats local{};
+  sem_stats* sp = stats ? stats : &local;
+  std::memset(sp, 0, sizeof(*sp));
+  const int64_t l0 = ctx->launches;
+  const int rc = forward_record(ctx, st, dt, nsteps, checkpoint_every, sensors, nsens, traces, rtol,
+                                atol, maxit, precond, sp, as_stream(stream));
+  sp->kernel_launches = ctx->launches - l0;
+  return rc;
+}
+
+int sem_adjoint_grad(sem_ctx* ctx, const double* trace_bar, double* g_sigma_l, double* g_sigma_t,
+                     double* g_theta, double rtol, double atol, int maxit, int precond,
+                     sem_stats* stats, void* stream) {
+  CK_CTX(ctx);
+  if (maxit < 0 || !(rtol >= 0.0) || !(atol >= 0.0)) return fail(ctx, SEM_ERR_ARG, "bad solver parameters");
+  DeviceGuard guard(ctx->device);
+  CK_DEV(trace_bar, "trace_bar");
+  CK_DEV(g_sigma_l, "g_sigma_l");
+  CK_DEV(g_sigma_t, "g_sigma_t");
+  CK_DEV(g_theta, "g_theta");
+  sem_stats local{};
+  sem_stats* sp = stats ? stats : &local;
+  std::memset(sp, 0, sizeof(*sp));
+  const int64_t l0 = ctx->launches;
+  const int rc = adjoint_grad(ctx, trace_bar, g_sigma_l, g_sigma_t, g_theta, rtol, atol, maxit,
+                              precond, sp, as_stream(stream));
+  sp->kernel_launches = ctx->launches - l0;
+  return rc;
 }
 
 int sem_set_timing(sem_ctx* ctx, int enable) {

@@ -23,7 +23,8 @@ struct Workspace {
   double* dot_result = nullptr;       // 1 double
 };
 
-struct Gmg;  // geometric multigrid hierarchy (sem_gmg.cu)
+struct Gmg;   // geometric multigrid hierarchy (sem_gmg.cu)
+struct Tape;  // checkpoints of a recorded forward run (sem_adjoint.cu)
 
 struct Timing {
   bool enabled = false;
@@ -49,6 +50,7 @@ struct sem_ctx {
   sem::Timing timing;
   int64_t launches = 0;             // libsem kernels launched so far
   sem::Gmg* gmg = nullptr;          // built on first use of the multigrid preconditioner
+  sem::Tape* tape = nullptr;        // recorded forward run for the adjoint
   int gmg_degree = 3, gmg_coarse_degree = 10, gmg_min_coarse_dofs = 2000;
   int gmg_precision = SEM_PREC_FP32;
   sem_state* host_state = nullptr;  // device copy of the state for sem_step_host
@@ -85,6 +87,15 @@ int gmg_pcg(sem_ctx* ctx, double alpha, const double* b, double* x, double rtol,
             int maxit, int* iters, double* final_res, sem_stats* stats, cudaStream_t s);
 int gmg_info(sem_ctx* ctx, double alpha, int max_levels, int* nlevels, int* p, int* dims,
              int64_t* ndofs, double* lambda_max, cudaStream_t s);
+
+// Adjoint (sem_adjoint.cu).
+void tape_free(sem_ctx* ctx);
+int forward_record(sem_ctx* ctx, sem_state* st, double dt, int nsteps, int every,
+                   const int* sensors, int nsens, double* traces, double rtol, double atol,
+                   int maxit, int precond, sem_stats* stats, cudaStream_t s);
+int adjoint_grad(sem_ctx* ctx, const double* trace_bar, double* g_sl, double* g_st, double* g_th,
+                 double rtol, double atol, int maxit, int precond, sem_stats* stats,
+                 cudaStream_t s);
 int cuda_fail(sem_ctx* ctx, cudaError_t e, const char* what);
 
 }  // namespace sem

@@ -60,7 +60,7 @@ struct Gmg {
     cudaGraphExec_t init = nullptr, iter = nullptr;
     int64_t init_kernels = 0, iter_kernels = 0;
   };
-  Graphs graphs[4];
+  Graphs graphs[16];
   int next_graph = 0;
   cudaStream_t capture = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;           // recorded around the FP64 apply
@@ -947,7 +947,7 @@ int pcg_iter_seq(sem_ctx* ctx, Gmg& g, double alpha, double* x, cudaStream_t s) 
 }
 
 // Captures (once per solution pointer, right-hand side, alpha and tolerances) the
-// set-up and iteration sequences as CUDA graphs; four are cached.
+// set-up and iteration sequences as CUDA graphs; sixteen are cached.
 template <typename T>
 int get_graphs(sem_ctx* ctx, Gmg& g, double alpha, const double* b, double* x, double rtol,
                double atol, Gmg::Graphs** out) {
@@ -957,7 +957,7 @@ int get_graphs(sem_ctx* ctx, Gmg& g, double alpha, const double* b, double* x, d
       return SEM_OK;
     }
   Gmg::Graphs& gr = g.graphs[g.next_graph];
-  g.next_graph = (g.next_graph + 1) % 4;
+  g.next_graph = (g.next_graph + 1) % 16;
   if (gr.init) { cudaGraphExecDestroy(gr.init); gr.init = nullptr; }
   if (gr.iter) { cudaGraphExecDestroy(gr.iter); gr.iter = nullptr; }
   cudaStream_t cs = g.capture;
