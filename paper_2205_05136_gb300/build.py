@@ -29,6 +29,7 @@ SOURCES = [
     "sem_noalloc.cu",
     "sem_gmg.cu",
     "sem_adjoint.cu",
+    "sem_transfer.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -33,6 +33,12 @@
 
 namespace sem {
 
+// Sum-factorized p-transfers (sem_transfer.cu).
+template <typename T>
+cudaError_t p_transfer(bool prolong, const Level& F, const Level& C, const double (*P)[kMaxN],
+                       const T* src_b, const T* src_t, T* dst, T* dst_t, const int* done,
+                       cudaStream_t s);
+
 struct GmgLevel {
   Level* L = nullptr;
   bool owned = false;
@@ -138,97 +144,6 @@ struct PTab {
   int nf, nc;
   double P[kMaxN][kMaxN];  // P[i][a] = l^c_a(x^f_i)
 };
-
-// x_f += P x_c on the elements; each fine node is written by one element (the
-// highest-index element holding it), which also clears t_f there.
-template <typename T>
-__global__ void k_prolong_p(int nelem, int nx, int ny, int nz, const int* __restrict__ map_c,
-                            const int* __restrict__ map_f, const __grid_constant__ PTab tab,
-                            const T* __restrict__ xc, T* __restrict__ xf, T* __restrict__ tf,
-                            const int* done) {
-  if (skip(done)) return;
-  const int e = blockIdx.x;
-  if (e >= nelem) return;
-  const int nf = tab.nf, nc = tab.nc, pf = nf - 1;
-  const int nf3 = nf * nf * nf, nc3 = nc * nc * nc;
-  __shared__ T cv[kMaxN * kMaxN * kMaxN];
-  __shared__ T s1[kMaxN * kMaxN * kMaxN];
-  __shared__ T s2[kMaxN * kMaxN * kMaxN];
-  for (int a = threadIdx.x; a < nc3; a += blockDim.x) cv[a] = xc[map_c[(size_t)e * nc3 + a]];
-  __syncthreads();
-  for (int w = threadIdx.x; w < nc * nc * nf; w += blockDim.x) {  // [k_c][j_c][i_f]
-    const int i = w % nf, kj = w / nf;
-    T s = T(0);
-    for (int a = 0; a < nc; ++a) s += (T)tab.P[i][a] * cv[kj * nc + a];
-    s1[w] = s;
-  }
-  __syncthreads();
-  for (int w = threadIdx.x; w < nc * nf * nf; w += blockDim.x) {  // [k_c][j_f][i_f]
-    const int i = w % nf, j = (w / nf) % nf, k = w / (nf * nf);
-    T s = T(0);
-    for (int b = 0; b < nc; ++b) s += (T)tab.P[j][b] * s1[(k * nc + b) * nf + i];
-    s2[w] = s;
-  }
-  __syncthreads();
-  const int ex = e % nx, ey = (e / nx) % ny, ez = e / (nx * ny);
-  for (int w = threadIdx.x; w < nf3; w += blockDim.x) {  // [k_f][j_f][i_f]
-    const int i = w % nf, j = (w / nf) % nf, k = w / (nf * nf);
-    const bool own = (i < pf || ex == nx - 1) && (j < pf || ey == ny - 1) && (k < pf || ez == nz - 1);
-    if (!own) continue;
-    T s = T(0);
-    for (int c = 0; c < nc; ++c) s += (T)tab.P[k][c] * s2[(c * nf + j) * nf + i];
-    const int g = map_f[(size_t)e * nf3 + w];
-    xf[g] += s;
-    tf[g] = T(0);
-  }
-}
-
-// b_c += P^T (b_f - t_f) on the elements, fine residuals divided by the number
-// of elements sharing the node.
-template <typename T>
-__global__ void k_restrict_p(int nelem, int nx, int ny, int nz, const int* __restrict__ map_c,
-                             const int* __restrict__ map_f, const __grid_constant__ PTab tab,
-                             const T* __restrict__ bf, const T* __restrict__ tf,
-                             T* __restrict__ bc, const int* done) {
-  if (skip(done)) return;
-  const int e = blockIdx.x;
-  if (e >= nelem) return;
-  const int nf = tab.nf, nc = tab.nc, pf = nf - 1;
-  const int nf3 = nf * nf * nf, nc3 = nc * nc * nc;
-  __shared__ T fv[kMaxN * kMaxN * kMaxN];
-  __shared__ T s1[kMaxN * kMaxN * kMaxN];
-  __shared__ T s2[kMaxN * kMaxN * kMaxN];
-  const int ex = e % nx, ey = (e / nx) % ny, ez = e / (nx * ny);
-  for (int w = threadIdx.x; w < nf3; w += blockDim.x) {
-    const int i = w % nf, j = (w / nf) % nf, k = w / (nf * nf);
-    const int m = (((i == 0 && ex > 0) || (i == pf && ex < nx - 1)) ? 2 : 1) *
-                  (((j == 0 && ey > 0) || (j == pf && ey < ny - 1)) ? 2 : 1) *
-                  (((k == 0 && ez > 0) || (k == pf && ez < nz - 1)) ? 2 : 1);
-    const int g = map_f[(size_t)e * nf3 + w];
-    fv[w] = (bf[g] - tf[g]) / (T)m;
-  }
-  __syncthreads();
-  for (int w = threadIdx.x; w < nf * nf * nc; w += blockDim.x) {  // [k_f][j_f][a]
-    const int a = w % nc, kj = w / nc;
-    T s = T(0);
-    for (int i = 0; i < nf; ++i) s += (T)tab.P[i][a] * fv[kj * nf + i];
-    s1[w] = s;
-  }
-  __syncthreads();
-  for (int w = threadIdx.x; w < nf * nc * nc; w += blockDim.x) {  // [k_f][b][a]
-    const int a = w % nc, b = (w / nc) % nc, k = w / (nc * nc);
-    T s = T(0);
-    for (int j = 0; j < nf; ++j) s += (T)tab.P[j][b] * s1[(k * nf + j) * nc + a];
-    s2[w] = s;
-  }
-  __syncthreads();
-  for (int w = threadIdx.x; w < nc3; w += blockDim.x) {  // [c][b][a]
-    const int a = w % nc, b = (w / nc) % nc, c = w / (nc * nc);
-    T s = T(0);
-    for (int k = 0; k < nf; ++k) s += (T)tab.P[k][c] * s2[(k * nc + b) * nc + a];
-    atomicAdd(bc + map_c[(size_t)e * nc3 + w], s);
-  }
-}
 
 // Coarse vertex k (and k+1) and weights of fine vertex I along one direction.
 __device__ __forceinline__ void hweights(int I, int nf, int nc, int& k, double& w0, double& w1) {
@@ -579,8 +494,6 @@ PTab make_ptab(const Level& fine, const Level& coarse) {
   return t;
 }
 
-int transfer_threads(const Level& f) { return f.n * f.n * f.n <= 64 ? 64 : 128; }
-
 // Restrict (b_l - t_l) into b_{l+1} (zeroed first).
 template <typename T>
 int restrict_to(sem_ctx* ctx, Gmg& g, int l, const int* done, cudaStream_t s) {
@@ -589,9 +502,8 @@ int restrict_to(sem_ctx* ctx, Gmg& g, int l, const int* done, cudaStream_t s) {
   k_zero<T><<<grid1d(C.L->ndofs), kThreads, 0, s>>>(C.L->ndofs, (T*)C.b, done);
   if (F.to_next == 0) {
     const PTab tab = make_ptab(*F.L, *C.L);
-    k_restrict_p<T><<<F.L->nelem, transfer_threads(*F.L), 0, s>>>(
-        F.L->nelem, F.L->nx, F.L->ny, F.L->nz, C.L->map, F.L->map, tab, (const T*)F.b,
-        (const T*)F.t, (T*)C.b, done);
+    GMG_CK(p_transfer<T>(false, *F.L, *C.L, tab.P, (const T*)F.b, (const T*)F.t, (T*)C.b, nullptr,
+                         done, s));
   } else {
     k_restrict_h<T><<<grid1d(F.L->ndofs), kThreads, 0, s>>>(
         F.L->nx, F.L->ny, F.L->nz, C.L->nx, C.L->ny, C.L->nz, (const T*)F.b, (const T*)F.t,
@@ -608,9 +520,8 @@ int prolong_from(sem_ctx* ctx, Gmg& g, int l, const int* done, cudaStream_t s) {
   GmgLevel& C = g.lv[l + 1];
   if (F.to_next == 0) {
     const PTab tab = make_ptab(*F.L, *C.L);
-    k_prolong_p<T><<<F.L->nelem, transfer_threads(*F.L), 0, s>>>(
-        F.L->nelem, F.L->nx, F.L->ny, F.L->nz, C.L->map, F.L->map, tab, (const T*)C.x, (T*)F.x,
-        (T*)F.t, done);
+    GMG_CK(p_transfer<T>(true, *F.L, *C.L, tab.P, (const T*)C.x, nullptr, (T*)F.x, (T*)F.t, done,
+                         s));
   } else {
     k_prolong_h<T><<<grid1d(F.L->ndofs), kThreads, 0, s>>>(
         F.L->nx, F.L->ny, F.L->nz, C.L->nx, C.L->ny, C.L->nz, (const T*)C.x, (T*)F.x, (T*)F.t,

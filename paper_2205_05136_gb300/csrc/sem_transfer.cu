@@ -1,0 +1,218 @@
+// p-multigrid transfers between Q_pf and Q_pc on the same mesh, by sum
+// factorization (Section 4.3: transfers are matrix-vector products).
+//
+//   prolongation  x_f += P x_c:  per element, coarse nodal values -> fine nodes
+//                 through the 1-D interpolation matrix P[i_f][a_c] = l^c_a(x^f_i)
+//                 applied along x, y, z; each fine node is written by one
+//                 element (the highest-index element holding it), which also
+//                 clears the fine work vector t there;
+//   restriction   b_c += P^T (b_f - t_f): the fine residual, divided by the
+//                 number of elements sharing each node, goes through P^T along
+//                 x, y, z and is scatter-added to the coarse nodes.
+// Mapping as in the operator kernel: E elements per CTA in shared memory, one
+// 1-D line per thread and sweep, the matrix in the kernel-parameter bank.
+#include "sem_apply_kernel.cuh"
+#include "sem_context.cuh"
+
+namespace sem {
+namespace {
+
+constexpr int kTThreads = 256;
+
+template <int NF, int NC, typename T>
+struct PMat {
+  T P[NF][NC];
+};
+
+template <int NF> struct TransferCfg { static constexpr int E = (256 + NF * NF - 1) / (NF * NF); };
+
+// out[i] = sum_a P[i][a] in[a]  (NC -> NF)
+template <int NF, int NC, typename T>
+__device__ __forceinline__ void up_line(const T (&P)[NF][NC], const T (&in)[NC], T (&out)[NF]) {
+#pragma unroll
+  for (int i = 0; i < NF; ++i) {
+    T acc = P[i][0] * in[0];
+#pragma unroll
+    for (int a = 1; a < NC; ++a) acc = fma(P[i][a], in[a], acc);
+    out[i] = acc;
+  }
+}
+
+// out[a] = sum_i P[i][a] in[i]  (NF -> NC)
+template <int NF, int NC, typename T>
+__device__ __forceinline__ void down_line(const T (&P)[NF][NC], const T (&in)[NF], T (&out)[NC]) {
+#pragma unroll
+  for (int a = 0; a < NC; ++a) {
+    T acc = P[0][a] * in[0];
+#pragma unroll
+    for (int i = 1; i < NF; ++i) acc = fma(P[i][a], in[i], acc);
+    out[a] = acc;
+  }
+}
+
+template <int NF, int NC, typename T>
+__global__ void __launch_bounds__(kTThreads)
+    k_prolong_sf(int nelem, int nx, int ny, int nz, const int* __restrict__ map_c,
+                 const int* __restrict__ map_f, const __grid_constant__ PMat<NF, NC, T> pm,
+                 const T* __restrict__ xc, T* __restrict__ xf, T* __restrict__ tf, const int* done) {
+  if (done != nullptr && *done) return;
+  constexpr int E = TransferCfg<NF>::E;
+  constexpr int NF3 = NF * NF * NF, NC3 = NC * NC * NC;
+  __shared__ T c0[E * NC3];
+  __shared__ T s1[E * NC * NC * NF];  // [k_c][j_c][i_f]
+  __shared__ T s2[E * NC * NF * NF];  // [k_c][j_f][i_f]
+  const int e0 = blockIdx.x * E;
+  for (int idx = threadIdx.x; idx < E * NC3; idx += blockDim.x) {
+    const int s = idx / NC3, a = idx - s * NC3, e = e0 + s;
+    c0[idx] = e < nelem ? xc[map_c[(size_t)e * NC3 + a]] : T(0);
+  }
+  __syncthreads();
+  for (int w = threadIdx.x; w < E * NC * NC; w += blockDim.x) {  // x-lines (j_c, k_c)
+    const int s = w / (NC * NC), l = w - s * NC * NC;
+    T in[NC], out[NF];
+#pragma unroll
+    for (int a = 0; a < NC; ++a) in[a] = c0[s * NC3 + l * NC + a];
+    up_line<NF, NC>(pm.P, in, out);
+#pragma unroll
+    for (int i = 0; i < NF; ++i) s1[s * NC * NC * NF + l * NF + i] = out[i];
+  }
+  __syncthreads();
+  for (int w = threadIdx.x; w < E * NC * NF; w += blockDim.x) {  // y-lines (i_f, k_c)
+    const int s = w / (NC * NF), l = w - s * NC * NF, i = l % NF, k = l / NF;
+    T in[NC], out[NF];
+#pragma unroll
+    for (int b = 0; b < NC; ++b) in[b] = s1[s * NC * NC * NF + (k * NC + b) * NF + i];
+    up_line<NF, NC>(pm.P, in, out);
+#pragma unroll
+    for (int j = 0; j < NF; ++j) s2[s * NC * NF * NF + (k * NF + j) * NF + i] = out[j];
+  }
+  __syncthreads();
+  for (int w = threadIdx.x; w < E * NF * NF; w += blockDim.x) {  // z-lines (i_f, j_f)
+    const int s = w / (NF * NF), l = w - s * NF * NF, i = l % NF, j = l / NF, e = e0 + s;
+    if (e >= nelem) continue;
+    T in[NC], out[NF];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) in[c] = s2[s * NC * NF * NF + (c * NF + j) * NF + i];
+    up_line<NF, NC>(pm.P, in, out);
+    const int ex = e % nx, ey = (e / nx) % ny, ez = e / (nx * ny);
+    const bool own_xy = (i < NF - 1 || ex == nx - 1) && (j < NF - 1 || ey == ny - 1);
+    if (!own_xy) continue;
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+      if (k == NF - 1 && ez != nz - 1) continue;
+      const int g = map_f[(size_t)e * NF3 + (k * NF + j) * NF + i];
+      xf[g] += out[k];
+      tf[g] = T(0);
+    }
+  }
+}
+
+template <int NF, int NC, typename T>
+__global__ void __launch_bounds__(kTThreads)
+    k_restrict_sf(int nelem, int nx, int ny, int nz, const int* __restrict__ map_c,
+                  const int* __restrict__ map_f, const __grid_constant__ PMat<NF, NC, T> pm,
+                  const T* __restrict__ bf, const T* __restrict__ tf, T* __restrict__ bc,
+                  const int* done) {
+  if (done != nullptr && *done) return;
+  constexpr int E = TransferCfg<NF>::E;
+  constexpr int NF3 = NF * NF * NF, NC3 = NC * NC * NC;
+  __shared__ T f0[E * NF3];
+  __shared__ T s1[E * NF * NF * NC];  // [k_f][j_f][a]
+  __shared__ T s2[E * NF * NC * NC];  // [k_f][b][a]
+  const int e0 = blockIdx.x * E;
+  for (int idx = threadIdx.x; idx < E * NF3; idx += blockDim.x) {
+    const int s = idx / NF3, loc = idx - s * NF3, e = e0 + s;
+    T v = T(0);
+    if (e < nelem) {
+      const int i = loc % NF, j = (loc / NF) % NF, k = loc / (NF * NF);
+      const int ex = e % nx, ey = (e / nx) % ny, ez = e / (nx * ny);
+      const int m = (((i == 0 && ex > 0) || (i == NF - 1 && ex < nx - 1)) ? 2 : 1) *
+                    (((j == 0 && ey > 0) || (j == NF - 1 && ey < ny - 1)) ? 2 : 1) *
+                    (((k == 0 && ez > 0) || (k == NF - 1 && ez < nz - 1)) ? 2 : 1);
+      const int g = map_f[(size_t)e * NF3 + loc];
+      v = (bf[g] - tf[g]) / (T)m;
+    }
+    f0[idx] = v;
+  }
+  __syncthreads();
+  for (int w = threadIdx.x; w < E * NF * NF; w += blockDim.x) {  // x-lines (j_f, k_f)
+    const int s = w / (NF * NF), l = w - s * NF * NF;
+    T in[NF], out[NC];
+#pragma unroll
+    for (int i = 0; i < NF; ++i) in[i] = f0[s * NF3 + l * NF + i];
+    down_line<NF, NC>(pm.P, in, out);
+#pragma unroll
+    for (int a = 0; a < NC; ++a) s1[s * NF * NF * NC + l * NC + a] = out[a];
+  }
+  __syncthreads();
+  for (int w = threadIdx.x; w < E * NF * NC; w += blockDim.x) {  // y-lines (a, k_f)
+    const int s = w / (NF * NC), l = w - s * NF * NC, a = l % NC, k = l / NC;
+    T in[NF], out[NC];
+#pragma unroll
+    for (int j = 0; j < NF; ++j) in[j] = s1[s * NF * NF * NC + (k * NF + j) * NC + a];
+    down_line<NF, NC>(pm.P, in, out);
+#pragma unroll
+    for (int b = 0; b < NC; ++b) s2[s * NF * NC * NC + (k * NC + b) * NC + a] = out[b];
+  }
+  __syncthreads();
+  for (int w = threadIdx.x; w < E * NC * NC; w += blockDim.x) {  // z-lines (a, b)
+    const int s = w / (NC * NC), l = w - s * NC * NC, a = l % NC, b = l / NC, e = e0 + s;
+    if (e >= nelem) continue;
+    T in[NF], out[NC];
+#pragma unroll
+    for (int k = 0; k < NF; ++k) in[k] = s2[s * NF * NC * NC + (k * NC + b) * NC + a];
+    down_line<NF, NC>(pm.P, in, out);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) atomicAdd(bc + map_c[(size_t)e * NC3 + (c * NC + b) * NC + a], out[c]);
+  }
+}
+
+template <int NF, int NC, typename T>
+cudaError_t launch_pair(bool prolong, const Level& F, const Level& C, const double (*P)[kMaxN],
+                        const T* src_b, const T* src_t, T* dst, T* dst_t, const int* done,
+                        cudaStream_t s) {
+  PMat<NF, NC, T> pm;
+  for (int i = 0; i < NF; ++i)
+    for (int a = 0; a < NC; ++a) pm.P[i][a] = (T)P[i][a];
+  const int E = TransferCfg<NF>::E;
+  const int grid = (F.nelem + E - 1) / E;
+  if (prolong)
+    k_prolong_sf<NF, NC, T><<<grid, kTThreads, 0, s>>>(F.nelem, F.nx, F.ny, F.nz, C.map, F.map, pm,
+                                                       src_b, dst, dst_t, done);
+  else
+    k_restrict_sf<NF, NC, T><<<grid, kTThreads, 0, s>>>(F.nelem, F.nx, F.ny, F.nz, C.map, F.map, pm,
+                                                        src_b, src_t, dst, done);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// prolong: dst (fine x) += P src_b (coarse x), dst_t (fine t) cleared.
+// restrict: dst (coarse b) += P^T (src_b - src_t) (fine b, fine t).
+template <typename T>
+cudaError_t p_transfer(bool prolong, const Level& F, const Level& C, const double (*P)[kMaxN],
+                       const T* src_b, const T* src_t, T* dst, T* dst_t, const int* done,
+                       cudaStream_t s) {
+  const int nf = F.n, nc = C.n;
+#define SEM_PAIR(A, B) \
+  if (nf == A && nc == B) return launch_pair<A, B, T>(prolong, F, C, P, src_b, src_t, dst, dst_t, done, s);
+  SEM_PAIR(7, 4)
+  SEM_PAIR(6, 3)
+  SEM_PAIR(5, 3)
+  SEM_PAIR(4, 2)
+  SEM_PAIR(3, 2)
+  SEM_PAIR(7, 2)
+  SEM_PAIR(6, 2)
+  SEM_PAIR(5, 2)
+#undef SEM_PAIR
+  return cudaErrorInvalidValue;
+}
+
+template cudaError_t p_transfer<float>(bool, const Level&, const Level&, const double (*)[kMaxN],
+                                       const float*, const float*, float*, float*, const int*,
+                                       cudaStream_t);
+template cudaError_t p_transfer<double>(bool, const Level&, const Level&, const double (*)[kMaxN],
+                                        const double*, const double*, double*, double*, const int*,
+                                        cudaStream_t);
+
+}  // namespace sem

@@ -39,7 +39,7 @@ def _setup(dims, p, quad, min_coarse, precision, perturb=0.1):
 
 
 @pytest.mark.parametrize("quad", ["LGL", "LG"])
-@pytest.mark.parametrize("dims,p", [((6, 4, 3), 4), ((5, 3, 3), 3), ((4, 4, 2), 6)])
+@pytest.mark.parametrize("dims,p", [((6, 4, 3), 4), ((5, 3, 3), 3), ((4, 4, 2), 6), ((3, 3, 2), 5), ((6, 3, 2), 2)])
 def test_hierarchy_and_vcycle_fp64(dims, p, quad):
     s, tissue, g, o, H = _setup(dims, p, quad, 30, capi.SEM_PREC_FP64)
     info = capi.sem_gmg_info(g.ctx, ALPHA)
