@@ -43,6 +43,7 @@ MAXIT = 2000
 STIM_RADIUS = 1.5    # mm
 STIM_AMP = 50.0      # mV/ms
 STIM_T_OFF = 1.0     # ms
+SLAB_LENGTHS = W.SLAB_LENGTHS_MM
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64: 152 SMs x 2 DFMA/clk x 2 flop x ~2.06 GHz
 
 # DRAM bytes (read + write) per launch of the CG apply kernel from one ncu capture
@@ -420,6 +421,185 @@ def run_sweep(args):
             torch.cuda.empty_cache()
 
 
+def _slab_ctx(gb, s, p, quad, tissue, dev=0):
+    slab = gb.Slab(s.flat_vertices(), s.nx, s.ny, s.nz, p, quad, device=dev)
+    slab.set_tissue(*tissue)
+    slab.set_ionic()
+    return slab
+
+
+def run_gmg8m(args):
+    """Full FP64-accurate monodomain run on a 40 x 20 x 6 mm slab at p = 4
+    (128 x 64 x 16 elements, 8.57 M DOFs), rotating fibres, 200 steps of
+    0.05 ms (10 ms), seeded stimulus ball r = 1.5 mm; flexible FP64 PCG with the
+    p-then-h multigrid (Chebyshev 3) in FP32."""
+    import torch
+    import paper_2205_05136_gb300 as gb
+    from paper_2205_05136_gb300 import build as gbuild, capi
+    gbuild.build()
+    s = W.slab(128, 64, 16, (40.0, 20.0, 6.0), perturb=0.1, seed=W.SEED_MESH)
+    ne = s.n_elements
+    tissue = (np.full(ne, 0.12), np.full(ne, 0.03), W.transmural_fiber_angles(s))
+    slab = _slab_ctx(gb, s, 4, args.quad, tissue)
+    centre = W.seeded_point(s.lengths, STIM_RADIUS, seed=W.SEED_STIM)
+    slab.set_stimulus("sphere", (*centre, STIM_RADIUS), STIM_AMP, 0.0, STIM_T_OFF)
+    capi.sem_set_gmg(slab.ctx, 3, 10, 2000, gb.SEM_PREC_FP32)
+    info = capi.sem_gmg_info(slab.ctx, 1.5 / DT)
+    slab.set_timing(True)
+    nsteps = args.steps if args.steps != 20 else 200
+    st = slab.new_state(-85.0, 1.0)
+    st.step(DT, 3, rtol=RTOL, maxit=MAXIT, precond=gb.SEM_PC_GMG)
+    st.restore({"u": torch.full((slab.ndofs,), -85.0, dtype=torch.float64, device="cuda"),
+                "u_prev": torch.full((slab.ndofs,), -85.0, dtype=torch.float64, device="cuda"),
+                "h": torch.ones(slab.ndofs, dtype=torch.float64, device="cuda"),
+                "h_prev": torch.ones(slab.ndofs, dtype=torch.float64, device="cuda"), "n": 0})
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    stats = st.step(DT, nsteps, rtol=RTOL, maxit=MAXIT, precond=gb.SEM_PC_GMG)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    u, h, n = st.get()
+    print(json.dumps({
+        "workload": "gmg8m: 40x20x6 mm slab, 128x64x16 Q4 elements, 10 ms of activation",
+        "ndofs": slab.ndofs, "steps": nsteps, "seconds": el, "steps_per_s": nsteps / el,
+        "gdof_steps_per_s": slab.ndofs * nsteps / el / 1e9,
+        "cg_iters_per_step": stats.cg_iters / nsteps,
+        "levels": {"p": info["p"], "dims": info["dims"], "ndofs": info["ndofs"]},
+        "u_max_mV": float(u.max()), "activated_fraction": float((u > -40.0).double().mean()),
+        "apply_ms": stats.apply_ms / max(stats.n_apply, 1)}), flush=True)
+    st.close()
+    slab.close()
+
+
+def run_mixed30m(args):
+    """Mixed precision at ~30 M DOFs (p = 4: 207 x 72 x 31; p = 6: 137 x 48 x 21):
+    per-field relative L2 and Linf errors of u and h after K steps with the FP32
+    and bf16-metric multigrid against the plain FP64 path, sampled operator rows
+    against the oracle, and step times."""
+    import torch
+    import paper_2205_05136_gb300 as gb
+    from paper_2205_05136_gb300 import build as gbuild, capi
+    from oracle import mesh as Mh
+    gbuild.build()
+    nsteps = args.steps if args.steps != 20 else 10
+    for p, dims in ((4, (207, 72, 31)), (6, (137, 48, 21))):
+        s = W.slab(*dims, SLAB_LENGTHS, perturb=0.1, seed=W.SEED_MESH)
+        ne = s.n_elements
+        tissue = (np.full(ne, 0.12), np.full(ne, 0.03), W.transmural_fiber_angles(s))
+        slab = _slab_ctx(gb, s, p, args.quad, tissue)
+        centre = W.seeded_point(s.lengths, STIM_RADIUS, seed=W.SEED_STIM)
+        slab.set_stimulus("sphere", (*centre, STIM_RADIUS), STIM_AMP, 0.0, STIM_T_OFF)
+        # sampled operator rows against the oracle
+        o = Mh.SlabSpace(s.flat_vertices(), *dims, p, args.quad)
+        uvec = W.uniform_vector(slab.ndofs, seed=W.SEED_U)
+        ut = torch.tensor(uvec, device="cuda")
+        y64 = slab.apply(ut, 30.0, 1.0).cpu().numpy()
+        idx = W.seeded_indices(slab.ndofs, 16, seed=7)
+        ref = Mh.sampled_rows(o, tissue, uvec, idx, 30.0, 1.0)
+        op_err = float(np.abs(y64[idx] - ref).max() / np.abs(ref).max())
+        y32 = slab.apply(ut.float(), 30.0, 1.0, precision=gb.SEM_PREC_FP32).double().cpu().numpy()
+        y16 = slab.apply(ut.float(), 30.0, 1.0, precision=gb.SEM_PREC_FP32_BF16).double().cpu().numpy()
+        rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))  # noqa: E731
+        out = {"workload": f"mixed30m p={p}", "ndofs": slab.ndofs, "nelem": ne, "steps": nsteps,
+               "apply_rel_err_fp64_vs_oracle_sampled": op_err,
+               "apply_rel_l2_fp32_vs_fp64": rel(y32, y64), "apply_rel_l2_bf16_vs_fp64": rel(y16, y64)}
+        results = {}
+        for name, pc, prec in (("fp64_jacobi", gb.SEM_PC_JACOBI, None),
+                               ("gmg_fp32", gb.SEM_PC_GMG, gb.SEM_PREC_FP32),
+                               ("gmg_bf16", gb.SEM_PC_GMG, gb.SEM_PREC_FP32_BF16)):
+            if prec is not None:
+                capi.sem_set_gmg(slab.ctx, 3, 8, 40000, prec)
+            st = slab.new_state(-85.0, 1.0)
+            st.step(DT, 1, rtol=RTOL, maxit=MAXIT * 4, precond=pc)  # warm-up (BDF1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            stt = st.step(DT, nsteps, rtol=RTOL, maxit=MAXIT * 4, precond=pc)
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            u, h, _ = st.get()
+            results[name] = (u, h)
+            out[name] = {"ms_per_step": el / nsteps * 1e3, "cg_iters_per_step": stt.cg_iters / nsteps}
+            st.close()
+        u64, h64 = results["fp64_jacobi"]
+        for name in ("gmg_fp32", "gmg_bf16"):
+            u, h = results[name]
+            out[name]["u_rel_l2"] = float(torch.linalg.norm(u - u64) / torch.linalg.norm(u64))
+            out[name]["u_rel_linf"] = float((u - u64).abs().max() / u64.abs().max())
+            out[name]["h_rel_l2"] = float(torch.linalg.norm(h - h64) / torch.linalg.norm(h64))
+            out[name]["h_rel_linf"] = float((h - h64).abs().max() / h64.abs().max())
+            out[name]["speedup_vs_fp64"] = out["fp64_jacobi"]["ms_per_step"] / out[name]["ms_per_step"]
+        print(json.dumps(out), flush=True)
+        slab.close()
+        del results
+        torch.cuda.empty_cache()
+
+
+def run_adjoint(args):
+    """Adjoint at p = 3 on a 140 x 49 x 21 deformed slab (3.99 M DOFs), 200 steps,
+    checkpoint every 20, 64 seeded sensors; target from conductivities perturbed
+    by U[0.8, 1.2] per element; gradient checked by central differences
+    (h = 1e-6) on 16 seeded elements x (sigma_l, sigma_t, theta)."""
+    import torch
+    import paper_2205_05136_gb300 as gb
+    from paper_2205_05136_gb300 import build as gbuild, capi
+    gbuild.build()
+    nsteps = args.steps if args.steps != 20 else 200
+    s = W.slab(140, 49, 21, SLAB_LENGTHS, perturb=0.1, seed=W.SEED_MESH)
+    ne = s.n_elements
+    base = (np.full(ne, 0.12), np.full(ne, 0.03), W.transmural_fiber_angles(s))
+    slab = _slab_ctx(gb, s, 3, args.quad, base)
+    centre = W.seeded_point(s.lengths, STIM_RADIUS, seed=W.SEED_STIM)
+    slab.set_stimulus("sphere", (*centre, STIM_RADIUS), STIM_AMP, 0.0, STIM_T_OFF)
+    capi.sem_set_gmg(slab.ctx, 3, 8, 40000, gb.SEM_PREC_FP32)
+    sensors = torch.tensor(W.seeded_indices(slab.ndofs, 64, seed=W.SEED_SENSORS), dtype=torch.int32)
+    dev = torch.device("cuda")
+    u0 = torch.full((slab.ndofs,), -85.0, dtype=torch.float64, device=dev)
+    h0 = torch.ones(slab.ndofs, dtype=torch.float64, device=dev)
+    kw = dict(checkpoint_every=20, rtol=1e-12, maxit=4 * MAXIT, precond=gb.SEM_PC_GMG)
+    pl, pt = W.perturbed_conductivities(base[0], base[1])
+    with torch.no_grad():
+        target = gb.traces(slab, torch.tensor(pl, device=dev), torch.tensor(pt, device=dev),
+                           torch.tensor(base[2], device=dev), u0, h0, DT, nsteps, sensors, **kw)
+    prm = [torch.tensor(b, device=dev, requires_grad=True) for b in base]
+
+    def loss_of(params):
+        T = gb.traces(slab, params[0], params[1], params[2], u0, h0, DT, nsteps, sensors, **kw)
+        return 0.5 * DT * torch.sum((T - target) ** 2)
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    L = loss_of(prm)
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    L.backward()
+    torch.cuda.synchronize()
+    t_bwd = time.perf_counter() - t0
+    grads = [p.grad.detach().cpu().numpy() for p in prm]
+    elems = W.seeded_indices(ne, 16, seed=W.SEED_FD)
+    checks, worst = [], 0.0
+    h = 1e-6
+    with torch.no_grad():
+        for k in range(3):
+            scale = np.abs(grads[k]).max()
+            for e in elems:
+                vals = []
+                for sgn in (1.0, -1.0):
+                    q = [t.detach().clone() for t in prm]
+                    q[k][e] += sgn * h
+                    vals.append(float(loss_of(q)))
+                fd = (vals[0] - vals[1]) / (2 * h)
+                err = abs(grads[k][e] - fd) / max(abs(fd), 1e-3 * scale)
+                worst = max(worst, err)
+                checks.append((k, int(e), float(grads[k][e]), fd))
+    print(json.dumps({
+        "workload": "adjoint p=3 140x49x21 (3.99 M DOFs), 200 steps, checkpoint 20, 64 sensors",
+        "ndofs": slab.ndofs, "steps": nsteps, "loss": float(L), "forward_s": t_fwd, "backward_s": t_bwd,
+        "fd_checks": len(checks), "fd_max_rel_dev": worst, "fd_h": h, "fd_samples": checks[:6]}),
+        flush=True)
+    slab.close()
+
+
 def run_reference(args):
     """Reference arm: the CPU oracle as it stands, on this workload."""
     rank = int(os.environ.get("RANK", "0"))
@@ -478,6 +658,8 @@ def main():
     # the iteration count (6 per step either way), so the benchmark stops at p = 1
     ap.add_argument("--mg-coarse-degree", type=int, default=8)
     ap.add_argument("--mg-min-coarse-dofs", type=int, default=40000)
+    ap.add_argument("--workload", default="timestep", choices=["timestep", "gmg8m", "mixed30m", "adjoint"],
+                    help="extra measurements of the multigrid, mixed-precision and adjoint workloads")
     ap.add_argument("--sweep", action="store_true")
     ap.add_argument("--sweep-p", type=int, nargs="*", default=[1, 2, 3, 4, 5, 6])
     args = ap.parse_args()
@@ -485,6 +667,12 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "gmg8m":
+        run_gmg8m(args)
+    elif args.workload == "mixed30m":
+        run_mixed30m(args)
+    elif args.workload == "adjoint":
+        run_adjoint(args)
     elif args.sweep:
         run_sweep(args)
     else:
