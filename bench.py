@@ -67,6 +67,15 @@ def apply_flops_per_element(p: int, quad: str) -> int:
     return sweeps * 2 * n ** 4 + 22 * n ** 3
 
 
+def apply_bytes_per_element_fp32(p: int, metric: str = "fp32") -> int:
+    """Algorithmic HBM bytes of one FP32 element apply: 7 metric values per
+    quadrature point (4 bytes, or 2 with the bf16 metric), the int32 map, and
+    u read + y written once per node (4 bytes each)."""
+    n = p + 1
+    mb = 2 if metric == "bf16" else 4
+    return 7 * mb * n ** 3 + 4 * n ** 3 + 8 * p ** 3
+
+
 def apply_bytes_per_element(p: int) -> int:
     """Algorithmic HBM bytes of one FP64 element apply: 7 metric doubles per
     quadrature point, the int32 map, and u read + y written once per node."""
@@ -90,7 +99,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -255,6 +264,7 @@ def run_gpu(args):
     capi.sem_set_gmg(slab.ctx, args.mg_degree, args.mg_coarse_degree, args.mg_min_coarse_dofs, prec)
 
     # plain FP64 path: Jacobi-CG with the FP64 operator
+    capi.sem_set_operator_precision(slab.ctx, gb.SEM_PREC_FP64)
     if args.arms in ("both", "fp64"):
         ms64, st64, u64, state64, clk64 = time_arm(slab, gb.SEM_PC_JACOBI, args, dist, dev,
                                                    clocks=args.arms == "fp64")
@@ -264,7 +274,11 @@ def run_gpu(args):
         state = slab.new_state(-85.0, 1.0)
         state.step(DT, 2, rtol=RTOL, maxit=MAXIT)
     else:
-        # mixed-precision path: flexible FP64 CG preconditioned by the FP32 multigrid V-cycle
+        # mixed-precision path: flexible FP64 CG (operator in double-float arithmetic unless
+        # --op-precision fp64) preconditioned by the FP32 multigrid V-cycle
+        capi.sem_set_operator_precision(
+            slab.ctx, gb.SEM_PREC_DF64 if args.op_precision == "df64" else gb.SEM_PREC_FP64)
+        capi.sem_set_gmg(slab.ctx, args.mg_degree, args.mg_coarse_degree, args.mg_min_coarse_dofs, prec)
         msmx, stats, umx, state, clk = time_arm(slab, gb.SEM_PC_GMG, args, dist, dev, clocks=True)
     if args.arms == "mixed":
         ms64, st64, u64 = float("nan"), stats, umx
@@ -278,6 +292,51 @@ def run_gpu(args):
     achieved_tf = flops / (apply_ms * 1e-3) / 1e12
     algo_bytes = n_e * apply_bytes_per_element(p)
     apply64_ms = st64.apply_ms / max(st64.n_apply, 1)
+    pk = peaks()
+    hbm_peak = pk.get("hbm_gbs", 6780.0)
+    outer_is_df = args.arms != "fp64" and args.op_precision == "df64"
+    outer = {
+        "kernel": f"sem_apply_kernel<P={p},{quad},{'df64' if outer_is_df else 'f64'},dot> (outer CG operator)",
+        "launches": int(stats.n_apply), "avg_ms": apply_ms,
+        "total_ms": apply_ms * stats.n_apply,
+        "fp64_equivalent_tflops": achieved_tf,
+        "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": algo_bytes,
+    }
+    kernels = {"outer_apply": outer}
+    dominant = "outer_apply"
+    if stats.n_smoother_apply > 0:
+        sm_ms = stats.smoother_apply_ms / stats.n_smoother_apply
+        sm_bytes = n_e * apply_bytes_per_element_fp32(p, args.mg_precision)
+        per_vcycle = 2 * args.mg_degree  # fine-level applies per V-cycle
+        kernels["smoother_apply"] = {
+            "kernel": f"sem_apply_kernel<P={p},{quad},f32,{'bf16' if args.mg_precision == 'bf16' else 'f32'} metric> "
+                      f"(fine-level V-cycle apply)",
+            "timed": int(stats.n_smoother_apply), "avg_ms": sm_ms,
+            "total_ms_est": sm_ms * per_vcycle * stats.n_smoother_apply,
+            "algorithmic_bytes_per_launch": sm_bytes,
+            "achieved_gbs": sm_bytes / (sm_ms * 1e-3) / 1e9,
+        }
+        if kernels["smoother_apply"]["total_ms_est"] > outer["total_ms"]:
+            dominant = "smoother_apply"
+    if dominant == "smoother_apply":
+        ksm = kernels["smoother_apply"]
+        roofline = {"bound": "hbm", "achieved": ksm["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
+                    "frac": ksm["achieved_gbs"] / hbm_peak, "traffic": None, "kernel": ksm["kernel"],
+                    "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs), burst figure"}
+    elif outer_is_df:
+        roofline = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": None, "kernel": outer["kernel"],
+                    "peak_note": ("FP64-equivalent flops of the double-float operator, which runs on the FP32 pipe, "
+                                  "against the nominal native FP64 peak of 1.25 TFLOP/s")}
+    else:
+        roofline = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved_tf / FP64_PEAK_TFLOPS,
+                    "traffic": args.traffic if args.traffic is not None else NCU_TRAFFIC.get((p, quad)),
+                    "kernel": outer["kernel"],
+                    "peak_note": "nominal FP64 1.25 TFLOP/s (no FP64 figure in MEASURED_PEAKS.json; DFMA probe measured 1.19)"}
+    roofline["algorithmic_flops_per_launch"] = flops if dominant == "outer_apply" else None
+    roofline["algorithmic_bytes_per_launch"] = (algo_bytes if dominant == "outer_apply"
+                                                else kernels["smoother_apply"]["algorithmic_bytes_per_launch"])
 
     # end to end through the public C ABI with host buffers (page-locked), one
     # step per call, continuing from the device state reached above
@@ -309,7 +368,6 @@ def run_gpu(args):
         except Exception as exc:  # report, never fail the GPU line
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {exc}"}
 
-    pk = peaks()
     line = {
         "metric": METRIC,
         "value": value,
@@ -321,13 +379,15 @@ def run_gpu(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64 (outer CG, residuals, inner products, ionic exp) + f32 (multigrid V-cycle)",
+        "dtype": ("f64 vectors, residuals, inner products, ionic exp; "
+                  f"{'double-float (f32 pairs)' if outer_is_df else 'f64'} operator; f32 multigrid V-cycle"),
         "data": "synthetic",
         "config": {
             "workload": (f"monodomain BDF2 time step, {'SEM-NI' if quad == 'LGL' else 'SEM'} Q{p} slab "
                          f"20x7x3 mm, {s.nx}x{s.ny}x{s.nz} hexahedra, {n_d} DOFs, +-10% vertex perturbation, "
                          f"fibres -60..+60 deg, dt {DT} ms, CG rtol {RTOL}"),
-            "solver": (f"flexible FP64 PCG + {args.mg_precision} GMG V-cycle (p-then-h coarsening, "
+            "solver": (f"flexible FP64 PCG ({args.op_precision} operator) + {args.mg_precision} GMG V-cycle "
+                       f"(p-then-h coarsening down to {args.mg_min_coarse_dofs} nodes, "
                        f"Chebyshev({args.mg_degree}), coarse Chebyshev({args.mg_coarse_degree}))"),
             "p": p, "quadrature": quad, "ndofs": n_d, "nelem": n_e,
             "parallelism": f"replicas x{ws}",
@@ -343,19 +403,12 @@ def run_gpu(args):
                       "apply_ms": apply64_ms, "apply_gdofs": n_d / (apply64_ms * 1e-3) / 1e9},
         "mixed_vs_fp64": {"speedup": ms64 / msmx, "rel_l2_u_diff": diff,
                           "note": "u after warm-up + timed steps of both paths, same start state"},
-        "roofline": {
-            "bound": "alu",
-            "achieved": achieved_tf,
-            "peak": FP64_PEAK_TFLOPS,
-            "unit": "TFLOP/s",
-            "frac": achieved_tf / FP64_PEAK_TFLOPS,
-            "traffic": args.traffic if args.traffic is not None else NCU_TRAFFIC.get((p, quad)),
-            "kernel": f"sem_apply_kernel<P={p},{quad},f64,dot> (outer-CG operator apply)",
-            "algorithmic_flops_per_launch": flops,
-            "algorithmic_bytes_per_launch": algo_bytes,
-            "hbm_frac_of_measured": (algo_bytes / (apply_ms * 1e-3) / 1e9) / pk.get("hbm_gbs", 6780.0),
-            "peak_note": "nominal FP64 1.25 TFLOP/s (no FP64 figure in MEASURED_PEAKS.json; DFMA probe measured 1.19)",
-        },
+        "roofline": roofline,
+        "kernels": kernels,
+        "fp64_apply_roofline": {"bound": "alu", "kernel": f"sem_apply_kernel<P={p},{quad},f64,dot> (plain FP64 path)",
+                                "achieved": flops / (apply64_ms * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                                "unit": "TFLOP/s", "frac": flops / (apply64_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+                                "traffic": NCU_TRAFFIC.get((p, quad))} if args.arms != "mixed" else None,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * 8 * n_d,
                 "d2h_bytes_per_step": 4 * 8 * n_d, "steps": n_e2e},
         "gpu_launches": int(stats.kernel_launches),
@@ -400,6 +453,21 @@ def run_sweep(args):
                    "tflops_algorithmic": flops / t / 1e12,
                    "frac_fp64_peak": flops / t / 1e12 / FP64_PEAK_TFLOPS,
                    "gbs_algorithmic": slab.nelem * apply_bytes_per_element(p) / t / 1e9}
+            ydf = torch.empty_like(u)
+            slab.apply(u, 30.0, 1.0, precision=gb.SEM_PREC_DF64, out=ydf)
+            torch.cuda.synchronize()
+            tdf = []
+            for _ in range(args.steps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                slab.apply(u, 30.0, 1.0, precision=gb.SEM_PREC_DF64, out=ydf)
+                b.record()
+                torch.cuda.synchronize()
+                tdf.append(a.elapsed_time(b) * 1e-3)
+            tdf = statistics.median(tdf)
+            out["df64_gdofs"] = slab.ndofs / tdf / 1e9
+            out["df64_apply_ms"] = tdf * 1e3
+            out["df64_rel_diff_vs_fp64"] = float(torch.linalg.norm(ydf - y) / torch.linalg.norm(y))
             for prec, name in ((gb.SEM_PREC_FP32, "fp32"), (gb.SEM_PREC_FP32_BF16, "fp32_bf16")):
                 u32 = u.float()
                 y32 = torch.empty_like(u32)
@@ -651,6 +719,8 @@ def main():
                     help="dram bytes per apply launch from an ncu capture of the current kernel")
     ap.add_argument("--ref-applies-per-step", type=float, default=33.0)
     ap.add_argument("--mg-precision", default="fp32", choices=["fp32", "bf16", "fp64"])
+    ap.add_argument("--op-precision", default="df64", choices=["df64", "fp64"],
+                    help="arithmetic of the outer CG operator in the mixed path")
     ap.add_argument("--arms", default="both", choices=["both", "mixed", "fp64"],
                     help="time the mixed-precision multigrid path, the plain FP64 path, or both")
     ap.add_argument("--mg-degree", type=int, default=3)

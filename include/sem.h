@@ -59,6 +59,8 @@ extern "C" {
 #define SEM_PREC_FP64 0      /* double vectors, double metric, double arithmetic */
 #define SEM_PREC_FP32 1      /* float vectors, float metric, float arithmetic */
 #define SEM_PREC_FP32_BF16 2 /* float vectors, bfloat16 metric, float arithmetic */
+#define SEM_PREC_DF64 3      /* double vectors, metric split into float pairs, double-float
+                                arithmetic on the FP32 pipe (FP64 results to ~1e-14) */
 
 #define SEM_PC_NONE 0
 #define SEM_PC_JACOBI 1
@@ -89,6 +91,8 @@ typedef struct {
   double apply_ms;        /* device time of operator-apply kernels (when timing on) */
   int64_t n_apply;        /* operator-apply launches timed */
   int64_t kernel_launches; /* libsem kernels launched by the call */
+  double smoother_apply_ms;   /* device time of timed fine-level multigrid smoother applies */
+  int64_t n_smoother_apply;   /* fine-level smoother applies timed (one per V-cycle) */
 } sem_stats;
 
 /* Library version string (static storage). */
@@ -128,11 +132,17 @@ int sem_set_tissue(sem_ctx* ctx, const double* sigma_l, const double* sigma_t,
                    const double* theta, void* stream);
 
 /* y = alpha M u + beta K u (Algorithm 1, cell loop with sum factorization).
- * precision SEM_PREC_FP64: u, y are device double[ndofs].
+ * precision SEM_PREC_FP64 or SEM_PREC_DF64: u, y are device double[ndofs].
  * precision SEM_PREC_FP32 / SEM_PREC_FP32_BF16: u, y are device float[ndofs].
  * y is overwritten; u and y must not overlap. */
 int sem_apply(sem_ctx* ctx, double alpha, double beta, const void* u, void* y, int precision,
               void* stream);
+
+/* Arithmetic of the operator inside sem_cg_solve / sem_step (the outer CG of
+ * the multigrid PCG included): SEM_PREC_FP64 (default, FP64 instructions) or
+ * SEM_PREC_DF64 (double-float on the FP32 pipe; vectors, residuals and inner
+ * products stay FP64). */
+int sem_set_operator_precision(sem_ctx* ctx, int precision);
 
 /* Diagonal of alpha M + beta K: device double d[ndofs]. */
 int sem_diagonal(sem_ctx* ctx, double alpha, double beta, double* d, void* stream);

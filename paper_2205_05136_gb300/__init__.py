@@ -17,7 +17,8 @@ import torch
 
 from . import capi
 from .autograd import traces  # noqa: F401
-from .capi import (SEM_PC_GMG, SEM_PC_JACOBI, SEM_PC_NONE, SEM_PREC_FP32, SEM_PREC_FP32_BF16,  # noqa: F401
+from .capi import (SEM_PC_GMG, SEM_PC_JACOBI, SEM_PC_NONE, SEM_PREC_DF64, SEM_PREC_FP32,  # noqa: F401
+                   SEM_PREC_FP32_BF16,
                    SEM_PREC_FP64, SEM_QUAD_LG, SEM_QUAD_LGL, SEM_REGION_BOX, SEM_REGION_SPHERE,
                    SemError)
 
@@ -71,7 +72,7 @@ class Slab:
         capi.sem_set_tissue(self._ctx, f(sigma_l), f(sigma_t), f(theta))
 
     def apply(self, u: torch.Tensor, alpha=1.0, beta=1.0, precision=SEM_PREC_FP64, out=None):
-        dt = torch.float64 if precision == SEM_PREC_FP64 else torch.float32
+        dt = torch.float64 if precision in (SEM_PREC_FP64, SEM_PREC_DF64) else torch.float32
         y = out if out is not None else self._vec(dt)
         capi.sem_apply(self._ctx, alpha, beta, u, y, precision)
         return y

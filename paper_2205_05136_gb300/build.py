@@ -24,6 +24,7 @@ SOURCES = [
     "sem_setup.cu",
     "sem_apply_fp64.cu",
     "sem_apply_fp32.cu",
+    "sem_apply_df64.cu",
     "sem_solver.cu",
     "sem_api.cu",
     "sem_noalloc.cu",

@@ -27,6 +27,7 @@ SEM_QUAD_LGL = 1
 SEM_PREC_FP64 = 0
 SEM_PREC_FP32 = 1
 SEM_PREC_FP32_BF16 = 2
+SEM_PREC_DF64 = 3
 SEM_PC_NONE = 0
 SEM_PC_JACOBI = 1
 SEM_PC_GMG = 2
@@ -46,7 +47,7 @@ EXPORTS = [
     "sem_cg_solve", "sem_set_ionic", "sem_set_stimulus", "sem_state_create", "sem_state_destroy",
     "sem_state_set", "sem_state_get", "sem_state_restore", "sem_step", "sem_step_host",
     "sem_set_timing", "sem_apply_dot_static", "sem_set_gmg", "sem_vcycle", "sem_gmg_info",
-    "sem_forward_record", "sem_adjoint_grad",
+    "sem_forward_record", "sem_adjoint_grad", "sem_set_operator_precision",
 ]
 
 
@@ -64,7 +65,8 @@ class sem_ionic_params(ctypes.Structure):
 class sem_stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int64), ("cg_iters", ctypes.c_int64),
                 ("last_residual", ctypes.c_double), ("apply_ms", ctypes.c_double),
-                ("n_apply", ctypes.c_int64), ("kernel_launches", ctypes.c_int64)]
+                ("n_apply", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("smoother_apply_ms", ctypes.c_double), ("n_smoother_apply", ctypes.c_int64)]
 
 
 _LIB = None
@@ -107,6 +109,7 @@ def lib():
             "sem_set_timing": (_I, [_P, _I]),
             "sem_apply_dot_static": (_I, [_P, _D, _D, _P, _P, _P, _P]),
             "sem_set_gmg": (_I, [_P, _I, _I, _I, _I]),
+            "sem_set_operator_precision": (_I, [_P, _I]),
             "sem_forward_record": (_I, [_P, _P, _D, _I, _I, _P, _I, _P, _D, _D, _I, _I,
                                         ctypes.POINTER(sem_stats), _P]),
             "sem_adjoint_grad": (_I, [_P, _P, _P, _P, _P, _D, _D, _I, _I, ctypes.POINTER(sem_stats), _P]),
@@ -194,7 +197,7 @@ def sem_set_tissue(ctx, sigma_l, sigma_t, theta, stream=None):
 
 
 def sem_apply(ctx, alpha, beta, u, y, precision=SEM_PREC_FP64, stream=None):
-    dt = torch.float64 if precision == SEM_PREC_FP64 else torch.float32
+    dt = torch.float64 if precision in (SEM_PREC_FP64, SEM_PREC_DF64) else torch.float32
     n = sem_num_dofs(ctx)
     return _check(lib().sem_apply(ctx, float(alpha), float(beta), _dev(u, dt, n, "u"),
                                   _dev(y, dt, n, "y"), int(precision), _stream(stream)), ctx)
@@ -348,3 +351,7 @@ def sem_adjoint_grad(ctx, trace_bar, g_sigma_l, g_sigma_t, g_theta, rtol, atol, 
                                   _dev(g_theta, torch.float64, ne, "g_theta"), float(rtol), float(atol),
                                   int(maxit), int(precond), ctypes.byref(stats), _stream(stream)), ctx)
     return stats
+
+
+def sem_set_operator_precision(ctx, precision):
+    return _check(lib().sem_set_operator_precision(ctx, int(precision)), ctx)

@@ -256,6 +256,8 @@ int sem_apply(sem_ctx* ctx, double alpha, double beta, const void* u, void* y, i
   switch (precision) {
     case SEM_PREC_FP64:
       return apply_fp64(ctx, alpha, beta, static_cast<const double*>(u), static_cast<double*>(y), s);
+    case SEM_PREC_DF64:
+      return apply_df64(ctx, alpha, beta, static_cast<const double*>(u), static_cast<double*>(y), s);
     case SEM_PREC_FP32:
       return apply_fp32(ctx, alpha, beta, static_cast<const float*>(u), static_cast<float*>(y), false, s);
     case SEM_PREC_FP32_BF16:
@@ -263,6 +265,17 @@ int sem_apply(sem_ctx* ctx, double alpha, double beta, const void* u, void* y, i
     default:
       return fail(ctx, SEM_ERR_ARG, "unknown precision");
   }
+}
+
+int sem_set_operator_precision(sem_ctx* ctx, int precision) {
+  CK_CTX(ctx);
+  if (precision != SEM_PREC_FP64 && precision != SEM_PREC_DF64)
+    return fail(ctx, SEM_ERR_ARG, "operator precision must be SEM_PREC_FP64 or SEM_PREC_DF64");
+  DeviceGuard guard(ctx->device);
+  cudaDeviceSynchronize();
+  ctx->op_precision = precision;
+  gmg_free(ctx);  // captured graphs embed the operator kernel
+  return SEM_OK;
 }
 
 int sem_diagonal(sem_ctx* ctx, double alpha, double beta, double* d, void* stream) {
@@ -413,10 +426,14 @@ int sem_step(sem_ctx* ctx, sem_state* st, double dt, int nsteps, double rtol, do
   std::memset(sp, 0, sizeof(*sp));
   const double ms0 = ctx->timing.ms;
   const int64_t c0 = ctx->timing.count;
+  const double sm0 = ctx->timing.smoother_ms;
+  const int64_t sc0 = ctx->timing.smoother_count;
   const int64_t l0 = ctx->launches;
   const int rc = time_steps(ctx, st, dt, nsteps, rtol, atol, maxit, precond, sp, as_stream(stream));
   sp->apply_ms = ctx->timing.ms - ms0;
   sp->n_apply = ctx->timing.count - c0;
+  sp->smoother_apply_ms = ctx->timing.smoother_ms - sm0;
+  sp->n_smoother_apply = ctx->timing.smoother_count - sc0;
   sp->kernel_launches = ctx->launches - l0;
   return rc;
 }

@@ -42,6 +42,16 @@ __device__ __forceinline__ float ldmetric(const float* p) { return __ldg(p); }
 __device__ __forceinline__ float ldmetric(const __nv_bfloat16* p) {
   return __bfloat162float(__ldg(p));
 }
+__device__ __forceinline__ df ldmetric(const df_pair* p) {
+  const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+  return df(v.x, v.y);
+}
+
+// Scatter-add of one element result; exact-match overloads so that no value is
+// converted between precisions.
+__device__ __forceinline__ void scatter_add(double* p, double v) { atomicAdd(p, v); }
+__device__ __forceinline__ void scatter_add(float* p, float v) { atomicAdd(p, v); }
+__device__ __forceinline__ void scatter_add(double* p, df v) { atomicAdd(p, (double)v); }
 
 // Base offset and stride of line l of an n^3 tile along direction DIR
 // (0: x-line (j,k), l = j + n k; 1: y-line (i,k), l = i + n k; 2: z-line (i,j), l = i + n j).
@@ -185,7 +195,7 @@ __global__ void __launch_bounds__(kApplyThreads)
   // gather u_e = P_e u
   for (int idx = threadIdx.x; idx < E * N3; idx += blockDim.x) {
     const int s = idx / N3, loc = idx - s * N3, e = e0 + s;
-    sA[idx] = (e < a.nelem) ? a.u[__ldg(a.map + (size_t)e * N3 + loc)] : T(0);
+    sA[idx] = (e < a.nelem) ? T(a.u[__ldg(a.map + (size_t)e * N3 + loc)]) : T(0);
   }
   __syncthreads();
 
@@ -267,7 +277,7 @@ __global__ void __launch_bounds__(kApplyThreads)
       const int g = __ldg(a.map + (size_t)e * N3 + loc);
       T v = sA[idx];
       if (a.scale_out) v *= a.out_scale;
-      atomicAdd(a.y + g, v);
+      scatter_add(a.y + g, v);
       if (DOT) dot = fma((double)a.u[g], (double)v, dot);
     }
   }

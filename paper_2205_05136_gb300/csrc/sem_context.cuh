@@ -29,8 +29,10 @@ struct Tape;  // checkpoints of a recorded forward run (sem_adjoint.cu)
 struct Timing {
   bool enabled = false;
   cudaEvent_t start = nullptr, stop = nullptr;
-  double ms = 0.0;
+  double ms = 0.0;            // outer operator applies
   int64_t count = 0;
+  double smoother_ms = 0.0;   // fine-level multigrid smoother applies (one per V-cycle timed)
+  int64_t smoother_count = 0;
 };
 
 }  // namespace sem
@@ -53,6 +55,7 @@ struct sem_ctx {
   sem::Tape* tape = nullptr;        // recorded forward run for the adjoint
   int gmg_degree = 3, gmg_coarse_degree = 10, gmg_min_coarse_dofs = 2000;
   int gmg_precision = SEM_PREC_FP32;
+  int op_precision = SEM_PREC_FP64;  // operator of the CG iterations: FP64 or DF64
   sem_state* host_state = nullptr;  // device copy of the state for sem_step_host
   std::string err;
 };
@@ -79,6 +82,12 @@ int time_steps(sem_ctx* ctx, sem_state* st, double dt, int nsteps, double rtol, 
 int fail(sem_ctx* ctx, int code, const std::string& msg);
 int apply_fp32(sem_ctx* ctx, double alpha, double beta, const float* u, float* y, bool bf16,
                cudaStream_t s);
+int apply_df64(sem_ctx* ctx, double alpha, double beta, const double* u, double* y,
+               cudaStream_t s);
+// The FP64-vector operator the solvers use (FP64 or df64 arithmetic per ctx->op_precision);
+// prepare_operator makes its metric copy and must run before any stream capture.
+cudaError_t prepare_operator(sem_ctx* ctx, cudaStream_t s);
+cudaError_t launch_operator(sem_ctx* ctx, const ApplyArgs64& a, cudaStream_t s);
 
 // Geometric multigrid (sem_gmg.cu).
 void gmg_free(sem_ctx* ctx);

@@ -69,7 +69,8 @@ struct Gmg {
   Graphs graphs[16];
   int next_graph = 0;
   cudaStream_t capture = nullptr;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;           // recorded around the FP64 apply
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;           // recorded around the outer operator apply
+  cudaEvent_t ev2 = nullptr, ev3 = nullptr;           // around the fine-level smoother apply
   double *lr = nullptr, *lz = nullptr, *lp = nullptr, *lAp = nullptr;  // Lanczos
   double* dots = nullptr;                              // device scalars
   double* partials = nullptr;
@@ -569,23 +570,26 @@ int chebyshev(sem_ctx* ctx, Gmg& g, int l, int degree, bool zero_start, const in
 }
 
 template <typename T>
-int vcycle_level(sem_ctx* ctx, Gmg& g, int l, const int* done, cudaStream_t s) {
+int vcycle_level(sem_ctx* ctx, Gmg& g, int l, const int* done, cudaStream_t s, bool record) {
   const int last = (int)g.lv.size() - 1;
   int rc;
   if (l == last) return chebyshev<T>(ctx, g, l, g.coarse_degree, true, done, s);
   if ((rc = chebyshev<T>(ctx, g, l, g.degree, true, done, s)) != SEM_OK) return rc;
   GmgLevel& V = g.lv[l];
   // t = A x (t is zero after the smoother), then b_{l+1} = R (b - t)
+  // the fine-level residual apply is bracketed by event nodes when `record`
+  if (record && l == 0) GMG_CK(cudaEventRecordWithFlags(g.ev2, s, cudaEventRecordExternal));
   if ((rc = level_apply(ctx, *V.L, g.precision, g.alpha, V.x, V.t, done, s)) != SEM_OK) return rc;
+  if (record && l == 0) GMG_CK(cudaEventRecordWithFlags(g.ev3, s, cudaEventRecordExternal));
   if ((rc = restrict_to<T>(ctx, g, l, done, s)) != SEM_OK) return rc;
-  if ((rc = vcycle_level<T>(ctx, g, l + 1, done, s)) != SEM_OK) return rc;
+  if ((rc = vcycle_level<T>(ctx, g, l + 1, done, s, false)) != SEM_OK) return rc;
   if ((rc = prolong_from<T>(ctx, g, l, done, s)) != SEM_OK) return rc;  // also clears t
   return chebyshev<T>(ctx, g, l, g.degree, false, done, s);
 }
 
-int vcycle(sem_ctx* ctx, Gmg& g, const int* done, cudaStream_t s) {
-  if (g.precision == SEM_PREC_FP64) return vcycle_level<double>(ctx, g, 0, done, s);
-  return vcycle_level<float>(ctx, g, 0, done, s);
+int vcycle(sem_ctx* ctx, Gmg& g, const int* done, cudaStream_t s, bool record = false) {
+  if (g.precision == SEM_PREC_FP64) return vcycle_level<double>(ctx, g, 0, done, s, record);
+  return vcycle_level<float>(ctx, g, 0, done, s, record);
 }
 
 // 10 Jacobi-PCG steps on level V from the fixed start vector; largest Lanczos eigenvalue.
@@ -679,6 +683,8 @@ void free_gmg_struct(Gmg* g) {
   if (g->capture) cudaStreamDestroy(g->capture);
   if (g->ev0) cudaEventDestroy(g->ev0);
   if (g->ev1) cudaEventDestroy(g->ev1);
+  if (g->ev2) cudaEventDestroy(g->ev2);
+  if (g->ev3) cudaEventDestroy(g->ev3);
   cudaFree(g->lr); cudaFree(g->lz); cudaFree(g->lp); cudaFree(g->lAp);
   cudaFree(g->dots); cudaFree(g->partials); cudaFree(g->tickets);
   delete g;
@@ -773,6 +779,8 @@ int build(sem_ctx* ctx, cudaStream_t s) {
   GMG_CK(cudaStreamCreateWithFlags(&g->capture, cudaStreamNonBlocking));
   GMG_CK(cudaEventCreate(&g->ev0));
   GMG_CK(cudaEventCreate(&g->ev1));
+  GMG_CK(cudaEventCreate(&g->ev2));
+  GMG_CK(cudaEventCreate(&g->ev3));
   double** lv4[] = {&g->lr, &g->lz, &g->lp, &g->lAp};
   for (double** v : lv4) GMG_CK(cudaMalloc(v, sizeof(double) * nmax));
   GMG_CK(cudaMalloc(&g->dots, sizeof(double) * 8));
@@ -815,7 +823,7 @@ int pcg_init_seq(sem_ctx* ctx, Gmg& g, double alpha, const double* b, const doub
     ApplyArgs64 a{};
     a.map = L.map; a.metric = L.metric; a.u = x; a.y = w.Ap; a.nelem = L.nelem;
     a.mass_coef = alpha; a.out_scale = 1.0; a.scale_out = 0;
-    GMG_CK(launch_apply_fp64(L, a, false, s));
+    GMG_CK(launch_operator(ctx, a, s));
   }
   k_fpcg_init<T><<<gr, kThreads, 0, s>>>(n, b, w.Ap, w.r, b0, w.cg, g.partials, stride, g.tickets,
                                          rtol, atol);
@@ -843,12 +851,12 @@ int pcg_iter_seq(sem_ctx* ctx, Gmg& g, double alpha, double* x, cudaStream_t s) 
   ap.dot_partials = w.apply_partials; ap.dot_ticket = w.tickets + 1; ap.cg = w.cg;
   // external records become event nodes of the captured graph (timing of the FP64 apply)
   GMG_CK(cudaEventRecordWithFlags(g.ev0, s, cudaEventRecordExternal));
-  GMG_CK(launch_apply_fp64(L, ap, false, s));
+  GMG_CK(launch_operator(ctx, ap, s));
   GMG_CK(cudaEventRecordWithFlags(g.ev1, s, cudaEventRecordExternal));
   k_fpcg_xr<T><<<gr, kThreads, 0, s>>>(n, x, w.p, w.Ap, w.r, (T*)g.lv[0].b, w.cg, g.partials,
                                        stride, g.tickets + 2);
   GMG_CK(cudaGetLastError());
-  int rc = vcycle(ctx, g, done, s);
+  int rc = vcycle(ctx, g, done, s, true);
   if (rc != SEM_OK) return rc;
   k_fpcg_z<T><<<gr, kThreads, 0, s>>>(n, (const T*)g.lv[0].x, g.z, w.r, nullptr, 0, w.cg,
                                       g.partials, stride, g.tickets + 1);
@@ -925,6 +933,12 @@ int pcg_t(sem_ctx* ctx, Gmg& g, double alpha, const double* b, double* x, double
       } else {
         cudaGetLastError();  // timing unavailable for these event nodes: not an error
       }
+      if (!w.cg_host->done && cudaEventElapsedTime(&ms, g.ev2, g.ev3) == cudaSuccess) {
+        tm.smoother_ms += ms;
+        tm.smoother_count += 1;
+      } else {
+        cudaGetLastError();
+      }
     }
     if (w.cg_host->done) { done_h = true; break; }
     if (launched >= maxit) break;
@@ -961,6 +975,7 @@ int gmg_pcg(sem_ctx* ctx, double alpha, const double* b, double* x, double rtol,
   int rc = ensure_workspace(ctx);
   if (rc != SEM_OK) return rc;
   if ((rc = build(ctx, s)) != SEM_OK) return rc;
+  GMG_CK(prepare_operator(ctx, s));
   Gmg& g = *ctx->gmg;
   if ((rc = set_alpha(ctx, g, alpha, s)) != SEM_OK) return rc;
   if (g.precision == SEM_PREC_FP64)

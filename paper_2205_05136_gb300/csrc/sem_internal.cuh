@@ -17,8 +17,14 @@
 #include <string>
 
 #include "sem.h"
+#include "sem_df64.cuh"
 
 namespace sem {
+
+// Storage type of the vectors an operator kernel reads and writes: the df64
+// operator works on FP64 vectors.
+template <typename T> struct VecOf { using type = T; };
+template <> struct VecOf<df> { using type = double; };
 
 constexpr int kMaxP = 6;
 constexpr int kMaxN = kMaxP + 1;
@@ -78,7 +84,8 @@ struct Level {
   double* metric = nullptr;  // [nelem][7][n^3]
   float* metric32 = nullptr;
   __nv_bfloat16* metric16 = nullptr;
-  bool metric32_valid = false, metric16_valid = false;
+  df_pair* metric2 = nullptr;  // FP64 metric split into FP32 pairs (df64 operator)
+  bool metric32_valid = false, metric16_valid = false, metric2_valid = false;
   double* mdiag = nullptr;
   double* kdiag = nullptr;
   double* xyz = nullptr;
@@ -89,8 +96,8 @@ template <typename T, typename MT>
 struct ApplyArgs {
   const int* map;
   const MT* metric;
-  const T* u;
-  T* y;
+  const typename VecOf<T>::type* u;
+  typename VecOf<T>::type* y;
   int nelem;
   T mass_coef;        // coefficient of the mass term inside the element kernel
   T out_scale;        // factor applied to the element result before the scatter
@@ -111,6 +118,8 @@ cudaError_t launch_apply_fp32(const Level& L, const ApplyArgs<float, float>& a, 
                               cudaStream_t s);
 cudaError_t launch_apply_bf16(const Level& L, const ApplyArgs<float, __nv_bfloat16>& a,
                               bool mass_only, cudaStream_t s);
+cudaError_t launch_apply_df64(const Level& L, const ApplyArgs<df, df_pair>& a, bool mass_only,
+                              cudaStream_t s);
 int apply_grid_blocks(const Level& L);
 
 // Level construction (sem_setup.cu): structured numbering of an nx x ny x nz
@@ -126,6 +135,7 @@ cudaError_t setup_geometry(Level& L, const double* sigma_l, const double* sigma_
                            const double* theta, int* d_bad, cudaStream_t s);
 cudaError_t setup_diagonals(Level& L, cudaStream_t s);
 cudaError_t setup_metric_lowp(Level& L, bool bf16, cudaStream_t s);
+cudaError_t setup_metric_df(Level& L, cudaStream_t s);
 cudaError_t setup_node_coords(Level& L, cudaStream_t s);
 cudaError_t setup_region_mask(const Level& L, int region, const double* prm, double* mask,
                               cudaStream_t s);

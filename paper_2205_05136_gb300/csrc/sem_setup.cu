@@ -248,6 +248,16 @@ __global__ void k_convert<__nv_bfloat16>(int64_t n, const double* __restrict__ i
     out[i] = __float2bfloat16_rn(__double2float_rn(in[i]));
 }
 
+__global__ void k_split_pairs(int64_t n, const double* __restrict__ in, df_pair* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = in[i];
+    const float h = __double2float_rn(x);
+    out[i].h = h;
+    out[i].l = __double2float_rn(x - (double)h);
+  }
+}
+
 int setup_threads(int n3) { return n3 <= 64 ? 64 : (n3 <= 128 ? 128 : 256); }
 
 }  // namespace
@@ -300,6 +310,7 @@ void level_free(Level& L) {
   cudaFree(L.metric);
   cudaFree(L.metric32);
   cudaFree(L.metric16);
+  cudaFree(L.metric2);
   cudaFree(L.mdiag);
   cudaFree(L.kdiag);
   cudaFree(L.xyz);
@@ -314,6 +325,7 @@ cudaError_t setup_geometry(Level& L, const double* sigma_l, const double* sigma_
                                                  L.quad == SEM_QUAD_LG, L.metric, d_bad);
   L.metric32_valid = false;
   L.metric16_valid = false;
+  L.metric2_valid = false;
   return cudaGetLastError();
 }
 
@@ -348,6 +360,15 @@ cudaError_t setup_metric_lowp(Level& L, bool bf16, cudaStream_t s) {
     k_convert<float><<<blocks, threads, 0, s>>>(count, L.metric, L.metric32);
     L.metric32_valid = true;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t setup_metric_df(Level& L, cudaStream_t s) {
+  const int64_t count = (int64_t)L.nelem * kMetricComps * L.n * L.n * L.n;
+  const int threads = 256;
+  const int blocks = (int)std::min<int64_t>((count + threads - 1) / threads, 152 * 16);
+  k_split_pairs<<<blocks, threads, 0, s>>>(count, L.metric, L.metric2);
+  L.metric2_valid = true;
   return cudaGetLastError();
 }
 

@@ -288,6 +288,44 @@ int apply_fp64(sem_ctx* ctx, double alpha, double beta, const double* u, double*
   return SEM_OK;
 }
 
+cudaError_t prepare_operator(sem_ctx* ctx, cudaStream_t s) {
+  Level& L = ctx->L;
+  if (ctx->op_precision != SEM_PREC_DF64 || L.metric2_valid) return cudaSuccess;
+  cudaError_t e;
+  if (!L.metric2 &&
+      (e = cudaMalloc(&L.metric2, sizeof(df_pair) * (size_t)L.nelem * kMetricComps * L.n * L.n * L.n)) != cudaSuccess)
+    return e;
+  return setup_metric_df(L, s);
+}
+
+cudaError_t launch_operator(sem_ctx* ctx, const ApplyArgs64& a, cudaStream_t s) {
+  Level& L = ctx->L;
+  if (ctx->op_precision != SEM_PREC_DF64) return launch_apply_fp64(L, a, false, s);
+  if (!L.metric2_valid) return cudaErrorNotReady;  // prepare_operator was not called
+  ApplyArgs<df, df_pair> d{};
+  d.map = a.map; d.metric = L.metric2; d.u = a.u; d.y = a.y; d.nelem = a.nelem;
+  d.mass_coef = df(a.mass_coef); d.out_scale = df(a.out_scale); d.scale_out = a.scale_out;
+  d.done = a.done; d.dot_partials = a.dot_partials; d.dot_ticket = a.dot_ticket; d.cg = a.cg;
+  d.dot_out = a.dot_out;
+  return launch_apply_df64(L, d, false, s);
+}
+
+int apply_df64(sem_ctx* ctx, double alpha, double beta, const double* u, double* y,
+               cudaStream_t s) {
+  const Level& L = ctx->L;
+  if (beta == 0.0) return apply_fp64(ctx, alpha, beta, u, y, s);  // the mass operator is FP64 either way
+  SEM_CK(cudaMemsetAsync(y, 0, sizeof(double) * L.ndofs, s));
+  ApplyArgs64 a = base_args(ctx, alpha, beta, u, y);
+  const int saved = ctx->op_precision;
+  ctx->op_precision = SEM_PREC_DF64;
+  cudaError_t e = prepare_operator(ctx, s);
+  if (e == cudaSuccess) e = launch_operator(ctx, a, s);
+  ctx->op_precision = saved;
+  SEM_CK(e);
+  ctx->launches += 1;
+  return SEM_OK;
+}
+
 int apply_fp32(sem_ctx* ctx, double alpha, double beta, const float* u, float* y, bool bf16,
                cudaStream_t s) {
   Level& L = ctx->L;
@@ -329,6 +367,7 @@ int cg_solve(sem_ctx* ctx, double alpha, const double* b, double* x, double rtol
              cudaStream_t s) {
   int rc = ensure_workspace(ctx);
   if (rc != SEM_OK) return rc;
+  SEM_CK(prepare_operator(ctx, s));
   Level& L = ctx->L;
   Workspace& w = ctx->ws;
   const int64_t n = L.ndofs;
@@ -351,7 +390,7 @@ int cg_solve(sem_ctx* ctx, double alpha, const double* b, double* x, double rtol
   SEM_CK(cudaMemsetAsync(w.Ap, 0, sizeof(double) * n, s));
   {
     ApplyArgs64 a = base_args(ctx, alpha, 1.0, x, w.Ap);
-    SEM_CK(launch_apply_fp64(L, a, false, s));
+    SEM_CK(launch_operator(ctx, a, s));
   }
   ctx->launches += 2;
   k_cg_init<<<vg, kVecThreads, 0, s>>>(n, b, w.Ap, inv, w.r, w.z, w.p, w.cg, w.vec_partials,
@@ -381,7 +420,7 @@ int cg_solve(sem_ctx* ctx, double alpha, const double* b, double* x, double rtol
     if (this_chunk > 0) {
       for (int c = 0; c < this_chunk; ++c) {
         if (tm.enabled) SEM_CK(cudaEventRecord(evs[2 * c], s));
-        SEM_CK(launch_apply_fp64(L, ap, false, s));
+        SEM_CK(launch_operator(ctx, ap, s));
         if (tm.enabled) SEM_CK(cudaEventRecord(evs[2 * c + 1], s));
         k_cg_xr<<<vg, kVecThreads, 0, s>>>(n, x, w.p, w.Ap, w.r, inv, w.z, w.cg, w.vec_partials,
                                            w.tickets + 0);

@@ -132,3 +132,38 @@ def test_sweep_workload_sampled_rows():
         assert np.abs(y[idx] - ref).max() < 1e-12 * scale, (p, quad)
         g.close()
         torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("quad", QUADS)
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6])
+def test_df64_apply_matches_assembled_operator(p, quad):
+    """Double-float arithmetic on the FP32 pipe meets the FP64 tolerance."""
+    s = W.slab(3, 2, 2, (3.0, 2.0, 1.5), perturb=0.15, seed=21)
+    tissue = _tissue(s)
+    g, o = _pair(s, p, quad, tissue)
+    u = W.uniform_vector(o.ndofs, -1.0, 1.0, seed=2)
+    M, K = Mh.assemble_mass_stiffness(o, tissue)
+    ut = torch.tensor(u, device="cuda")
+    for alpha, beta in [(30.0, 1.0), (0.0, 1.0), (2.5, 0.7)]:
+        y = g.apply(ut, alpha, beta, precision=gb.SEM_PREC_DF64).cpu().numpy()
+        ref = alpha * (M @ u) + beta * (K @ u)
+        assert rel(y, ref) < 1e-12, (alpha, beta, rel(y, ref))
+
+
+def test_df64_sweep_workload_sampled_rows():
+    for p, quad, count in [(4, "LGL", 64), (4, "LG", 64)]:
+        s = W.sweep_slab(p)
+        tissue = (np.full(s.n_elements, 0.12), np.full(s.n_elements, 0.03), W.transmural_fiber_angles(s))
+        g = gb.Slab(s.flat_vertices(), s.nx, s.ny, s.nz, p, quad)
+        g.set_tissue(*tissue)
+        o = Mh.SlabSpace(s.flat_vertices(), s.nx, s.ny, s.nz, p, quad)
+        u = W.uniform_vector(o.ndofs, -1.0, 1.0, seed=W.SEED_U)
+        ut = torch.tensor(u, device="cuda")
+        y = g.apply(ut, 30.0, 1.0, precision=gb.SEM_PREC_DF64).cpu().numpy()
+        y64 = g.apply(ut, 30.0, 1.0).cpu().numpy()
+        idx = W.seeded_indices(o.ndofs, count, seed=7)
+        ref = Mh.sampled_rows(o, tissue, u, idx, 30.0, 1.0)
+        assert np.abs(y[idx] - ref).max() < 1e-12 * np.abs(ref).max()
+        assert rel(y, y64) < 1e-12
+        g.close()
+        torch.cuda.empty_cache()

@@ -188,3 +188,29 @@ def test_ionic_parameters_reach_the_kernel():
     u, h, _ = st.get()
     ref = ionic.single_cell_semi_implicit(-60.0, 0.8, 0.25, 0.05, prm)
     assert np.abs(u.cpu().numpy() - ref[0]).max() < 1e-10 * abs(ref[0])
+
+
+@pytest.mark.parametrize("precond", [capi.SEM_PC_JACOBI, capi.SEM_PC_GMG])
+@pytest.mark.parametrize("quad", ["LGL", "LG"])
+def test_df64_operator_in_cg_and_time_steps(quad, precond):
+    """The double-float operator inside CG (and the multigrid PCG) reaches the
+    FP64 solution, and 20 time steps match the oracle to 1e-10."""
+    s, tissue, g, o = _small(3, quad, perturb=0.1, dims=(4, 3, 2))
+    capi.sem_set_operator_precision(g.ctx, capi.SEM_PREC_DF64)
+    capi.sem_set_gmg(g.ctx, 3, 10, 50, capi.SEM_PREC_FP32)
+    alpha = 1.5 / 0.05
+    A = Mh.assemble(o, tissue, alpha, 1.0)
+    b = W.uniform_vector(o.ndofs, -1.0, 1.0, seed=3)
+    import scipy.sparse.linalg as spla
+    xref = spla.spsolve(A.tocsc(), b)
+    x = torch.zeros(o.ndofs, dtype=torch.float64, device="cuda")
+    g.cg_solve(alpha, torch.tensor(b, device="cuda"), x, rtol=1e-13, maxit=5000, precond=precond)
+    assert rel(x.cpu().numpy(), xref) < 1e-11
+    box = (0.0, 0.0, 0.0, 3.0, 3.0, 1.5)
+    g.set_ionic()
+    g.set_stimulus("box", box, 50.0, 0.0, 1.0)
+    st = g.new_state(-85.0, 1.0)
+    st.step(0.05, 20, rtol=1e-13, maxit=5000, precond=precond)
+    u, _, _ = st.get()
+    ref = _oracle_run(o, tissue, 0.05, 20, ("box", box), 50.0, 1.0)
+    assert rel(u.cpu().numpy(), ref["u"]) < 1e-10
