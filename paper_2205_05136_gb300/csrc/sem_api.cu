@@ -168,6 +168,10 @@ int sem_create(sem_ctx** out, int nx, int ny, int nz, const double* vertices, in
     return SEM_ERR_ARG;
   }
   DeviceGuard guard(device);
+  if (cudaError_t pe = prime_apply_kernels(); pe != cudaSuccess) {
+    g_create_err = std::string("kernel attribute setup failed: ") + cudaGetErrorString(pe);
+    return SEM_ERR_CUDA;
+  }
   sem_ctx* ctx = new (std::nothrow) sem_ctx();
   if (!ctx) { g_create_err = "host allocation failed"; return SEM_ERR_NOMEM; }
   ctx->device = device;

@@ -14,4 +14,10 @@ cudaError_t launch_apply_bf16(const Level& L, const ApplyArgs<float, __nv_bfloat
   return dispatch_apply<float, __nv_bfloat16>(L, a, mass_only, false, s);
 }
 
+cudaError_t prime_apply_kernels() {
+  cudaError_t e = prime_all<float, float>();
+  if (e != cudaSuccess) return e;
+  return prime_all<float, __nv_bfloat16>();
+}
+
 }  // namespace sem

@@ -179,18 +179,56 @@ __device__ __forceinline__ bool finish_reduction(double partial, double* partial
   return threadIdx.x == 0;
 }
 
+// Shared-memory bytes of one CTA: three n^3 tiles per element, plus, when
+// StageMetric is set, the CTA's metric block staged by cp.async at kernel entry
+// (16-byte aligned thanks to the padded metric layout).  Staging is off: on
+// GB300 the extra 36 KB per CTA halves the resident CTAs of the FP32 kernel and
+// measured slower (p = 4: 63 us against 58 us per launch), because the gather
+// and scatter latencies then overlap less.
+template <typename T> struct StageMetric { static constexpr bool value = false; };
+
+template <int P, typename T, typename MT>
+__host__ __device__ constexpr size_t apply_tile_bytes() {
+  return ((size_t)3 * ApplyCfg<P>::E * (P + 1) * (P + 1) * (P + 1) * sizeof(T) + 15) / 16 * 16;
+}
+template <int P, typename T, typename MT>
+__host__ __device__ constexpr size_t apply_smem_bytes() {
+  return apply_tile_bytes<P, T, MT>() +
+         (StageMetric<T>::value ? (size_t)ApplyCfg<P>::E * kMetricComps * padded_n3(P + 1) * sizeof(MT) : 0);
+}
+
+__device__ __forceinline__ float ldsmetric(const float* p) { return *p; }
+__device__ __forceinline__ float ldsmetric(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+__device__ __forceinline__ double ldsmetric(const double* p) { return *p; }
+__device__ __forceinline__ df ldsmetric(const df_pair* p) { return df(p->h, p->l); }
+
 template <int P, int QUAD, typename T, typename MT, bool DOT, bool MASS_ONLY>
 __global__ void __launch_bounds__(kApplyThreads)
     sem_apply_kernel(const ApplyArgs<T, MT> a, const __grid_constant__ KTab<P + 1, T> tab) {
-  constexpr int N = P + 1, N2 = N * N, N3 = N2 * N;
+  constexpr int N = P + 1, N2 = N * N, N3 = N2 * N, N3P = padded_n3(N);
   constexpr int E = ApplyCfg<P>::E;
-  __shared__ T sA[E * N3];
-  __shared__ T sB[E * N3];
-  __shared__ T sC[E * N3];
+  constexpr bool STAGE = StageMetric<T>::value && !MASS_ONLY;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sA = reinterpret_cast<T*>(smem_raw);
+  T* sB = sA + E * N3;
+  T* sC = sB + E * N3;
+  MT* sM = reinterpret_cast<MT*>(smem_raw + apply_tile_bytes<P, T, MT>());
   __shared__ double red[32];
 
   if (a.done != nullptr && *a.done) return;
   const int e0 = blockIdx.x * E;
+
+  if (STAGE) {  // the CTA's metric block: contiguous, 16-byte aligned, a multiple of 16 bytes
+    const int ne = min(E, a.nelem - e0);
+    const size_t bytes = (size_t)ne * kMetricComps * N3P * sizeof(MT);
+    const char* src = reinterpret_cast<const char*>(a.metric + (size_t)e0 * kMetricComps * N3P);
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(sM);
+    for (size_t off = (size_t)threadIdx.x * 16; off < bytes; off += (size_t)blockDim.x * 16)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst + (unsigned)off),
+                   "l"(src + off)
+                   : "memory");
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  }
 
   // gather u_e = P_e u
   for (int idx = threadIdx.x; idx < E * N3; idx += blockDim.x) {
@@ -212,7 +250,7 @@ __global__ void __launch_bounds__(kApplyThreads)
     for (int idx = threadIdx.x; idx < E * N3; idx += blockDim.x) {
       const int s = idx / N3, loc = idx - s * N3, e = e0 + s;
       if (e < a.nelem) {
-        const T W = ldmetric(a.metric + ((size_t)e * kMetricComps + 6) * N3 + loc);
+        const T W = ldmetric(a.metric + ((size_t)e * kMetricComps + 6) * N3P + loc);
         sA[idx] = (a.mass_coef * W) * sA[idx];
       }
     }
@@ -221,6 +259,7 @@ __global__ void __launch_bounds__(kApplyThreads)
     // reference gradient along x and y (into sB, sC)
     sweep<N, E, 0>(tab.D, sA, sB);
     sweep<N, E, 1>(tab.D, sA, sC);
+    if (STAGE) asm volatile("cp.async.wait_all;\n" ::: "memory");
     __syncthreads();
     // z-gradient, quadrature-point stage and transposed z-sweep on the columns
     for (int w = threadIdx.x; w < E * N2; w += blockDim.x) {
@@ -233,17 +272,29 @@ __global__ void __launch_bounds__(kApplyThreads)
 #pragma unroll
       for (int k = 0; k < N; ++k) uz[k] = pa[k * N2];
       mat_line<N>(tab.D, uz, g3);
-      const MT* mp = a.metric + (size_t)e * kMetricComps * N3 + c;
+      const MT* mp = STAGE ? sM + (size_t)s * kMetricComps * N3P + c
+                           : a.metric + (size_t)e * kMetricComps * N3P + c;
 #pragma unroll
       for (int k = 0; k < N; ++k) {
         const T g1 = pb[k * N2], g2 = pc[k * N2];
-        const T G00 = ldmetric(mp + 0 * N3 + k * N2);
-        const T G01 = ldmetric(mp + 1 * N3 + k * N2);
-        const T G02 = ldmetric(mp + 2 * N3 + k * N2);
-        const T G11 = ldmetric(mp + 3 * N3 + k * N2);
-        const T G12 = ldmetric(mp + 4 * N3 + k * N2);
-        const T G22 = ldmetric(mp + 5 * N3 + k * N2);
-        const T W = ldmetric(mp + 6 * N3 + k * N2);
+        T G00, G01, G02, G11, G12, G22, W;
+        if (STAGE) {
+          G00 = ldsmetric(mp + 0 * N3P + k * N2);
+          G01 = ldsmetric(mp + 1 * N3P + k * N2);
+          G02 = ldsmetric(mp + 2 * N3P + k * N2);
+          G11 = ldsmetric(mp + 3 * N3P + k * N2);
+          G12 = ldsmetric(mp + 4 * N3P + k * N2);
+          G22 = ldsmetric(mp + 5 * N3P + k * N2);
+          W = ldsmetric(mp + 6 * N3P + k * N2);
+        } else {
+          G00 = ldmetric(mp + 0 * N3P + k * N2);
+          G01 = ldmetric(mp + 1 * N3P + k * N2);
+          G02 = ldmetric(mp + 2 * N3P + k * N2);
+          G11 = ldmetric(mp + 3 * N3P + k * N2);
+          G12 = ldmetric(mp + 4 * N3P + k * N2);
+          G22 = ldmetric(mp + 5 * N3P + k * N2);
+          W = ldmetric(mp + 6 * N3P + k * N2);
+        }
         pb[k * N2] = fma(G02, g3[k], fma(G01, g2, G00 * g1));
         pc[k * N2] = fma(G12, g3[k], fma(G11, g2, G01 * g1));
         q3[k] = fma(G22, g3[k], fma(G12, g2, G02 * g1));
@@ -309,14 +360,41 @@ cudaError_t launch_apply_t(const Level& L, const ApplyArgs<T, MT>& a, bool mass_
   const int E = ApplyCfg<P>::E;
   const int grid = (L.nelem + E - 1) / E;
   if (grid == 0) return cudaSuccess;
+  constexpr size_t tiles = apply_tile_bytes<P, T, MT>();
+  constexpr size_t full = apply_smem_bytes<P, T, MT>();
   if (mass_only) {
-    sem_apply_kernel<P, QUAD, T, MT, false, true><<<grid, kApplyThreads, 0, s>>>(a, tab);
+    sem_apply_kernel<P, QUAD, T, MT, false, true><<<grid, kApplyThreads, tiles, s>>>(a, tab);
   } else if (dot) {
-    sem_apply_kernel<P, QUAD, T, MT, true, false><<<grid, kApplyThreads, 0, s>>>(a, tab);
+    sem_apply_kernel<P, QUAD, T, MT, true, false><<<grid, kApplyThreads, full, s>>>(a, tab);
   } else {
-    sem_apply_kernel<P, QUAD, T, MT, false, false><<<grid, kApplyThreads, 0, s>>>(a, tab);
+    sem_apply_kernel<P, QUAD, T, MT, false, false><<<grid, kApplyThreads, full, s>>>(a, tab);
   }
   return cudaGetLastError();
+}
+
+// Dynamic shared-memory limits of the three variants of one instantiation.
+template <int P, int QUAD, typename T, typename MT>
+cudaError_t prime_t() {
+  constexpr int full = (int)apply_smem_bytes<P, T, MT>();
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(sem_apply_kernel<P, QUAD, T, MT, false, false>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, full)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(sem_apply_kernel<P, QUAD, T, MT, true, false>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, full)) != cudaSuccess) return e;
+  return cudaFuncSetAttribute(sem_apply_kernel<P, QUAD, T, MT, false, true>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)apply_tile_bytes<P, T, MT>());
+}
+
+template <typename T, typename MT>
+cudaError_t prime_all() {
+  cudaError_t e;
+#define SEM_PRIME(PP)                                                                   \
+  if ((e = prime_t<PP, SEM_QUAD_LG, T, MT>()) != cudaSuccess) return e;                \
+  if ((e = prime_t<PP, SEM_QUAD_LGL, T, MT>()) != cudaSuccess) return e;
+  SEM_PRIME(1) SEM_PRIME(2) SEM_PRIME(3) SEM_PRIME(4) SEM_PRIME(5) SEM_PRIME(6)
+#undef SEM_PRIME
+  return cudaSuccess;
 }
 
 template <typename T, typename MT>

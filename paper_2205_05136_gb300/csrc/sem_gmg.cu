@@ -762,11 +762,11 @@ int build(sem_ctx* ctx, cudaStream_t s) {
     Level& L = *V.L;
     nmax = std::max(nmax, L.ndofs);
     if (g->precision == SEM_PREC_FP32 && !L.metric32_valid) {
-      if (!L.metric32) GMG_CK(cudaMalloc(&L.metric32, sizeof(float) * (size_t)L.nelem * kMetricComps * L.n * L.n * L.n));
+      if (!L.metric32) GMG_CK(cudaMalloc(&L.metric32, sizeof(float) * metric_count(L)));
       GMG_CK(setup_metric_lowp(L, false, s));
     }
     if (g->precision == SEM_PREC_FP32_BF16 && !L.metric16_valid) {
-      if (!L.metric16) GMG_CK(cudaMalloc(&L.metric16, sizeof(__nv_bfloat16) * (size_t)L.nelem * kMetricComps * L.n * L.n * L.n));
+      if (!L.metric16) GMG_CK(cudaMalloc(&L.metric16, sizeof(__nv_bfloat16) * metric_count(L)));
       GMG_CK(setup_metric_lowp(L, true, s));
     }
     void** vecs[] = {&V.b, &V.x, &V.t, &V.d, &V.invd};

@@ -2,7 +2,8 @@
 //
 // Layout of the data in HBM (one context = one slab, one device):
 //   map      int32  [nelem][n^3]   local node a = i + n j + n^2 k -> global node
-//   metric   double [nelem][7][n^3] per quadrature point: G00 G01 G02 G11 G12 G22 W,
+//   metric   double [nelem][7][n3p] per quadrature point: G00 G01 G02 G11 G12 G22 W,
+//            n3p = n^3 rounded up to a multiple of 8 (16-byte aligned blocks),
 //            G = w |det J| J^{-1} D J^{-T}, W = w |det J|  (element-blocked SoA)
 //   metric32 float / bf16 copies of the same array for the mixed-precision applies
 //   mdiag    double [ndofs]  diagonal of the assembled mass matrix
@@ -29,6 +30,11 @@ template <> struct VecOf<df> { using type = double; };
 constexpr int kMaxP = 6;
 constexpr int kMaxN = kMaxP + 1;
 constexpr int kMetricComps = 7;
+
+// Quadrature points per element rounded up to a multiple of 8: every element's
+// metric block and each of its 7 components then start on a 16-byte boundary
+// in every storage precision (bf16, float, double, float pairs).
+__host__ __device__ constexpr int padded_n3(int n) { return ((n * n * n + 7) / 8) * 8; }
 
 // 1-D tables of one degree p and one quadrature kind (host side, double).
 struct Tables1D {
@@ -91,6 +97,11 @@ struct Level {
   double* xyz = nullptr;
 };
 
+// Number of metric values of a level (7 components x padded points per element).
+inline size_t metric_count(const Level& L) {
+  return (size_t)L.nelem * kMetricComps * padded_n3(L.n);
+}
+
 // Arguments of the element kernel y += A_e u_e (scatter-add into y).
 template <typename T, typename MT>
 struct ApplyArgs {
@@ -121,6 +132,9 @@ cudaError_t launch_apply_bf16(const Level& L, const ApplyArgs<float, __nv_bfloat
 cudaError_t launch_apply_df64(const Level& L, const ApplyArgs<df, df_pair>& a, bool mass_only,
                               cudaStream_t s);
 int apply_grid_blocks(const Level& L);
+// Raises the dynamic shared-memory limit of the kernels that stage the metric in
+// shared memory; call once per device before any stream capture.
+cudaError_t prime_apply_kernels();
 
 // Level construction (sem_setup.cu): structured numbering of an nx x ny x nz
 // slab with host vertices, device allocation of map, element vertices, metric,

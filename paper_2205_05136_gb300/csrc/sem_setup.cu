@@ -148,14 +148,15 @@ __global__ void k_metric(int nelem, const double* __restrict__ evert,
     for (int r = 0; r < 3; ++r)
       for (int c = 0; c < 3; ++c)
         G[r][c] = W * (T[r][0] * inv[c][0] + T[r][1] * inv[c][1] + T[r][2] * inv[c][2]);
-    double* out = metric + (size_t)e * kMetricComps * n3 + a;
-    out[0 * n3] = G[0][0];
-    out[1 * n3] = 0.5 * (G[0][1] + G[1][0]);
-    out[2 * n3] = 0.5 * (G[0][2] + G[2][0]);
-    out[3 * n3] = G[1][1];
-    out[4 * n3] = 0.5 * (G[1][2] + G[2][1]);
-    out[5 * n3] = G[2][2];
-    out[6 * n3] = W;
+    const int n3p = padded_n3(n);
+    double* out = metric + (size_t)e * kMetricComps * n3p + a;
+    out[0 * n3p] = G[0][0];
+    out[1 * n3p] = 0.5 * (G[0][1] + G[1][0]);
+    out[2 * n3p] = 0.5 * (G[0][2] + G[2][0]);
+    out[3 * n3p] = G[1][1];
+    out[4 * n3p] = 0.5 * (G[1][2] + G[2][1]);
+    out[5 * n3p] = G[2][2];
+    out[6 * n3p] = W;
   }
 }
 
@@ -189,7 +190,8 @@ __global__ void k_diagonals(int nelem, const int* __restrict__ map,
   const int e = blockIdx.x;
   if (e >= nelem) return;
   const int n = tab.n, n2 = n * n, n3 = n2 * n;
-  const double* me = metric + (size_t)e * kMetricComps * n3;
+  const int n3p = padded_n3(n);
+  const double* me = metric + (size_t)e * kMetricComps * n3p;
   for (int a = threadIdx.x; a < n3; a += blockDim.x) {
     const int i = a % n, j = (a / n) % n, k = a / n2;
     double Msum = 0.0, Ksum = 0.0;
@@ -200,9 +202,9 @@ __global__ void k_diagonals(int nelem, const int* __restrict__ map,
           const double b0 = tab.Bq[qx][i], b1 = tab.Bq[qy][j], b2 = tab.Bq[qz][k];
           const double d0 = tab.Dq[qx][i], d1 = tab.Dq[qy][j], d2 = tab.Dq[qz][k];
           const double gx = d0 * b1 * b2, gy = b0 * d1 * b2, gz = b0 * b1 * d2, ph = b0 * b1 * b2;
-          const double G00 = me[0 * n3 + q], G01 = me[1 * n3 + q], G02 = me[2 * n3 + q];
-          const double G11 = me[3 * n3 + q], G12 = me[4 * n3 + q], G22 = me[5 * n3 + q];
-          const double W = me[6 * n3 + q];
+          const double G00 = me[0 * n3p + q], G01 = me[1 * n3p + q], G02 = me[2 * n3p + q];
+          const double G11 = me[3 * n3p + q], G12 = me[4 * n3p + q], G22 = me[5 * n3p + q];
+          const double W = me[6 * n3p + q];
           Ksum += G00 * gx * gx + G11 * gy * gy + G22 * gz * gz +
                   2.0 * (G01 * gx * gy + G02 * gx * gz + G12 * gy * gz);
           Msum += W * ph * ph;
@@ -290,11 +292,12 @@ cudaError_t level_create(Level& L, int nx, int ny, int nz, const double* vertice
               for (int d = 0; d < 3; ++d) ev[e * 24 + (a + 2 * b + 4 * c) * 3 + d] = vertices[v * 3 + d];
             }
       }
-  const size_t nm = (size_t)L.nelem * kMetricComps * n3;
+  const size_t nm = metric_count(L);
   cudaError_t e;
   if ((e = cudaMalloc(&L.map, sizeof(int) * map.size())) != cudaSuccess) return e;
   if ((e = cudaMalloc(&L.evert, sizeof(double) * ev.size())) != cudaSuccess) return e;
   if ((e = cudaMalloc(&L.metric, sizeof(double) * nm)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(L.metric, 0, sizeof(double) * nm, s)) != cudaSuccess) return e;  // padding
   if ((e = cudaMalloc(&L.mdiag, sizeof(double) * L.ndofs)) != cudaSuccess) return e;
   if ((e = cudaMalloc(&L.kdiag, sizeof(double) * L.ndofs)) != cudaSuccess) return e;
   if (coords && (e = cudaMalloc(&L.xyz, sizeof(double) * 3 * L.ndofs)) != cudaSuccess) return e;
@@ -350,7 +353,7 @@ cudaError_t setup_diagonals(Level& L, cudaStream_t s) {
 }
 
 cudaError_t setup_metric_lowp(Level& L, bool bf16, cudaStream_t s) {
-  const int64_t count = (int64_t)L.nelem * kMetricComps * L.n * L.n * L.n;
+  const int64_t count = (int64_t)metric_count(L);
   const int threads = 256;
   const int blocks = (int)std::min<int64_t>((count + threads - 1) / threads, 152 * 16);
   if (bf16) {
@@ -364,7 +367,7 @@ cudaError_t setup_metric_lowp(Level& L, bool bf16, cudaStream_t s) {
 }
 
 cudaError_t setup_metric_df(Level& L, cudaStream_t s) {
-  const int64_t count = (int64_t)L.nelem * kMetricComps * L.n * L.n * L.n;
+  const int64_t count = (int64_t)metric_count(L);
   const int threads = 256;
   const int blocks = (int)std::min<int64_t>((count + threads - 1) / threads, 152 * 16);
   k_split_pairs<<<blocks, threads, 0, s>>>(count, L.metric, L.metric2);

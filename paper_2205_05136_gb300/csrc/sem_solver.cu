@@ -293,7 +293,7 @@ cudaError_t prepare_operator(sem_ctx* ctx, cudaStream_t s) {
   if (ctx->op_precision != SEM_PREC_DF64 || L.metric2_valid) return cudaSuccess;
   cudaError_t e;
   if (!L.metric2 &&
-      (e = cudaMalloc(&L.metric2, sizeof(df_pair) * (size_t)L.nelem * kMetricComps * L.n * L.n * L.n)) != cudaSuccess)
+      (e = cudaMalloc(&L.metric2, sizeof(df_pair) * metric_count(L))) != cudaSuccess)
     return e;
   return setup_metric_df(L, s);
 }
@@ -331,13 +331,12 @@ int apply_fp32(sem_ctx* ctx, double alpha, double beta, const float* u, float* y
   Level& L = ctx->L;
   if (bf16 && !L.metric16_valid) {
     if (!L.metric16)
-      SEM_CK(cudaMalloc(&L.metric16, sizeof(__nv_bfloat16) * (size_t)L.nelem * kMetricComps *
-                                         L.n * L.n * L.n));
+      SEM_CK(cudaMalloc(&L.metric16, sizeof(__nv_bfloat16) * metric_count(L)));
     SEM_CK(setup_metric_lowp(L, true, s));
   }
   if (!bf16 && !L.metric32_valid) {
     if (!L.metric32)
-      SEM_CK(cudaMalloc(&L.metric32, sizeof(float) * (size_t)L.nelem * kMetricComps * L.n * L.n * L.n));
+      SEM_CK(cudaMalloc(&L.metric32, sizeof(float) * metric_count(L)));
     SEM_CK(setup_metric_lowp(L, false, s));
   }
   if (beta == 0.0 && L.quad == SEM_QUAD_LGL) {
