@@ -723,11 +723,12 @@ def main():
                     help="arithmetic of the outer CG operator in the mixed path")
     ap.add_argument("--arms", default="both", choices=["both", "mixed", "fp64"],
                     help="time the mixed-precision multigrid path, the plain FP64 path, or both")
-    ap.add_argument("--mg-degree", type=int, default=3)
-    # on the 2 M DOF slab at dt = 0.05 ms the h-levels below the p = 1 level do not lower
-    # the iteration count (6 per step either way), so the benchmark stops at p = 1
-    ap.add_argument("--mg-coarse-degree", type=int, default=8)
-    ap.add_argument("--mg-min-coarse-dofs", type=int, default=40000)
+    ap.add_argument("--mg-degree", type=int, default=6)
+    # tuned on the 2 M DOF slab at dt = 0.05 ms (mass-dominated operator): a degree-6
+    # Chebyshev smoother on the p = 4 level with the p = 2 level as coarsest level
+    # (Chebyshev 2) gives 3 PCG iterations per step and the shortest step time
+    ap.add_argument("--mg-coarse-degree", type=int, default=2)
+    ap.add_argument("--mg-min-coarse-dofs", type=int, default=300000)
     ap.add_argument("--workload", default="timestep", choices=["timestep", "gmg8m", "mixed30m", "adjoint"],
                     help="extra measurements of the multigrid, mixed-precision and adjoint workloads")
     ap.add_argument("--sweep", action="store_true")
