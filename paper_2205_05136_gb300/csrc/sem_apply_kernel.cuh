@@ -93,11 +93,12 @@ __device__ __forceinline__ void matT_line(const T (&M)[N][N], const T (&in)[N], 
   }
 }
 
-// dst = M along DIR of src, for every line of the E element tiles.
+// dst = M along DIR of src, for every line of the E element tiles (thread tid
+// of a group of nth threads).
 template <int N, int E, int DIR, typename T>
-__device__ __forceinline__ void sweep(const T (&M)[N][N], const T* src, T* dst) {
+__device__ __forceinline__ void sweep(const T (&M)[N][N], const T* src, T* dst, int tid, int nth) {
   constexpr int N2 = N * N, N3 = N2 * N;
-  for (int w = threadIdx.x; w < E * N2; w += blockDim.x) {
+  for (int w = tid; w < E * N2; w += nth) {
     const int s = w / N2, l = w - s * N2;
     int base, stride;
     line_geom<N, DIR>(l, base, stride);
@@ -114,9 +115,9 @@ __device__ __forceinline__ void sweep(const T (&M)[N][N], const T* src, T* dst) 
 
 // dst = M^T along DIR of src (ACC: dst += M^T src).  src may equal dst.
 template <int N, int E, int DIR, bool ACC, typename T>
-__device__ __forceinline__ void sweepT(const T (&M)[N][N], const T* src, T* dst) {
+__device__ __forceinline__ void sweepT(const T (&M)[N][N], const T* src, T* dst, int tid, int nth) {
   constexpr int N2 = N * N, N3 = N2 * N;
-  for (int w = threadIdx.x; w < E * N2; w += blockDim.x) {
+  for (int w = tid; w < E * N2; w += nth) {
     const int s = w / N2, l = w - s * N2;
     int base, stride;
     line_geom<N, DIR>(l, base, stride);
@@ -191,6 +192,8 @@ template <int P, typename T, typename MT>
 __host__ __device__ constexpr size_t apply_tile_bytes() {
   return ((size_t)3 * ApplyCfg<P>::E * (P + 1) * (P + 1) * (P + 1) * sizeof(T) + 15) / 16 * 16;
 }
+template <int P, typename T>
+__host__ __device__ constexpr size_t apply_warp_tile_bytes();
 template <int P, typename T, typename MT>
 __host__ __device__ constexpr size_t apply_smem_bytes() {
   return apply_tile_bytes<P, T, MT>() +
@@ -202,21 +205,46 @@ __device__ __forceinline__ float ldsmetric(const __nv_bfloat16* p) { return __bf
 __device__ __forceinline__ double ldsmetric(const double* p) { return *p; }
 __device__ __forceinline__ df ldsmetric(const df_pair* p) { return df(p->h, p->l); }
 
-template <int P, int QUAD, typename T, typename MT, bool DOT, bool MASS_ONLY>
+// Warp-per-element mode (WARP): each warp of the CTA owns one element and
+// synchronises with __syncwarp only, so the warps of an SM run their gather,
+// sweep, metric and scatter phases independently.  Used for the FP32 kernels,
+// which are bound by memory latency rather than by arithmetic.
+constexpr int kWarpsPerCta = kApplyThreads / 32;
+
+// Elements per warp in warp mode: G n^2 lines close to 32 lanes (p <= 4).
+template <int P> struct WarpCfg { static constexpr int G = 1; };
+template <> struct WarpCfg<1> { static constexpr int G = 8; };
+template <> struct WarpCfg<2> { static constexpr int G = 3; };
+template <> struct WarpCfg<3> { static constexpr int G = 2; };
+
+template <int P, typename T>
+__host__ __device__ constexpr size_t apply_warp_tile_bytes() {
+  return (size_t)3 * kWarpsPerCta * WarpCfg<P>::G * (P + 1) * (P + 1) * (P + 1) * sizeof(T);
+}
+
+template <int P, int QUAD, typename T, typename MT, bool DOT, bool MASS_ONLY, bool WARP = false>
 __global__ void __launch_bounds__(kApplyThreads)
     sem_apply_kernel(const ApplyArgs<T, MT> a, const __grid_constant__ KTab<P + 1, T> tab) {
+  static_assert(!(WARP && DOT), "the fused inner product needs the CTA-wide mode");
   constexpr int N = P + 1, N2 = N * N, N3 = N2 * N, N3P = padded_n3(N);
-  constexpr int E = ApplyCfg<P>::E;
-  constexpr bool STAGE = StageMetric<T>::value && !MASS_ONLY;
+  constexpr int E = WARP ? WarpCfg<P>::G : ApplyCfg<P>::E;
+  constexpr bool STAGE = StageMetric<T>::value && !MASS_ONLY && !WARP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sA = reinterpret_cast<T*>(smem_raw);
+  const int warp = threadIdx.x >> 5;
+  const int tid = WARP ? (threadIdx.x & 31) : threadIdx.x;
+  const int nth = WARP ? 32 : blockDim.x;
+  T* sA = reinterpret_cast<T*>(smem_raw) + (WARP ? warp * 3 * E * N3 : 0);
   T* sB = sA + E * N3;
   T* sC = sB + E * N3;
   MT* sM = reinterpret_cast<MT*>(smem_raw + apply_tile_bytes<P, T, MT>());
   __shared__ double red[32];
+  auto group_sync = [] {
+    if (WARP) __syncwarp(); else __syncthreads();
+  };
 
   if (a.done != nullptr && *a.done) return;
-  const int e0 = blockIdx.x * E;
+  const int e0 = WARP ? (blockIdx.x * kWarpsPerCta + warp) * E : blockIdx.x * E;
+  if (WARP && e0 >= a.nelem) return;  // no CTA-wide barrier follows in this mode
 
   if (STAGE) {  // the CTA's metric block: contiguous, 16-byte aligned, a multiple of 16 bytes
     const int ne = min(E, a.nelem - e0);
@@ -231,38 +259,38 @@ __global__ void __launch_bounds__(kApplyThreads)
   }
 
   // gather u_e = P_e u
-  for (int idx = threadIdx.x; idx < E * N3; idx += blockDim.x) {
+  for (int idx = tid; idx < E * N3; idx += nth) {
     const int s = idx / N3, loc = idx - s * N3, e = e0 + s;
     sA[idx] = (e < a.nelem) ? T(a.u[__ldg(a.map + (size_t)e * N3 + loc)]) : T(0);
   }
-  __syncthreads();
+  group_sync();
 
   if (QUAD == SEM_QUAD_LG) {  // values at the Gauss points
-    sweep<N, E, 0>(tab.Bi, sA, sB);
-    __syncthreads();
-    sweep<N, E, 1>(tab.Bi, sB, sC);
-    __syncthreads();
-    sweep<N, E, 2>(tab.Bi, sC, sA);
-    __syncthreads();
+    sweep<N, E, 0>(tab.Bi, sA, sB, tid, nth);
+    group_sync();
+    sweep<N, E, 1>(tab.Bi, sB, sC, tid, nth);
+    group_sync();
+    sweep<N, E, 2>(tab.Bi, sC, sA, tid, nth);
+    group_sync();
   }
 
   if (MASS_ONLY) {
-    for (int idx = threadIdx.x; idx < E * N3; idx += blockDim.x) {
+    for (int idx = tid; idx < E * N3; idx += nth) {
       const int s = idx / N3, loc = idx - s * N3, e = e0 + s;
       if (e < a.nelem) {
         const T W = ldmetric(a.metric + ((size_t)e * kMetricComps + 6) * N3P + loc);
         sA[idx] = (a.mass_coef * W) * sA[idx];
       }
     }
-    __syncthreads();
+    group_sync();
   } else {
     // reference gradient along x and y (into sB, sC)
-    sweep<N, E, 0>(tab.D, sA, sB);
-    sweep<N, E, 1>(tab.D, sA, sC);
+    sweep<N, E, 0>(tab.D, sA, sB, tid, nth);
+    sweep<N, E, 1>(tab.D, sA, sC, tid, nth);
     if (STAGE) asm volatile("cp.async.wait_all;\n" ::: "memory");
-    __syncthreads();
+    group_sync();
     // z-gradient, quadrature-point stage and transposed z-sweep on the columns
-    for (int w = threadIdx.x; w < E * N2; w += blockDim.x) {
+    for (int w = tid; w < E * N2; w += nth) {
       const int s = w / N2, c = w - s * N2, e = e0 + s;
       if (e >= a.nelem) continue;
       T* pa = sA + s * N3 + c;
@@ -304,25 +332,25 @@ __global__ void __launch_bounds__(kApplyThreads)
 #pragma unroll
       for (int k = 0; k < N; ++k) pa[k * N2] = m[k];
     }
-    __syncthreads();
-    sweepT<N, E, 1, true>(tab.D, sC, sA);
-    __syncthreads();
-    sweepT<N, E, 0, true>(tab.D, sB, sA);
-    __syncthreads();
+    group_sync();
+    sweepT<N, E, 1, true>(tab.D, sC, sA, tid, nth);
+    group_sync();
+    sweepT<N, E, 0, true>(tab.D, sB, sA, tid, nth);
+    group_sync();
   }
 
   if (QUAD == SEM_QUAD_LG) {  // back from the Gauss points to the nodes
-    sweepT<N, E, 0, false>(tab.Bi, sA, sB);
-    __syncthreads();
-    sweepT<N, E, 1, false>(tab.Bi, sB, sC);
-    __syncthreads();
-    sweepT<N, E, 2, false>(tab.Bi, sC, sA);
-    __syncthreads();
+    sweepT<N, E, 0, false>(tab.Bi, sA, sB, tid, nth);
+    group_sync();
+    sweepT<N, E, 1, false>(tab.Bi, sB, sC, tid, nth);
+    group_sync();
+    sweepT<N, E, 2, false>(tab.Bi, sC, sA, tid, nth);
+    group_sync();
   }
 
   // scatter-add y += P_e^T y_e
   double dot = 0.0;
-  for (int idx = threadIdx.x; idx < E * N3; idx += blockDim.x) {
+  for (int idx = tid; idx < E * N3; idx += nth) {
     const int s = idx / N3, loc = idx - s * N3, e = e0 + s;
     if (e < a.nelem) {
       const int g = __ldg(a.map + (size_t)e * N3 + loc);
@@ -362,6 +390,19 @@ cudaError_t launch_apply_t(const Level& L, const ApplyArgs<T, MT>& a, bool mass_
   if (grid == 0) return cudaSuccess;
   constexpr size_t tiles = apply_tile_bytes<P, T, MT>();
   constexpr size_t full = apply_smem_bytes<P, T, MT>();
+  // FP32 kernels at p <= 4: elements owned by warps (measured faster; at p = 5, 6
+  // the n^2 = 36, 49 lines fill warps poorly and the CTA-wide mode is faster)
+  constexpr bool warp_mode = sizeof(T) == 4 && P <= 4;
+  if (warp_mode && !dot) {
+    constexpr int per_cta = kWarpsPerCta * WarpCfg<P>::G;
+    const int wgrid = (L.nelem + per_cta - 1) / per_cta;
+    constexpr size_t wbytes = apply_warp_tile_bytes<P, T>();
+    if (mass_only)
+      sem_apply_kernel<P, QUAD, T, MT, false, true, true><<<wgrid, kApplyThreads, wbytes, s>>>(a, tab);
+    else
+      sem_apply_kernel<P, QUAD, T, MT, false, false, true><<<wgrid, kApplyThreads, wbytes, s>>>(a, tab);
+    return cudaGetLastError();
+  }
   if (mass_only) {
     sem_apply_kernel<P, QUAD, T, MT, false, true><<<grid, kApplyThreads, tiles, s>>>(a, tab);
   } else if (dot) {
