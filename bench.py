@@ -44,6 +44,7 @@ STIM_RADIUS = 1.5    # mm
 STIM_AMP = 50.0      # mV/ms
 STIM_T_OFF = 1.0     # ms
 SLAB_LENGTHS = W.SLAB_LENGTHS_MM
+MG_DTYPE = {"fp32": "f32", "bf16": "f32 arithmetic / bf16 metric", "fp64": "f64"}
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64: 152 SMs x 2 DFMA/clk x 2 flop x ~2.06 GHz
 
 # DRAM bytes (read + write) per launch of the CG apply kernel from one ncu capture
@@ -380,7 +381,8 @@ def run_gpu(args):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": ("f64 vectors, residuals, inner products, ionic exp; "
-                  f"{'double-float (f32 pairs)' if outer_is_df else 'f64'} operator; f32 multigrid V-cycle"),
+                  f"{'double-float (f32 pairs)' if outer_is_df else 'f64'} operator; "
+                  f"{MG_DTYPE[args.mg_precision]} multigrid V-cycle"),
         "data": "synthetic",
         "config": {
             "workload": (f"monodomain BDF2 time step, {'SEM-NI' if quad == 'LGL' else 'SEM'} Q{p} slab "
@@ -718,7 +720,7 @@ def main():
     ap.add_argument("--traffic", type=float, default=None,
                     help="dram bytes per apply launch from an ncu capture of the current kernel")
     ap.add_argument("--ref-applies-per-step", type=float, default=33.0)
-    ap.add_argument("--mg-precision", default="fp32", choices=["fp32", "bf16", "fp64"])
+    ap.add_argument("--mg-precision", default="bf16", choices=["fp32", "bf16", "fp64"])
     ap.add_argument("--op-precision", default="df64", choices=["df64", "fp64"],
                     help="arithmetic of the outer CG operator in the mixed path")
     ap.add_argument("--arms", default="both", choices=["both", "mixed", "fp64"],
