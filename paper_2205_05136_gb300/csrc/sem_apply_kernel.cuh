@@ -22,6 +22,9 @@
 // atomicAdd (RED) through the element-to-DOF map.
 #pragma once
 
+#include <algorithm>
+#include <type_traits>
+
 #include "sem_internal.cuh"
 
 namespace sem {
@@ -197,13 +200,42 @@ __host__ __device__ constexpr size_t apply_warp_tile_bytes();
 template <int P, typename T, typename MT>
 __host__ __device__ constexpr size_t apply_smem_bytes() {
   return apply_tile_bytes<P, T, MT>() +
-         (StageMetric<T>::value ? (size_t)ApplyCfg<P>::E * kMetricComps * padded_n3(P + 1) * sizeof(MT) : 0);
+         (StageMetric<T>::value ? (size_t)ApplyCfg<P>::E * MetricLayout<MT>::block(P + 1) * sizeof(MT) : 0);
 }
 
 __device__ __forceinline__ float ldsmetric(const float* p) { return *p; }
 __device__ __forceinline__ float ldsmetric(const __nv_bfloat16* p) { return __bfloat162float(*p); }
 __device__ __forceinline__ double ldsmetric(const double* p) { return *p; }
 __device__ __forceinline__ df ldsmetric(const df_pair* p) { return df(p->h, p->l); }
+
+// The 7 metric values G00 G01 G02 G11 G12 G22 W of one quadrature point, from
+// global memory (ld_point_g) or shared memory (ld_point_s); cs is the component
+// stride of the layout.  The point-major bf16 layout holds them in 16 bytes,
+// read by one 128-bit load.
+__device__ __forceinline__ float bf16_lo(unsigned w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16_hi(unsigned w) { return __uint_as_float(w & 0xffff0000u); }
+__device__ __forceinline__ void unpack_point(const uint4 v, float (&g)[kMetricComps]) {
+  g[0] = bf16_lo(v.x); g[1] = bf16_hi(v.x);
+  g[2] = bf16_lo(v.y); g[3] = bf16_hi(v.y);
+  g[4] = bf16_lo(v.z); g[5] = bf16_hi(v.z);
+  g[6] = bf16_lo(v.w);
+}
+template <typename T, typename MT>
+__device__ __forceinline__ void ld_point_g(const MT* p, int cs, T (&g)[kMetricComps]) {
+#pragma unroll
+  for (int c = 0; c < kMetricComps; ++c) g[c] = ldmetric(p + c * cs);
+}
+__device__ __forceinline__ void ld_point_g(const __nv_bfloat16* p, int, float (&g)[kMetricComps]) {
+  unpack_point(__ldg(reinterpret_cast<const uint4*>(p)), g);
+}
+template <typename T, typename MT>
+__device__ __forceinline__ void ld_point_s(const MT* p, int cs, T (&g)[kMetricComps]) {
+#pragma unroll
+  for (int c = 0; c < kMetricComps; ++c) g[c] = ldsmetric(p + c * cs);
+}
+__device__ __forceinline__ void ld_point_s(const __nv_bfloat16* p, int, float (&g)[kMetricComps]) {
+  unpack_point(*reinterpret_cast<const uint4*>(p), g);
+}
 
 // Warp-per-element mode (WARP): each warp of the CTA owns one element and
 // synchronises with __syncwarp only, so the warps of an SM run their gather,
@@ -226,7 +258,9 @@ template <int P, int QUAD, typename T, typename MT, bool DOT, bool MASS_ONLY, bo
 __global__ void __launch_bounds__(kApplyThreads)
     sem_apply_kernel(const ApplyArgs<T, MT> a, const __grid_constant__ KTab<P + 1, T> tab) {
   static_assert(!(WARP && DOT), "the fused inner product needs the CTA-wide mode");
-  constexpr int N = P + 1, N2 = N * N, N3 = N2 * N, N3P = padded_n3(N);
+  constexpr int N = P + 1, N2 = N * N, N3 = N2 * N;
+  using ML = MetricLayout<MT>;
+  constexpr int BLK = ML::block(N), CS = ML::comp_stride(N), PS = ML::kPointStride;
   constexpr int E = WARP ? WarpCfg<P>::G : ApplyCfg<P>::E;
   constexpr bool STAGE = StageMetric<T>::value && !MASS_ONLY && !WARP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -248,8 +282,8 @@ __global__ void __launch_bounds__(kApplyThreads)
 
   if (STAGE) {  // the CTA's metric block: contiguous, 16-byte aligned, a multiple of 16 bytes
     const int ne = min(E, a.nelem - e0);
-    const size_t bytes = (size_t)ne * kMetricComps * N3P * sizeof(MT);
-    const char* src = reinterpret_cast<const char*>(a.metric + (size_t)e0 * kMetricComps * N3P);
+    const size_t bytes = (size_t)ne * BLK * sizeof(MT);
+    const char* src = reinterpret_cast<const char*>(a.metric + (size_t)e0 * BLK);
     const unsigned dst = (unsigned)__cvta_generic_to_shared(sM);
     for (size_t off = (size_t)threadIdx.x * 16; off < bytes; off += (size_t)blockDim.x * 16)
       asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst + (unsigned)off),
@@ -278,7 +312,7 @@ __global__ void __launch_bounds__(kApplyThreads)
     for (int idx = tid; idx < E * N3; idx += nth) {
       const int s = idx / N3, loc = idx - s * N3, e = e0 + s;
       if (e < a.nelem) {
-        const T W = ldmetric(a.metric + ((size_t)e * kMetricComps + 6) * N3P + loc);
+        const T W = ldmetric(a.metric + (size_t)e * BLK + 6 * CS + loc * PS);
         sA[idx] = (a.mass_coef * W) * sA[idx];
       }
     }
@@ -300,29 +334,14 @@ __global__ void __launch_bounds__(kApplyThreads)
 #pragma unroll
       for (int k = 0; k < N; ++k) uz[k] = pa[k * N2];
       mat_line<N>(tab.D, uz, g3);
-      const MT* mp = STAGE ? sM + (size_t)s * kMetricComps * N3P + c
-                           : a.metric + (size_t)e * kMetricComps * N3P + c;
+      const MT* mp = STAGE ? sM + (size_t)s * BLK + c * PS : a.metric + (size_t)e * BLK + c * PS;
 #pragma unroll
       for (int k = 0; k < N; ++k) {
         const T g1 = pb[k * N2], g2 = pc[k * N2];
-        T G00, G01, G02, G11, G12, G22, W;
-        if (STAGE) {
-          G00 = ldsmetric(mp + 0 * N3P + k * N2);
-          G01 = ldsmetric(mp + 1 * N3P + k * N2);
-          G02 = ldsmetric(mp + 2 * N3P + k * N2);
-          G11 = ldsmetric(mp + 3 * N3P + k * N2);
-          G12 = ldsmetric(mp + 4 * N3P + k * N2);
-          G22 = ldsmetric(mp + 5 * N3P + k * N2);
-          W = ldsmetric(mp + 6 * N3P + k * N2);
-        } else {
-          G00 = ldmetric(mp + 0 * N3P + k * N2);
-          G01 = ldmetric(mp + 1 * N3P + k * N2);
-          G02 = ldmetric(mp + 2 * N3P + k * N2);
-          G11 = ldmetric(mp + 3 * N3P + k * N2);
-          G12 = ldmetric(mp + 4 * N3P + k * N2);
-          G22 = ldmetric(mp + 5 * N3P + k * N2);
-          W = ldmetric(mp + 6 * N3P + k * N2);
-        }
+        T gm[kMetricComps];
+        if (STAGE) ld_point_s(mp + k * N2 * PS, CS, gm);
+        else ld_point_g(mp + k * N2 * PS, CS, gm);
+        const T G00 = gm[0], G01 = gm[1], G02 = gm[2], G11 = gm[3], G12 = gm[4], G22 = gm[5], W = gm[6];
         pb[k * N2] = fma(G02, g3[k], fma(G01, g2, G00 * g1));
         pc[k * N2] = fma(G12, g3[k], fma(G11, g2, G01 * g1));
         q3[k] = fma(G22, g3[k], fma(G12, g2, G02 * g1));
@@ -374,6 +393,290 @@ __global__ void __launch_bounds__(kApplyThreads)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Pipelined warp kernel of the FP32 operator (p <= 4, stiffness and mass).
+//
+// A warp that owns one element at a time waits for the map, then for the
+// gathered values, then for the metric, and has nothing in flight while it
+// computes.  Here each warp loops over "units" of G consecutive elements
+// (unit j of the warp is unit w + j W, W warps in the grid) and keeps the
+// copies of unit j+1 in flight while it computes unit j:
+//   - the unit's metric block, contiguous in the element-blocked layout
+//     (16-byte aligned), by 16-byte cp.async;
+//   - the unit's nodal values, gathered by 4-byte cp.async from the map
+//     entries, which were loaded into registers one unit earlier still.
+// Two stage buffers per warp; a stage is complete after cp.async.wait_group
+// and visible to the whole warp after __syncwarp.  The grid is persistent
+// (the CTAs that are resident at once), so the pipeline runs over several units.
+//
+// Every lane owns one line of each sweep (G n^2 <= 32 for p <= 4).  Lanes
+// beyond the unit's G n^2 lines run the same instructions on the line of lane
+// (lane - G n^2): their loads are broadcasts of that lane's, their stores are
+// predicated off, so no sweep needs a divergent branch.
+template <int P, typename MT>
+struct PipeCfg {
+  static constexpr int N = P + 1, N2 = N * N, N3 = N2 * N;
+  static constexpr int BLK = MetricLayout<MT>::block(N);  // metric values of an element
+  static constexpr int G = WarpCfg<P>::G;
+  static constexpr int NL = G * N2;                  // lines per sweep direction
+  static constexpr int UT = G * N3;                  // nodal values of a unit
+  static constexpr int UTP = (UT + 3) / 4 * 4;       // float tile padded to 16 bytes
+  static constexpr int MV = G * BLK;                 // metric values of a unit
+  static constexpr int LPL = (UT + 31) / 32;         // nodes per lane
+  static constexpr int CH = (int)(MV * sizeof(MT) / 16);  // 16-byte chunks of a unit's metric
+  // two metric stages, two nodal stages and the two work tiles of the sweeps
+  static constexpr size_t warp_bytes = 2 * (size_t)MV * sizeof(MT) + 4 * (size_t)UTP * sizeof(float);
+  static constexpr size_t cta_bytes = kWarpsPerCta * warp_bytes;
+  static_assert(NL <= 32, "a unit must have at most 32 lines per direction");
+  static_assert((MV * sizeof(MT)) % 16 == 0 && (UTP * sizeof(float)) % 16 == 0,
+                "stage buffers must stay 16-byte aligned");
+};
+
+__device__ __forceinline__ void cp_async_16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int K>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory"); }
+
+// Map entries of unit `unit` for this lane (node idx = lane + 32 t of the unit);
+// entries of nodes outside the mesh are 0 and never used.
+template <int P, typename MT>
+__device__ __forceinline__ void pipe_load_map(const ApplyArgs<float, MT>& a, int unit, int nunits, int lane,
+                                              int (&m)[PipeCfg<P, MT>::LPL]) {
+  using C = PipeCfg<P, MT>;
+  const int nv = unit < nunits ? min(C::UT, (a.nelem - unit * C::G) * C::N3) : 0;  // nodes present
+  const int* src = a.map + (size_t)unit * C::UT;
+#pragma unroll
+  for (int t = 0; t < C::LPL; ++t) {
+    const int idx = lane + 32 * t;
+    m[t] = idx < nv ? __ldg(src + idx) : 0;
+  }
+}
+
+// Issues the copies of one unit into a stage (metric block and gathered u).
+template <int P, typename MT>
+__device__ __forceinline__ void pipe_issue(const ApplyArgs<float, MT>& a, int unit, int lane,
+                                           const int (&m)[PipeCfg<P, MT>::LPL], MT* sM, float* sU) {
+  using C = PipeCfg<P, MT>;
+  const int e0 = unit * C::G;
+  const char* src = reinterpret_cast<const char*>(a.metric + (size_t)e0 * C::BLK);
+  char* dst = reinterpret_cast<char*>(sM);
+  if (e0 + C::G <= a.nelem) {  // full unit: compile-time trip counts
+#pragma unroll
+    for (int t = 0; t < (C::CH + 31) / 32; ++t) {
+      const int c = lane + 32 * t;
+      if (C::CH % 32 == 0 || c < C::CH) cp_async_16(dst + 16 * c, src + 16 * c);
+    }
+#pragma unroll
+    for (int t = 0; t < C::LPL; ++t) {
+      const int idx = lane + 32 * t;
+      if (C::UT % 32 == 0 || idx < C::UT) cp_async_4(sU + idx, a.u + m[t]);
+    }
+  } else {  // the mesh's last, partial unit: zeros in the missing elements' tiles
+    const int ne = a.nelem - e0;
+    const int chunks = (int)((size_t)ne * C::BLK * sizeof(MT) / 16);
+    for (int c = lane; c < chunks; c += 32) cp_async_16(dst + 16 * c, src + 16 * c);
+#pragma unroll
+    for (int t = 0; t < C::LPL; ++t) {
+      const int idx = lane + 32 * t;
+      if (idx < C::UT) {
+        if (idx < ne * C::N3) cp_async_4(sU + idx, a.u + m[t]);
+        else sU[idx] = 0.f;
+      }
+    }
+  }
+}
+
+// One 1-D line of n values at stride STRIDE: dst = M src (TRANS: M^T src;
+// ACC: dst += ...).  src may equal dst.
+template <int N, int STRIDE, bool TRANS, bool ACC, typename T>
+__device__ __forceinline__ void lane_line(const T (&M)[N][N], const T* src, T* dst, bool store) {
+  T in[N], out[N];
+#pragma unroll
+  for (int t = 0; t < N; ++t) in[t] = src[t * STRIDE];
+  if (ACC) {
+#pragma unroll
+    for (int t = 0; t < N; ++t) out[t] = dst[t * STRIDE];
+  }
+  if (TRANS) matT_line<N, ACC>(M, in, out);
+  else mat_line<N>(M, in, out);
+#pragma unroll
+  for (int t = 0; t < N; ++t)
+    if (store) dst[t * STRIDE] = out[t];
+}
+
+template <int P, int QUAD, typename MT>
+__global__ void __launch_bounds__(kApplyThreads, 4)
+    sem_apply_pipe_kernel(const ApplyArgs<float, MT> a, const __grid_constant__ KTab<P + 1, float> tab,
+                          int nunits) {
+  using C = PipeCfg<P, MT>;
+  using T = float;
+  constexpr int N = C::N, N2 = C::N2, N3 = C::N3, G = C::G, LPL = C::LPL, NL = C::NL;
+  constexpr int CS = MetricLayout<MT>::comp_stride(N), PS = MetricLayout<MT>::kPointStride;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (a.done != nullptr && *a.done) return;
+  int unit = blockIdx.x * kWarpsPerCta + warp;
+  if (unit >= nunits) return;  // no CTA-wide barrier in this kernel
+  const int tw = gridDim.x * kWarpsPerCta;
+  unsigned char* wb = smem_raw + (size_t)warp * C::warp_bytes;
+  MT* sM0 = reinterpret_cast<MT*>(wb);
+  T* sU0 = reinterpret_cast<T*>(wb + 2 * (size_t)C::MV * sizeof(MT));
+  T* sB = sU0 + 2 * C::UTP;
+  T* sC = sB + C::UTP;  // followed by the scratch lines of the lanes >= NL
+
+  // line offsets of this lane (of lane - NL for the lanes >= NL): element slot ls, line ll
+  const bool act = lane < NL;
+  const int lw = act ? lane : lane - NL;
+  const int ls = lw / N2, ll = lw - ls * N2;
+  const int ox = ls * N3 + ll * N;                      // x-line (j, k) = ll
+  const int oy = ls * N3 + (ll / N) * N2 + (ll % N);    // y-line (i, k): i = ll % N, k = ll / N
+  const int oz = ls * N3 + ll;                          // z-line (i, j) = ll
+  const int mo = ls * C::BLK + ll * PS;  // the lane's first metric value in a unit stage
+
+  int mc[LPL], mn[LPL], mnn[LPL];  // map entries of units j, j+1, j+2
+  pipe_load_map<P>(a, unit, nunits, lane, mc);
+  pipe_issue<P>(a, unit, lane, mc, sM0, sU0);
+  cp_async_commit();
+  pipe_load_map<P>(a, unit + tw, nunits, lane, mn);
+  int b = 0;
+  for (; unit < nunits; unit += tw) {
+    const int nxt = unit + tw;
+    if (nxt < nunits) pipe_issue<P>(a, nxt, lane, mn, sM0 + (b ^ 1) * C::MV, sU0 + (b ^ 1) * C::UTP);
+    cp_async_commit();  // possibly empty group: keeps "all but the newest group" = stage b
+    pipe_load_map<P>(a, nxt + tw, nunits, lane, mnn);
+    cp_async_wait<1>();
+    __syncwarp();
+
+    T* sA = sU0 + b * C::UTP;
+    const MT* sM = sM0 + b * C::MV;
+    const int e0 = unit * G;
+    if (QUAD == SEM_QUAD_LG) {  // values at the Gauss points
+      lane_line<N, 1, false, false>(tab.Bi, sA + ox, sB + ox, act);
+      __syncwarp();
+      lane_line<N, N, false, false>(tab.Bi, sB + oy, sC + oy, act);
+      __syncwarp();
+      lane_line<N, N2, false, false>(tab.Bi, sC + oz, sA + oz, act);
+      __syncwarp();
+    }
+    // reference gradient along x and y (into sB, sC)
+    lane_line<N, 1, false, false>(tab.D, sA + ox, sB + ox, act);
+    lane_line<N, N, false, false>(tab.D, sA + oy, sC + oy, act);
+    __syncwarp();
+    // z-gradient, quadrature-point stage and transposed z-sweep on the lane's column
+    {
+      T* pa = sA + oz;
+      T* pb = sB + oz;
+      T* pc = sC + oz;
+      T uz[N], g3[N], q3[N], m[N];
+#pragma unroll
+      for (int k = 0; k < N; ++k) uz[k] = pa[k * N2];
+      mat_line<N>(tab.D, uz, g3);
+      const MT* mp = sM + mo;
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const T g1 = pb[k * N2], g2 = pc[k * N2];
+        T gm[kMetricComps];
+        ld_point_s(mp + k * N2 * PS, CS, gm);
+        const T G00 = gm[0], G01 = gm[1], G02 = gm[2], G11 = gm[3], G12 = gm[4], G22 = gm[5], W = gm[6];
+        const T q1 = fma(G02, g3[k], fma(G01, g2, G00 * g1));
+        const T q2 = fma(G12, g3[k], fma(G11, g2, G01 * g1));
+        if (act) {
+          pb[k * N2] = q1;
+          pc[k * N2] = q2;
+        }
+        q3[k] = fma(G22, g3[k], fma(G12, g2, G02 * g1));
+        m[k] = (a.mass_coef * W) * uz[k];
+      }
+      matT_line<N, true>(tab.D, q3, m);
+#pragma unroll
+      for (int k = 0; k < N; ++k)
+        if (act) pa[k * N2] = m[k];
+    }
+    __syncwarp();
+    lane_line<N, N, true, true>(tab.D, sC + oy, sA + oy, act);
+    __syncwarp();
+    lane_line<N, 1, true, true>(tab.D, sB + ox, sA + ox, act);
+    __syncwarp();
+    if (QUAD == SEM_QUAD_LG) {  // back from the Gauss points to the nodes
+      lane_line<N, 1, true, false>(tab.Bi, sA + ox, sB + ox, act);
+      __syncwarp();
+      lane_line<N, N, true, false>(tab.Bi, sB + oy, sC + oy, act);
+      __syncwarp();
+      lane_line<N, N2, true, false>(tab.Bi, sC + oz, sA + oz, act);
+      __syncwarp();
+    }
+    // scatter-add y += P_e^T y_e
+    const T sc = a.scale_out ? a.out_scale : T(1);
+    if (e0 + G <= a.nelem) {
+#pragma unroll
+      for (int t = 0; t < LPL; ++t) {
+        const int idx = lane + 32 * t;
+        if (C::UT % 32 == 0 || idx < C::UT) atomicAdd(a.y + mc[t], sA[idx] * sc);
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < LPL; ++t) {
+        const int idx = lane + 32 * t;
+        if (idx < C::UT && e0 + idx / N3 < a.nelem) atomicAdd(a.y + mc[t], sA[idx] * sc);
+      }
+    }
+    __syncwarp();  // stage b is refilled by the next iteration's issue
+#pragma unroll
+    for (int t = 0; t < LPL; ++t) {
+      mc[t] = mn[t];
+      mn[t] = mnn[t];
+    }
+    b ^= 1;
+  }
+  cp_async_wait<0>();
+}
+
+// Persistent grid of the pipelined kernel: the CTAs resident on the device at
+// once (set by prime_t, before any stream capture), at most one warp per unit.
+template <int P, int QUAD, typename MT>
+struct PipeGrid {
+  static inline int resident = 0;
+};
+
+template <int P, int QUAD, typename MT>
+cudaError_t pipe_prime() {
+  using C = PipeCfg<P, MT>;
+  cudaError_t e = cudaFuncSetAttribute(sem_apply_pipe_kernel<P, QUAD, MT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::cta_bytes);
+  int dev = 0, sms = 0, per_sm = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sem_apply_pipe_kernel<P, QUAD, MT>,
+                                                      kApplyThreads, C::cta_bytes);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  PipeGrid<P, QUAD, MT>::resident = sms * per_sm;
+  return cudaSuccess;
+}
+
+template <int P, int QUAD, typename MT>
+cudaError_t launch_apply_pipe(const Level& L, const ApplyArgs<float, MT>& a, const KTab<P + 1, float>& tab,
+                              cudaStream_t s) {
+  using C = PipeCfg<P, MT>;
+  const int resident = PipeGrid<P, QUAD, MT>::resident;
+  if (resident < 1) return cudaErrorInitializationError;  // prime_apply_kernels was not called
+  const int nunits = (L.nelem + C::G - 1) / C::G;
+  const int grid = std::min(resident, (nunits + kWarpsPerCta - 1) / kWarpsPerCta);
+  if (grid == 0) return cudaSuccess;
+  sem_apply_pipe_kernel<P, QUAD, MT><<<grid, kApplyThreads, C::cta_bytes, s>>>(a, tab, nunits);
+  return cudaGetLastError();
+}
+
 // Launch helper shared by the precision-specific translation units.
 template <int P, int QUAD, typename T, typename MT>
 cudaError_t launch_apply_t(const Level& L, const ApplyArgs<T, MT>& a, bool mass_only, bool dot,
@@ -393,6 +696,9 @@ cudaError_t launch_apply_t(const Level& L, const ApplyArgs<T, MT>& a, bool mass_
   // FP32 kernels at p <= 4: elements owned by warps (measured faster; at p = 5, 6
   // the n^2 = 36, 49 lines fill warps poorly and the CTA-wide mode is faster)
   constexpr bool warp_mode = sizeof(T) == 4 && P <= 4;
+  if constexpr (std::is_same<T, float>::value && P <= 4) {
+    if (!mass_only && !dot) return launch_apply_pipe<P, QUAD, MT>(L, a, tab, s);
+  }
   if (warp_mode && !dot) {
     constexpr int per_cta = kWarpsPerCta * WarpCfg<P>::G;
     const int wgrid = (L.nelem + per_cta - 1) / per_cta;
@@ -418,6 +724,9 @@ template <int P, int QUAD, typename T, typename MT>
 cudaError_t prime_t() {
   constexpr int full = (int)apply_smem_bytes<P, T, MT>();
   cudaError_t e;
+  if constexpr (std::is_same<T, float>::value && P <= 4) {
+    if ((e = pipe_prime<P, QUAD, MT>()) != cudaSuccess) return e;
+  }
   if ((e = cudaFuncSetAttribute(sem_apply_kernel<P, QUAD, T, MT, false, false>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, full)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(sem_apply_kernel<P, QUAD, T, MT, true, false>,

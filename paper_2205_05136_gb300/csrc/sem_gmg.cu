@@ -766,7 +766,7 @@ int build(sem_ctx* ctx, cudaStream_t s) {
       GMG_CK(setup_metric_lowp(L, false, s));
     }
     if (g->precision == SEM_PREC_FP32_BF16 && !L.metric16_valid) {
-      if (!L.metric16) GMG_CK(cudaMalloc(&L.metric16, sizeof(__nv_bfloat16) * metric_count(L)));
+      if (!L.metric16) GMG_CK(cudaMalloc(&L.metric16, sizeof(__nv_bfloat16) * metric16_count(L)));
       GMG_CK(setup_metric_lowp(L, true, s));
     }
     void** vecs[] = {&V.b, &V.x, &V.t, &V.d, &V.invd};

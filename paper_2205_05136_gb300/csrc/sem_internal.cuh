@@ -5,7 +5,9 @@
 //   metric   double [nelem][7][n3p] per quadrature point: G00 G01 G02 G11 G12 G22 W,
 //            n3p = n^3 rounded up to a multiple of 8 (16-byte aligned blocks),
 //            G = w |det J| J^{-1} D J^{-T}, W = w |det J|  (element-blocked SoA)
-//   metric32 float / bf16 copies of the same array for the mixed-precision applies
+//   metric32 float [nelem][7][n3p] copy of the same array (mixed-precision applies)
+//   metric16 bf16  [nelem][n^3][8] point-major copy: the 7 values of a quadrature
+//            point (and one zero) in 16 bytes, read by one 128-bit load
 //   mdiag    double [ndofs]  diagonal of the assembled mass matrix
 //   kdiag    double [ndofs]  diagonal of the assembled stiffness matrix
 //   xyz      double [3][ndofs] node coordinates
@@ -100,6 +102,29 @@ struct Level {
 // Number of metric values of a level (7 components x padded points per element).
 inline size_t metric_count(const Level& L) {
   return (size_t)L.nelem * kMetricComps * padded_n3(L.n);
+}
+
+// Index of component c of quadrature point q inside one element's metric block:
+// component-major [7][n3p] for double, float and float pairs; point-major
+// [n^3][8] for bf16 (the storage precision whose 7 values fit one 16-byte load).
+template <typename MT>
+struct MetricLayout {
+  static constexpr bool kPointMajor = false;
+  __host__ __device__ static constexpr int block(int n) { return kMetricComps * padded_n3(n); }
+  __host__ __device__ static constexpr int comp_stride(int n) { return padded_n3(n); }
+  static constexpr int kPointStride = 1;
+};
+template <>
+struct MetricLayout<__nv_bfloat16> {
+  static constexpr bool kPointMajor = true;
+  __host__ __device__ static constexpr int block(int n) { return 8 * n * n * n; }
+  __host__ __device__ static constexpr int comp_stride(int) { return 1; }
+  static constexpr int kPointStride = 8;
+};
+
+// Number of values of the bf16 metric of a level.
+inline size_t metric16_count(const Level& L) {
+  return (size_t)L.nelem * MetricLayout<__nv_bfloat16>::block(L.n);
 }
 
 // Arguments of the element kernel y += A_e u_e (scatter-add into y).

@@ -242,12 +242,16 @@ __global__ void k_convert<float>(int64_t n, const double* __restrict__ in, float
     out[i] = __double2float_rn(in[i]);
 }
 
-template <>
-__global__ void k_convert<__nv_bfloat16>(int64_t n, const double* __restrict__ in,
-                                         __nv_bfloat16* __restrict__ out) {
+// bf16 copy in the point-major layout: out[e][q][c] = in[e][c][q] (c < 7), out[e][q][7] = 0.
+__global__ void k_convert_points_bf16(int64_t n, int n3, int n3p, const double* __restrict__ in,
+                                      __nv_bfloat16* __restrict__ out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = __float2bfloat16_rn(__double2float_rn(in[i]));
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = i / (8 * n3);
+    const int r = (int)(i - e * 8 * n3), q = r >> 3, c = r & 7;
+    const double v = c < kMetricComps ? in[(e * kMetricComps + c) * n3p + q] : 0.0;
+    out[i] = __float2bfloat16_rn(__double2float_rn(v));
+  }
 }
 
 __global__ void k_split_pairs(int64_t n, const double* __restrict__ in, df_pair* __restrict__ out) {
@@ -357,7 +361,10 @@ cudaError_t setup_metric_lowp(Level& L, bool bf16, cudaStream_t s) {
   const int threads = 256;
   const int blocks = (int)std::min<int64_t>((count + threads - 1) / threads, 152 * 16);
   if (bf16) {
-    k_convert<__nv_bfloat16><<<blocks, threads, 0, s>>>(count, L.metric, L.metric16);
+    const int64_t count16 = (int64_t)metric16_count(L);
+    const int blocks16 = (int)std::min<int64_t>((count16 + threads - 1) / threads, 152 * 16);
+    k_convert_points_bf16<<<blocks16, threads, 0, s>>>(count16, L.n * L.n * L.n, padded_n3(L.n),
+                                                       L.metric, L.metric16);
     L.metric16_valid = true;
   } else {
     k_convert<float><<<blocks, threads, 0, s>>>(count, L.metric, L.metric32);

@@ -331,7 +331,7 @@ int apply_fp32(sem_ctx* ctx, double alpha, double beta, const float* u, float* y
   Level& L = ctx->L;
   if (bf16 && !L.metric16_valid) {
     if (!L.metric16)
-      SEM_CK(cudaMalloc(&L.metric16, sizeof(__nv_bfloat16) * metric_count(L)));
+      SEM_CK(cudaMalloc(&L.metric16, sizeof(__nv_bfloat16) * metric16_count(L)));
     SEM_CK(setup_metric_lowp(L, true, s));
   }
   if (!bf16 && !L.metric32_valid) {
