@@ -47,9 +47,12 @@ SLAB_LENGTHS = W.SLAB_LENGTHS_MM
 MG_DTYPE = {"fp32": "f32", "bf16": "f32 arithmetic / bf16 metric", "fp64": "f64"}
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64: 152 SMs x 2 DFMA/clk x 2 flop x ~2.06 GHz
 
-# DRAM bytes (read + write) per launch of the CG apply kernel from one ncu capture
-# (profiles/sem_apply_fp64_p4_semni_2M.md); an entry is removed whenever that kernel changes.
+# DRAM bytes (read + write) per launch from one ncu capture of the kernel on this
+# slab; an entry is removed whenever its kernel changes.
+#   FP64 CG apply: profiles/sem_apply_fp64_p4_semni_2M.md
 NCU_TRAFFIC = {(4, "LGL"): 267.783424e6 + 12.869632e6}
+#   FP32 smoother apply (bf16 metric, pipelined warp kernel): profiles/sem_apply_pipe_bf16_p4_semni_2M.md
+NCU_TRAFFIC_SMOOTHER = {(4, "LGL", "bf16"): 94.769152e6 + 2.514432e6}
 
 
 def peaks():
@@ -310,8 +313,8 @@ def run_gpu(args):
         sm_bytes = n_e * apply_bytes_per_element_fp32(p, args.mg_precision)
         per_vcycle = 2 * args.mg_degree  # fine-level applies per V-cycle
         kernels["smoother_apply"] = {
-            "kernel": f"sem_apply_kernel<P={p},{quad},f32,{'bf16' if args.mg_precision == 'bf16' else 'f32'} metric> "
-                      f"(fine-level V-cycle apply)",
+            "kernel": (f"{'sem_apply_pipe_kernel' if p <= 4 else 'sem_apply_kernel'}<P={p},{quad},f32,"
+                       f"{'bf16' if args.mg_precision == 'bf16' else 'f32'} metric> (fine-level V-cycle apply)"),
             "timed": int(stats.n_smoother_apply), "avg_ms": sm_ms,
             "total_ms_est": sm_ms * per_vcycle * stats.n_smoother_apply,
             "algorithmic_bytes_per_launch": sm_bytes,
@@ -322,7 +325,8 @@ def run_gpu(args):
     if dominant == "smoother_apply":
         ksm = kernels["smoother_apply"]
         roofline = {"bound": "hbm", "achieved": ksm["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
-                    "frac": ksm["achieved_gbs"] / hbm_peak, "traffic": None, "kernel": ksm["kernel"],
+                    "frac": ksm["achieved_gbs"] / hbm_peak,
+                    "traffic": NCU_TRAFFIC_SMOOTHER.get((p, quad, args.mg_precision)), "kernel": ksm["kernel"],
                     "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs), burst figure"}
     elif outer_is_df:
         roofline = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
