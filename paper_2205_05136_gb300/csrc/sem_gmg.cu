@@ -320,13 +320,15 @@ __global__ void k_fpcg_init(int64_t n, const double* __restrict__ b, double* __r
   }
 }
 
-// z_new = (double) x0; first: p = z_new, rz = r.z_new; else
-// beta = (r.z_new - r.z_old) / rz, rz = r.z_new (z holds z_old on entry).
+// z_new = (double) x0; first iteration (no iteration finished yet): p = z_new,
+// rz = r.z_new; else beta = (r.z_new - r.z_old) / rz, rz = r.z_new (z holds
+// z_old on entry).
 template <typename T>
 __global__ void k_fpcg_z(int64_t n, const T* __restrict__ x0, double* __restrict__ z,
-                         const double* __restrict__ r, double* __restrict__ p, int first,
-                         CgScalars* cg, double* partials, int stride, unsigned int* ticket) {
+                         const double* __restrict__ r, double* __restrict__ p, CgScalars* cg,
+                         double* partials, int stride, unsigned int* ticket) {
   if (cg->done) return;
+  const bool first = cg->iters == 0;
   double v[2] = {0.0, 0.0};
   GRID_LOOP(i, n) {
     const double zi = (double)x0[i];
@@ -356,7 +358,7 @@ __global__ void k_fpcg_z(int64_t n, const T* __restrict__ x0, double* __restrict
 
 __global__ void k_fpcg_p(int64_t n, const double* __restrict__ z, double* __restrict__ p,
                          const CgScalars* cg) {
-  if (cg->done) return;
+  if (cg->done || cg->iters == 0) return;  // first iteration: k_fpcg_z set p = z
   const double beta = cg->beta;
   GRID_LOOP(i, n) p[i] = fma(beta, p[i], z[i]);
 }
@@ -809,6 +811,10 @@ int64_t count_kernels(cudaGraph_t graph) {
 }
 
 // The PCG launch sequences, issued on stream s (a capture stream when graphs are built).
+// Set-up: r = b - A x, stopping threshold, convergence test.  One iteration:
+// z = V(r), beta, p = z + beta p, A p with alpha = r.z / p.Ap, x and r updated,
+// convergence test.  The iteration ends with the test, so the host launches no
+// V-cycle after convergence.
 template <typename T>
 int pcg_init_seq(sem_ctx* ctx, Gmg& g, double alpha, const double* b, const double* x, double rtol,
                  double atol, cudaStream_t s) {
@@ -828,12 +834,6 @@ int pcg_init_seq(sem_ctx* ctx, Gmg& g, double alpha, const double* b, const doub
   k_fpcg_init<T><<<gr, kThreads, 0, s>>>(n, b, w.Ap, w.r, b0, w.cg, g.partials, stride, g.tickets,
                                          rtol, atol);
   GMG_CK(cudaGetLastError());
-  const int* done = &w.cg->done;
-  int rc = vcycle(ctx, g, done, s);
-  if (rc != SEM_OK) return rc;
-  k_fpcg_z<T><<<gr, kThreads, 0, s>>>(n, (const T*)g.lv[0].x, g.z, w.r, w.p, 1, w.cg, g.partials,
-                                      stride, g.tickets + 1);
-  GMG_CK(cudaGetLastError());
   return SEM_OK;
 }
 
@@ -845,22 +845,22 @@ int pcg_iter_seq(sem_ctx* ctx, Gmg& g, double alpha, double* x, cudaStream_t s) 
   const int gr = grid1d(n);
   const int stride = g.partial_len;
   const int* done = &w.cg->done;
+  int rc = vcycle(ctx, g, done, s, true);
+  if (rc != SEM_OK) return rc;
+  k_fpcg_z<T><<<gr, kThreads, 0, s>>>(n, (const T*)g.lv[0].x, g.z, w.r, w.p, w.cg, g.partials,
+                                      stride, g.tickets + 1);
+  k_fpcg_p<<<gr, kThreads, 0, s>>>(n, g.z, w.p, w.cg);
+  GMG_CK(cudaGetLastError());
   ApplyArgs64 ap{};
   ap.map = L.map; ap.metric = L.metric; ap.u = w.p; ap.y = w.Ap; ap.nelem = L.nelem;
   ap.mass_coef = alpha; ap.out_scale = 1.0; ap.scale_out = 0; ap.done = done;
   ap.dot_partials = w.apply_partials; ap.dot_ticket = w.tickets + 1; ap.cg = w.cg;
-  // external records become event nodes of the captured graph (timing of the FP64 apply)
+  // external records become event nodes of the captured graph (timing of the outer apply)
   GMG_CK(cudaEventRecordWithFlags(g.ev0, s, cudaEventRecordExternal));
   GMG_CK(launch_operator(ctx, ap, s));
   GMG_CK(cudaEventRecordWithFlags(g.ev1, s, cudaEventRecordExternal));
   k_fpcg_xr<T><<<gr, kThreads, 0, s>>>(n, x, w.p, w.Ap, w.r, (T*)g.lv[0].b, w.cg, g.partials,
                                        stride, g.tickets + 2);
-  GMG_CK(cudaGetLastError());
-  int rc = vcycle(ctx, g, done, s, true);
-  if (rc != SEM_OK) return rc;
-  k_fpcg_z<T><<<gr, kThreads, 0, s>>>(n, (const T*)g.lv[0].x, g.z, w.r, nullptr, 0, w.cg,
-                                      g.partials, stride, g.tickets + 1);
-  k_fpcg_p<<<gr, kThreads, 0, s>>>(n, g.z, w.p, w.cg);
   GMG_CK(cudaGetLastError());
   return SEM_OK;
 }
@@ -933,7 +933,7 @@ int pcg_t(sem_ctx* ctx, Gmg& g, double alpha, const double* b, double* x, double
       } else {
         cudaGetLastError();  // timing unavailable for these event nodes: not an error
       }
-      if (!w.cg_host->done && cudaEventElapsedTime(&ms, g.ev2, g.ev3) == cudaSuccess) {
+      if (cudaEventElapsedTime(&ms, g.ev2, g.ev3) == cudaSuccess) {
         tm.smoother_ms += ms;
         tm.smoother_count += 1;
       } else {

@@ -176,29 +176,35 @@ struct IonicArgs {
 //   I_ion(u*, h^{n+1}); g = history/dt terms - I_ion + I_app
 //   out = mdiag * g (SEM-NI: M diagonal) or g (SEM: M g applied afterwards)
 //   x0 = u^n (warm start of CG)
+// With the switch s = 1 / (1 + E), E = exp(-(v - v_gate) / kappa), the opening
+// and closing rates are a = E / ((1 + E) tau_open) and b = 1 / ((1 + E) tau_close);
+// multiplying the gate update through by (1 + E) leaves one FP64 division:
+//   BDF2: h = (H (1 + E) + 2 dt E / tau_open) / (3 (1 + E) + 2 dt (E / tau_open + 1 / tau_close)),
+//         H = 4 h^n - h^{n-1}
+//   BDF1: h = (h^n (1 + E) + dt E / tau_open) / ((1 + E) + dt (E / tau_open + 1 / tau_close)).
+// The exponent is capped at 80 (v more than 0.8 below v_gate): s < 2e-35 there,
+// below the rounding of h.
 __global__ void __launch_bounds__(kVecThreads)
     k_ionic_rhs(int64_t n, const double* __restrict__ un, const double* __restrict__ unm1,
                 const double* __restrict__ hn, const double* __restrict__ hnm1,
                 double* __restrict__ hnext, double* __restrict__ x0, double* __restrict__ out,
                 const double* __restrict__ mdiag, const double* __restrict__ mask, double iapp,
                 const IonicArgs prm, double dt, int first) {
+  const double inv_dt = 1.0 / dt, inv_2dt = 0.5 / dt;
+  const double c_open = (first ? dt : 2.0 * dt) * prm.inv_tau_open;
+  const double c_close = (first ? dt : 2.0 * dt) * prm.inv_tau_close;
+  const double c_den = first ? 1.0 : 3.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double u0 = un[i];
     const double u1 = first ? u0 : unm1[i];
     const double us = first ? u0 : 2.0 * u0 - u1;
     const double v = (us - prm.u_rest) * prm.inv_amp;
-    const double sw = 1.0 / (1.0 + exp(-(v - prm.v_gate) * prm.inv_kappa));
-    const double ra = (1.0 - sw) * prm.inv_tau_open;
-    const double rb = sw * prm.inv_tau_close;
-    double h, hist;
-    if (first) {
-      h = (hn[i] + dt * ra) / (1.0 + dt * (ra + rb));
-      hist = u0 / dt;
-    } else {
-      h = (4.0 * hn[i] - hnm1[i] + 2.0 * dt * ra) / (3.0 + 2.0 * dt * (ra + rb));
-      hist = (4.0 * u0 - u1) / (2.0 * dt);
-    }
+    const double E = exp(fmin(-(v - prm.v_gate) * prm.inv_kappa, 80.0));
+    const double ope = 1.0 + E;
+    const double H = first ? hn[i] : fma(4.0, hn[i], -hnm1[i]);
+    const double h = fma(H, ope, c_open * E) / fma(c_den, ope, fma(c_open, E, c_close));
+    const double hist = first ? u0 * inv_dt : fma(4.0, u0, -u1) * inv_2dt;
     const double iion = -prm.u_amp * (h * v * v * (1.0 - v) * prm.inv_tau_in - v * prm.inv_tau_out);
     double g = hist - iion;
     if (mask != nullptr) g += iapp * mask[i];
