@@ -160,7 +160,8 @@ int sem_cg_solve(sem_ctx* ctx, double alpha, const double* b, double* x, double 
 /* Geometric multigrid preconditioner (Section 4.3), used by sem_cg_solve and
  * sem_step with precond = SEM_PC_GMG.  Levels: the fine Q_p level, p-coarsened
  * levels on the same mesh (p -> p/2 -> ... -> 1), then 2:1 h-coarsened Q_1
- * levels until a level has at most min_coarse_dofs nodes; operators are
+ * levels; coarsening stops at the first level (p- or h-) with at most
+ * min_coarse_dofs nodes; operators are
  * rediscretised per level.  Smoother: Chebyshev-Jacobi of the given degree on
  * [0.08, 1.2] x lambda_max(D^{-1} A), lambda_max from 10 Lanczos (CG) steps;
  * coarse_degree Chebyshev steps on the coarsest level.  precision: the

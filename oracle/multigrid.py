@@ -22,8 +22,9 @@ on an octree, the workloads ask for p-coarsening followed by h-coarsening):
 * restriction = prolongation^T; coarse operators are rediscretised
   (alpha M_l + K_l on each level); a coarse element takes the tissue of its
   first fine child (lowest x, y, z);
-* coarsening stops when a level has at most ``min_coarse_dofs`` nodes or
-  cannot be coarsened further.
+* coarsening (p first, then h) goes on while a level has more than
+  ``min_coarse_dofs`` nodes and can be coarsened further, so a p-level may be
+  the coarsest one.
 
 Chebyshev semi-iteration for A x = b with preconditioner D^{-1} on the
 interval [a, b] of the spectrum of D^{-1} A (theta = (b+a)/2, delta = (b-a)/2,
@@ -203,7 +204,7 @@ class Hierarchy:
         self.tissues = [tissue]
         self.P = []
         s, t = fine, tissue
-        while s.p > 1:
+        while s.p > 1 and s.ndofs > min_coarse_dofs:
             pc = max(1, s.p // 2)
             c = SlabSpace(s.V.reshape(-1, 3), s.nx, s.ny, s.nz, pc, s.quad)
             self.P.append(p_prolongation(c, s))

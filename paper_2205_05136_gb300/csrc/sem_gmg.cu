@@ -710,7 +710,9 @@ int build(sem_ctx* ctx, cudaStream_t s) {
   int nx = ctx->L.nx, ny = ctx->L.ny, nz = ctx->L.nz, p = ctx->L.p;
   const int quad = ctx->L.quad;
   GMG_CK(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), s));
-  while (p > 1) {  // p-coarsening on the fine mesh
+  // p-coarsening on the fine mesh, then h-coarsening, while the level is larger
+  // than min_coarse_dofs (a p-level may be the coarsest)
+  while (p > 1 && g->lv.back().L->ndofs > ctx->gmg_min_coarse_dofs) {
     const int pc = std::max(1, p / 2);
     GmgLevel V;
     V.L = new Level();

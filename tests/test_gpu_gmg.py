@@ -39,9 +39,11 @@ def _setup(dims, p, quad, min_coarse, precision, perturb=0.1):
 
 
 @pytest.mark.parametrize("quad", ["LGL", "LG"])
-@pytest.mark.parametrize("dims,p", [((6, 4, 3), 4), ((5, 3, 3), 3), ((4, 4, 2), 6), ((3, 3, 2), 5), ((6, 3, 2), 2)])
-def test_hierarchy_and_vcycle_fp64(dims, p, quad):
-    s, tissue, g, o, H = _setup(dims, p, quad, 30, capi.SEM_PREC_FP64)
+@pytest.mark.parametrize("dims,p,min_coarse", [((6, 4, 3), 4, 30), ((5, 3, 3), 3, 30), ((4, 4, 2), 6, 30),
+                                               ((3, 3, 2), 5, 30), ((6, 3, 2), 2, 30),
+                                               ((6, 4, 3), 4, 1000)])
+def test_hierarchy_and_vcycle_fp64(dims, p, min_coarse, quad):
+    s, tissue, g, o, H = _setup(dims, p, quad, min_coarse, capi.SEM_PREC_FP64)
     info = capi.sem_gmg_info(g.ctx, ALPHA)
     assert info["nlevels"] == H.nlevels
     assert info["p"] == [sp_.p for sp_ in H.spaces]

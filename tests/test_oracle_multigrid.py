@@ -104,3 +104,17 @@ def test_vcycle_symmetric_and_pcg_converges(quad):
     xref = spla.spsolve(H.A[0].tocsc(), y)
     assert np.linalg.norm(x - xref) < 1e-10 * np.linalg.norm(xref)
     assert it <= 15, it
+
+
+@pytest.mark.parametrize("min_coarse,ps", [(1000, [4, 2]), (500, [4, 2, 1]), (100, [4, 2, 1, 1])])
+def test_coarsening_stops_at_first_small_level(min_coarse, ps):
+    """p-levels of the 6 x 4 x 3 slab at p = 4 have 5525, 819 and 140 nodes; coarsening
+    (p first, then h) stops at the first level with at most min_coarse_dofs nodes."""
+    s = W.slab(6, 4, 3, (20.0, 7.0, 3.0), perturb=0.1)
+    tissue = (np.full(s.n_elements, 0.12), np.full(s.n_elements, 0.03), W.transmural_fiber_angles(s))
+    H = MG.Hierarchy(_space(s, 4, "LGL"), tissue, 30.0, degree=3, coarse_degree=10,
+                     min_coarse_dofs=min_coarse)
+    assert [sp_.p for sp_ in H.spaces] == ps
+    assert [sp_.ndofs for sp_ in H.spaces][:3] == [5525, 819, 140][:len(ps)]
+    assert H.spaces[-1].ndofs <= min_coarse
+    assert all(sp_.ndofs > min_coarse for sp_ in H.spaces[:-1])
