@@ -65,60 +65,71 @@ __device__ __forceinline__ void line_geom(int l, int& base, int& stride) {
   else { base = l; stride = N * N; }
 }
 
-// out[q] = sum_l M[q][l] in[l]
-template <int N, typename T>
-__device__ __forceinline__ void mat_line(const T (&M)[N][N], const T (&in)[N], T (&out)[N]) {
+// out = M in (ACC: out += M in) for M in even-odd form (EoMat), ANTI for
+// s = -1.  With e_l = in_l + in_{n-1-l}, o_l = in_l - in_{n-1-l} (l < H):
+//   se_q = sum_l a[q][l] e_l (+ a[q][H] in_H),  so_q = sum_l b[q][l] o_l,
+//   out_q = se_q + so_q,  out_{n-1-q} = (ANTI ? so_q - se_q : se_q - so_q)   (q < H),
+//   odd n: out_H = ANTI ? sum_l c[l] o_l : sum_l c[l] e_l + c[H] in_H.
+// At n = 5 that is 12 multiply-adds and 8 additions instead of 25 multiply-adds.
+template <int N, bool ANTI, bool ACC, typename T>
+__device__ __forceinline__ void eo_line(const EoMat<N, T>& M, const T (&in)[N], T (&out)[N]) {
+  if constexpr (EoMat<N, T>::kDirect) {  // out_q (+)= sum_l m[q][l] in_l
 #pragma unroll
-  for (int q = 0; q < N; ++q) {
-    T acc = M[q][0] * in[0];
+    for (int q = 0; q < N; ++q) {
+      T acc = ACC ? fma(M.m[q][0], in[0], out[q]) : M.m[q][0] * in[0];
 #pragma unroll
-    for (int l = 1; l < N; ++l) acc = fma(M[q][l], in[l], acc);
-    out[q] = acc;
-  }
-}
-
-// out[l] = sum_q M[q][l] in[q]  (ACC: out[l] += ...)
-template <int N, bool ACC, typename T>
-__device__ __forceinline__ void matT_line(const T (&M)[N][N], const T (&in)[N], T (&out)[N]) {
-#pragma unroll
-  for (int l = 0; l < N; ++l) {
-    T acc;
-    if (ACC) {
-      acc = out[l];
-#pragma unroll
-      for (int q = 0; q < N; ++q) acc = fma(M[q][l], in[q], acc);
-    } else {
-      acc = M[0][l] * in[0];
-#pragma unroll
-      for (int q = 1; q < N; ++q) acc = fma(M[q][l], in[q], acc);
+      for (int l = 1; l < N; ++l) acc = fma(M.m[q][l], in[l], acc);
+      out[q] = acc;
     }
-    out[l] = acc;
+    return;
+  }
+  constexpr int H = N / 2;
+  constexpr bool ODD = (N & 1) != 0;
+  T e[H], o[H];
+#pragma unroll
+  for (int l = 0; l < H; ++l) {
+    e[l] = in[l] + in[N - 1 - l];
+    o[l] = in[l] - in[N - 1 - l];
+  }
+#pragma unroll
+  for (int q = 0; q < H; ++q) {
+    T se = M.a[q][0] * e[0];
+#pragma unroll
+    for (int l = 1; l < H; ++l) se = fma(M.a[q][l], e[l], se);
+    if (ODD) se = fma(M.a[q][H], in[H], se);
+    T so = M.b[q][0] * o[0];
+#pragma unroll
+    for (int l = 1; l < H; ++l) so = fma(M.b[q][l], o[l], so);
+    const T y0 = se + so;
+    const T y1 = ANTI ? so - se : se - so;
+    if (ACC) {
+      out[q] = out[q] + y0;
+      out[N - 1 - q] = out[N - 1 - q] + y1;
+    } else {
+      out[q] = y0;
+      out[N - 1 - q] = y1;
+    }
+  }
+  if (ODD) {
+    T ym;
+    if (ANTI) {
+      ym = M.c[0] * o[0];
+#pragma unroll
+      for (int l = 1; l < H; ++l) ym = fma(M.c[l], o[l], ym);
+    } else {
+      ym = M.c[0] * e[0];
+#pragma unroll
+      for (int l = 1; l < H; ++l) ym = fma(M.c[l], e[l], ym);
+      ym = fma(M.c[H], in[H], ym);
+    }
+    out[H] = ACC ? out[H] + ym : ym;
   }
 }
 
-// dst = M along DIR of src, for every line of the E element tiles (thread tid
-// of a group of nth threads).
-template <int N, int E, int DIR, typename T>
-__device__ __forceinline__ void sweep(const T (&M)[N][N], const T* src, T* dst, int tid, int nth) {
-  constexpr int N2 = N * N, N3 = N2 * N;
-  for (int w = tid; w < E * N2; w += nth) {
-    const int s = w / N2, l = w - s * N2;
-    int base, stride;
-    line_geom<N, DIR>(l, base, stride);
-    const T* ps = src + s * N3 + base;
-    T* pd = dst + s * N3 + base;
-    T in[N], out[N];
-#pragma unroll
-    for (int t = 0; t < N; ++t) in[t] = ps[t * stride];
-    mat_line<N>(M, in, out);
-#pragma unroll
-    for (int t = 0; t < N; ++t) pd[t * stride] = out[t];
-  }
-}
-
-// dst = M^T along DIR of src (ACC: dst += M^T src).  src may equal dst.
-template <int N, int E, int DIR, bool ACC, typename T>
-__device__ __forceinline__ void sweepT(const T (&M)[N][N], const T* src, T* dst, int tid, int nth) {
+// dst = M along DIR of src (ACC: dst += ...), for every line of the E element
+// tiles (thread tid of a group of nth threads).  src may equal dst.
+template <int N, int E, int DIR, bool ANTI, bool ACC, typename T>
+__device__ __forceinline__ void sweep(const EoMat<N, T>& M, const T* src, T* dst, int tid, int nth) {
   constexpr int N2 = N * N, N3 = N2 * N;
   for (int w = tid; w < E * N2; w += nth) {
     const int s = w / N2, l = w - s * N2;
@@ -133,7 +144,7 @@ __device__ __forceinline__ void sweepT(const T (&M)[N][N], const T* src, T* dst,
 #pragma unroll
       for (int t = 0; t < N; ++t) out[t] = pd[t * stride];
     }
-    matT_line<N, ACC>(M, in, out);
+    eo_line<N, ANTI, ACC>(M, in, out);
 #pragma unroll
     for (int t = 0; t < N; ++t) pd[t * stride] = out[t];
   }
@@ -291,6 +302,20 @@ __global__ void __launch_bounds__(kApplyThreads)
                    : "memory");
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   }
+  if (std::is_same<T, df>::value && !STAGE && !MASS_ONLY) {
+    // Bulk prefetch of the group's metric block (contiguous, 16-byte aligned, a
+    // multiple of 16 bytes) into L2, in 16 KB pieces: the quadrature-point stage
+    // reads it after the gather and two sweeps, and then hits L2.  Measured
+    // faster for the memory-latency-bound double-float kernel only (the FP64
+    // kernel is bound by the FP64 pipe, the FP32 ones stage the metric).
+    const int ne = min(E, a.nelem - e0);
+    const unsigned bytes = (unsigned)((size_t)ne * BLK * sizeof(MT));
+    const char* src = reinterpret_cast<const char*>(a.metric + (size_t)e0 * BLK);
+    for (unsigned off = (unsigned)tid * 16384u; off < bytes; off += (unsigned)nth * 16384u)
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(src + off),
+                   "r"(min(16384u, bytes - off))
+                   : "memory");
+  }
 
   // gather u_e = P_e u
   for (int idx = tid; idx < E * N3; idx += nth) {
@@ -300,11 +325,11 @@ __global__ void __launch_bounds__(kApplyThreads)
   group_sync();
 
   if (QUAD == SEM_QUAD_LG) {  // values at the Gauss points
-    sweep<N, E, 0>(tab.Bi, sA, sB, tid, nth);
+    sweep<N, E, 0, false, false>(tab.Bi, sA, sB, tid, nth);
     group_sync();
-    sweep<N, E, 1>(tab.Bi, sB, sC, tid, nth);
+    sweep<N, E, 1, false, false>(tab.Bi, sB, sC, tid, nth);
     group_sync();
-    sweep<N, E, 2>(tab.Bi, sC, sA, tid, nth);
+    sweep<N, E, 2, false, false>(tab.Bi, sC, sA, tid, nth);
     group_sync();
   }
 
@@ -319,8 +344,8 @@ __global__ void __launch_bounds__(kApplyThreads)
     group_sync();
   } else {
     // reference gradient along x and y (into sB, sC)
-    sweep<N, E, 0>(tab.D, sA, sB, tid, nth);
-    sweep<N, E, 1>(tab.D, sA, sC, tid, nth);
+    sweep<N, E, 0, true, false>(tab.D, sA, sB, tid, nth);
+    sweep<N, E, 1, true, false>(tab.D, sA, sC, tid, nth);
     if (STAGE) asm volatile("cp.async.wait_all;\n" ::: "memory");
     group_sync();
     // z-gradient, quadrature-point stage and transposed z-sweep on the columns
@@ -333,7 +358,7 @@ __global__ void __launch_bounds__(kApplyThreads)
       T uz[N], g3[N], q3[N], m[N];
 #pragma unroll
       for (int k = 0; k < N; ++k) uz[k] = pa[k * N2];
-      mat_line<N>(tab.D, uz, g3);
+      eo_line<N, true, false>(tab.D, uz, g3);
       const MT* mp = STAGE ? sM + (size_t)s * BLK + c * PS : a.metric + (size_t)e * BLK + c * PS;
 #pragma unroll
       for (int k = 0; k < N; ++k) {
@@ -347,23 +372,23 @@ __global__ void __launch_bounds__(kApplyThreads)
         q3[k] = fma(G22, g3[k], fma(G12, g2, G02 * g1));
         m[k] = (a.mass_coef * W) * uz[k];
       }
-      matT_line<N, true>(tab.D, q3, m);
+      eo_line<N, true, true>(tab.Dt, q3, m);
 #pragma unroll
       for (int k = 0; k < N; ++k) pa[k * N2] = m[k];
     }
     group_sync();
-    sweepT<N, E, 1, true>(tab.D, sC, sA, tid, nth);
+    sweep<N, E, 1, true, true>(tab.Dt, sC, sA, tid, nth);
     group_sync();
-    sweepT<N, E, 0, true>(tab.D, sB, sA, tid, nth);
+    sweep<N, E, 0, true, true>(tab.Dt, sB, sA, tid, nth);
     group_sync();
   }
 
   if (QUAD == SEM_QUAD_LG) {  // back from the Gauss points to the nodes
-    sweepT<N, E, 0, false>(tab.Bi, sA, sB, tid, nth);
+    sweep<N, E, 0, false, false>(tab.Bit, sA, sB, tid, nth);
     group_sync();
-    sweepT<N, E, 1, false>(tab.Bi, sB, sC, tid, nth);
+    sweep<N, E, 1, false, false>(tab.Bit, sB, sC, tid, nth);
     group_sync();
-    sweepT<N, E, 2, false>(tab.Bi, sC, sA, tid, nth);
+    sweep<N, E, 2, false, false>(tab.Bit, sC, sA, tid, nth);
     group_sync();
   }
 
@@ -495,10 +520,10 @@ __device__ __forceinline__ void pipe_issue(const ApplyArgs<float, MT>& a, int un
   }
 }
 
-// One 1-D line of n values at stride STRIDE: dst = M src (TRANS: M^T src;
-// ACC: dst += ...).  src may equal dst.
-template <int N, int STRIDE, bool TRANS, bool ACC, typename T>
-__device__ __forceinline__ void lane_line(const T (&M)[N][N], const T* src, T* dst, bool store) {
+// One 1-D line of n values at stride STRIDE: dst = M src (ACC: dst += M src),
+// M in even-odd form.  src may equal dst.
+template <int N, int STRIDE, bool ANTI, bool ACC, typename T>
+__device__ __forceinline__ void lane_line(const EoMat<N, T>& M, const T* src, T* dst, bool store) {
   T in[N], out[N];
 #pragma unroll
   for (int t = 0; t < N; ++t) in[t] = src[t * STRIDE];
@@ -506,8 +531,7 @@ __device__ __forceinline__ void lane_line(const T (&M)[N][N], const T* src, T* d
 #pragma unroll
     for (int t = 0; t < N; ++t) out[t] = dst[t * STRIDE];
   }
-  if (TRANS) matT_line<N, ACC>(M, in, out);
-  else mat_line<N>(M, in, out);
+  eo_line<N, ANTI, ACC>(M, in, out);
 #pragma unroll
   for (int t = 0; t < N; ++t)
     if (store) dst[t * STRIDE] = out[t];
@@ -568,8 +592,8 @@ __global__ void __launch_bounds__(kApplyThreads, 4)
       __syncwarp();
     }
     // reference gradient along x and y (into sB, sC)
-    lane_line<N, 1, false, false>(tab.D, sA + ox, sB + ox, act);
-    lane_line<N, N, false, false>(tab.D, sA + oy, sC + oy, act);
+    lane_line<N, 1, true, false>(tab.D, sA + ox, sB + ox, act);
+    lane_line<N, N, true, false>(tab.D, sA + oy, sC + oy, act);
     __syncwarp();
     // z-gradient, quadrature-point stage and transposed z-sweep on the lane's column
     {
@@ -579,7 +603,7 @@ __global__ void __launch_bounds__(kApplyThreads, 4)
       T uz[N], g3[N], q3[N], m[N];
 #pragma unroll
       for (int k = 0; k < N; ++k) uz[k] = pa[k * N2];
-      mat_line<N>(tab.D, uz, g3);
+      eo_line<N, true, false>(tab.D, uz, g3);
       const MT* mp = sM + mo;
 #pragma unroll
       for (int k = 0; k < N; ++k) {
@@ -596,22 +620,22 @@ __global__ void __launch_bounds__(kApplyThreads, 4)
         q3[k] = fma(G22, g3[k], fma(G12, g2, G02 * g1));
         m[k] = (a.mass_coef * W) * uz[k];
       }
-      matT_line<N, true>(tab.D, q3, m);
+      eo_line<N, true, true>(tab.Dt, q3, m);
 #pragma unroll
       for (int k = 0; k < N; ++k)
         if (act) pa[k * N2] = m[k];
     }
     __syncwarp();
-    lane_line<N, N, true, true>(tab.D, sC + oy, sA + oy, act);
+    lane_line<N, N, true, true>(tab.Dt, sC + oy, sA + oy, act);
     __syncwarp();
-    lane_line<N, 1, true, true>(tab.D, sB + ox, sA + ox, act);
+    lane_line<N, 1, true, true>(tab.Dt, sB + ox, sA + ox, act);
     __syncwarp();
     if (QUAD == SEM_QUAD_LG) {  // back from the Gauss points to the nodes
-      lane_line<N, 1, true, false>(tab.Bi, sA + ox, sB + ox, act);
+      lane_line<N, 1, false, false>(tab.Bit, sA + ox, sB + ox, act);
       __syncwarp();
-      lane_line<N, N, true, false>(tab.Bi, sB + oy, sC + oy, act);
+      lane_line<N, N, false, false>(tab.Bit, sB + oy, sC + oy, act);
       __syncwarp();
-      lane_line<N, N2, true, false>(tab.Bi, sC + oz, sA + oz, act);
+      lane_line<N, N2, false, false>(tab.Bit, sC + oz, sA + oz, act);
       __syncwarp();
     }
     // scatter-add y += P_e^T y_e
@@ -677,17 +701,35 @@ cudaError_t launch_apply_pipe(const Level& L, const ApplyArgs<float, MT>& a, con
   return cudaGetLastError();
 }
 
+// Even-odd form (EoMat) of the n x n matrix M (or of its transpose), from the
+// host tables; the mirrored rows are implied by the symmetry of M.
+template <int N, typename T>
+void make_eo(EoMat<N, T>& E, const double (&M)[kMaxN][kMaxN], bool transpose) {
+  constexpr int H = N / 2;
+  auto m = [&](int q, int l) { return transpose ? M[l][q] : M[q][l]; };
+  for (int q = 0; q < H; ++q) {
+    for (int l = 0; l < H; ++l) {
+      E.a[q][l] = (T)(0.5 * (m(q, l) + m(q, N - 1 - l)));
+      E.b[q][l] = (T)(0.5 * (m(q, l) - m(q, N - 1 - l)));
+    }
+    E.a[q][H] = (T)((N & 1) ? m(q, H) : 0.0);
+  }
+  for (int l = 0; l <= H; ++l) E.c[l] = (T)((N & 1) ? m(H, l) : 0.0);
+  if constexpr (EoMat<N, T>::kDirect)
+    for (int q = 0; q < N; ++q)
+      for (int l = 0; l < N; ++l) E.m[q][l] = (T)m(q, l);
+}
+
 // Launch helper shared by the precision-specific translation units.
 template <int P, int QUAD, typename T, typename MT>
 cudaError_t launch_apply_t(const Level& L, const ApplyArgs<T, MT>& a, bool mass_only, bool dot,
                            cudaStream_t s) {
   constexpr int N = P + 1;
   KTab<N, T> tab;
-  for (int q = 0; q < N; ++q)
-    for (int l = 0; l < N; ++l) {
-      tab.D[q][l] = (T)(QUAD == SEM_QUAD_LG ? L.tab.Dg[q][l] : L.tab.D[q][l]);
-      tab.Bi[q][l] = (T)L.tab.Bi[q][l];
-    }
+  make_eo(tab.D, QUAD == SEM_QUAD_LG ? L.tab.Dg : L.tab.D, false);
+  make_eo(tab.Dt, QUAD == SEM_QUAD_LG ? L.tab.Dg : L.tab.D, true);
+  make_eo(tab.Bi, L.tab.Bi, false);
+  make_eo(tab.Bit, L.tab.Bi, true);
   const int E = ApplyCfg<P>::E;
   const int grid = (L.nelem + E - 1) / E;
   if (grid == 0) return cudaSuccess;

@@ -51,13 +51,33 @@ struct Tables1D {
 // Builds the tables of degree p (1..kMaxP) for quad SEM_QUAD_LG / SEM_QUAD_LGL.
 void build_tables(int p, int quad, Tables1D* t);
 
+// Even-odd form of an n x n matrix M with M[n-1-q][n-1-l] = s M[q][l]: s = -1
+// for a derivative matrix on points symmetric about 0 (and its transpose),
+// s = +1 for interpolation between two symmetric point sets.  With H = n / 2,
+// for q, l < H:
+//   a[q][l] = (M[q][l] + M[q][n-1-l]) / 2,   b[q][l] = (M[q][l] - M[q][n-1-l]) / 2,
+// and for odd n the middle column a[q][H] = M[q][H] and the middle row
+// c[l] = M[H][l] (l <= H).  A product y = M x then takes about half the
+// multiplications (see eo_line).  For n = 2 and 4 the split saves no
+// multiplication, so the matrix itself (m) is kept and multiplied directly.
+template <int N, typename T>
+struct EoMat {
+  static constexpr int H = N / 2;
+  static constexpr bool kDirect = (N == 2 || N == 4);
+  static constexpr int NM = kDirect ? N : 1;
+  T a[H][H + 1];
+  T b[H][H];
+  T c[H + 1];
+  T m[NM][NM];
+};
+
 // Tables in the kernel's arithmetic type, passed to kernels by value (kernel
 // parameter space): accesses with compile-time indices become constant-bank
 // operands of the FMA instructions.
 template <int N, typename T>
 struct KTab {
-  T D[N][N];   // derivative matrix used for the gradient (D for SEM-NI, Dg for SEM)
-  T Bi[N][N];  // interpolation GLL -> quadrature points (SEM only)
+  EoMat<N, T> D, Dt;    // derivative matrix of the gradient (D for SEM-NI, Dg for SEM), its transpose
+  EoMat<N, T> Bi, Bit;  // interpolation GLL -> quadrature points (SEM only), its transpose
 };
 
 // Deterministic grid reductions: every block writes a partial, the last block
