@@ -344,17 +344,23 @@ def run_gpu(args):
                                                 else kernels["smoother_apply"]["algorithmic_bytes_per_launch"])
 
     # end to end through the public C ABI with host buffers (page-locked), one
-    # step per call, continuing from the device state reached above
+    # step per call, continuing from the device state reached above: each call
+    # reads u^n, u^{n-1}, h^n, h^{n-1} from host memory and writes u^{n+1},
+    # h^{n+1} to host memory; the caller rotates three host arrays per field
     ck = state.checkpoint()
-    hu, hup = ck["u"].cpu().pin_memory(), ck["u_prev"].cpu().pin_memory()
-    hh, hhp = ck["h"].cpu().pin_memory(), ck["h_prev"].cpu().pin_memory()
+    hu = [ck["u_prev"].cpu().pin_memory(), ck["u"].cpu().pin_memory(),
+          torch.empty(n_d, dtype=torch.float64).pin_memory()]
+    hh = [ck["h_prev"].cpu().pin_memory(), ck["h"].cpu().pin_memory(),
+          torch.empty(n_d, dtype=torch.float64).pin_memory()]
     n2 = ck["n"]
     n_e2e = max(1, min(args.steps, 10))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(n_e2e):
-        capi.sem_step_host(slab.ctx, hu, hup, hh, hhp, n2 + k, DT, RTOL, 0.0, MAXIT,
-                           gb.SEM_PC_JACOBI if args.arms == "fp64" else gb.SEM_PC_GMG)
+        capi.sem_step_host_out(slab.ctx, hu[1], hu[0], hh[1], hh[0], hu[2], hh[2], n2 + k, DT, RTOL, 0.0,
+                               MAXIT, gb.SEM_PC_JACOBI if args.arms == "fp64" else gb.SEM_PC_GMG)
+        hu = [hu[1], hu[2], hu[0]]
+        hh = [hh[1], hh[2], hh[0]]
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e_value = n_d * n_e2e / e2e_s / 1e9 * ws
@@ -416,7 +422,8 @@ def run_gpu(args):
                                 "unit": "TFLOP/s", "frac": flops / (apply64_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
                                 "traffic": NCU_TRAFFIC.get((p, quad))} if args.arms != "mixed" else None,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * 8 * n_d,
-                "d2h_bytes_per_step": 4 * 8 * n_d, "steps": n_e2e},
+                "d2h_bytes_per_step": 2 * 8 * n_d, "steps": n_e2e,
+                "call": "sem_step_host_out (page-locked host arrays, rotated by the caller)"},
         "gpu_launches": int(stats.kernel_launches),
         "clocks": clk,
         "cpu_baseline": cpu,

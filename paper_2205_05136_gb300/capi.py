@@ -45,7 +45,7 @@ EXPORTS = [
     "sem_version", "sem_create", "sem_destroy", "sem_last_error", "sem_num_dofs",
     "sem_num_elements", "sem_dof_coords", "sem_set_tissue", "sem_apply", "sem_diagonal",
     "sem_cg_solve", "sem_set_ionic", "sem_set_stimulus", "sem_state_create", "sem_state_destroy",
-    "sem_state_set", "sem_state_get", "sem_state_restore", "sem_step", "sem_step_host",
+    "sem_state_set", "sem_state_get", "sem_state_restore", "sem_step", "sem_step_host", "sem_step_host_out",
     "sem_set_timing", "sem_apply_dot_static", "sem_set_gmg", "sem_vcycle", "sem_gmg_info",
     "sem_forward_record", "sem_adjoint_grad", "sem_set_operator_precision",
 ]
@@ -106,6 +106,8 @@ def lib():
             "sem_step": (_I, [_P, _P, _D, _I, _D, _D, _I, _I, ctypes.POINTER(sem_stats), _P]),
             "sem_step_host": (_I, [_P, _P, _P, _P, _P, _I64, _D, _D, _D, _I, _I,
                                    ctypes.POINTER(sem_stats), _P]),
+            "sem_step_host_out": (_I, [_P, _P, _P, _P, _P, _P, _P, _I64, _D, _D, _D, _I, _I,
+                                       ctypes.POINTER(sem_stats), _P]),
             "sem_set_timing": (_I, [_P, _I]),
             "sem_apply_dot_static": (_I, [_P, _D, _D, _P, _P, _P, _P]),
             "sem_set_gmg": (_I, [_P, _I, _I, _I, _I]),
@@ -285,6 +287,23 @@ def sem_step_host(ctx, u, u_prev, h, h_prev, n, dt, rtol, atol, maxit, precond=S
     _check(lib().sem_step_host(ctx, _P(u.data_ptr()), _P(u_prev.data_ptr()), _P(h.data_ptr()),
                                _P(h_prev.data_ptr()), int(n), float(dt), float(rtol), float(atol),
                                int(maxit), int(precond), ctypes.byref(stats), _stream(stream)), ctx)
+    return stats
+
+
+def sem_step_host_out(ctx, u, u_prev, h, h_prev, u_next, h_next, n, dt, rtol, atol, maxit,
+                      precond=SEM_PC_JACOBI, stream=None):
+    """Inputs u, u_prev, h, h_prev and outputs u_next, h_next: contiguous float64
+    CPU tensors (page-locked ones are read and written by the device in place)."""
+    nd = sem_num_dofs(ctx)
+    for t, name in ((u, "u"), (u_prev, "u_prev"), (h, "h"), (h_prev, "h_prev"),
+                    (u_next, "u_next"), (h_next, "h_next")):
+        if t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous() or t.numel() != nd:
+            raise TypeError(f"{name} must be a contiguous float64 CPU tensor of {nd} entries")
+    stats = sem_stats()
+    _check(lib().sem_step_host_out(ctx, _P(u.data_ptr()), _P(u_prev.data_ptr()), _P(h.data_ptr()),
+                                   _P(h_prev.data_ptr()), _P(u_next.data_ptr()), _P(h_next.data_ptr()),
+                                   int(n), float(dt), float(rtol), float(atol), int(maxit), int(precond),
+                                   ctypes.byref(stats), _stream(stream)), ctx)
     return stats
 
 

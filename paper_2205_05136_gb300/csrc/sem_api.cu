@@ -472,6 +472,72 @@ int sem_step_host(sem_ctx* ctx, double* u, double* u_prev, double* h, double* h_
   return SEM_OK;
 }
 
+namespace {
+// Device address of page-locked host memory (mapped into the device's address
+// space), or nullptr for pageable memory.
+double* mapped_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? static_cast<double*>(at.devicePointer) : nullptr;
+}
+
+bool overlaps(const void* a, const void* b, size_t bytes) {
+  const char* x = static_cast<const char*>(a);
+  const char* y = static_cast<const char*>(b);
+  return x < y + bytes && y < x + bytes;
+}
+}  // namespace
+
+int sem_step_host_out(sem_ctx* ctx, const double* u, const double* u_prev, const double* h,
+                      const double* h_prev, double* u_next, double* h_next, int64_t n, double dt,
+                      double rtol, double atol, int maxit, int precond, sem_stats* stats, void* stream) {
+  CK_CTX(ctx);
+  DeviceGuard guard(ctx->device);
+  const void* all[6] = {u, u_prev, h, h_prev, u_next, h_next};
+  for (const void* p : all)
+    if (!is_host_ptr(p)) return fail(ctx, SEM_ERR_ARG, "u, u_prev, h, h_prev, u_next, h_next must be host memory");
+  if (n < 0) return fail(ctx, SEM_ERR_ARG, "n must be >= 0");
+  const size_t bytes = sizeof(double) * ctx->L.ndofs;
+  for (int o = 4; o < 6; ++o)
+    for (int i = 0; i < 6; ++i)
+      if (i != o && overlaps(all[o], all[i], bytes))
+        return fail(ctx, SEM_ERR_ARG, "u_next and h_next must not overlap any other array");
+  if (ctx->host_state == nullptr) {
+    int rc = sem_state_create(ctx, &ctx->host_state);
+    if (rc != SEM_OK) return rc;
+  }
+  sem_state* st = ctx->host_state;
+  cudaStream_t s = as_stream(stream);
+  // Page-locked inputs are read in place by the ionic update (over the host
+  // link, while it computes) and h^{n+1} is written straight to h_next; pageable
+  // arrays are staged through the state's device buffers.
+  sem_state view = *st;
+  view.cur = 0; view.prev = 1; view.next = 2; view.n = n;
+  const double* in[4] = {u, u_prev, h, h_prev};
+  double* dev_in[4] = {st->U[0], st->U[1], st->H[0], st->H[1]};
+  double* use[4];
+  for (int i = 0; i < 4; ++i) {
+    use[i] = mapped_ptr(in[i]);
+    if (use[i] == nullptr) {
+      SEM_CK(cudaMemcpyAsync(dev_in[i], in[i], bytes, cudaMemcpyHostToDevice, s));
+      use[i] = dev_in[i];
+    }
+  }
+  view.U[0] = use[0]; view.U[1] = use[1]; view.H[0] = use[2]; view.H[1] = use[3];
+  double* h_out = mapped_ptr(h_next);
+  view.H[2] = h_out ? h_out : st->H[2];
+  view.U[2] = st->U[2];
+  int rc = sem_step(ctx, &view, dt, 1, rtol, atol, maxit, precond, stats, stream);
+  if (rc != SEM_OK) return rc;
+  SEM_CK(cudaMemcpyAsync(u_next, st->U[2], bytes, cudaMemcpyDeviceToHost, s));
+  if (h_out == nullptr) SEM_CK(cudaMemcpyAsync(h_next, st->H[2], bytes, cudaMemcpyDeviceToHost, s));
+  SEM_CK(cudaStreamSynchronize(s));
+  return SEM_OK;
+}
+
 int sem_set_gmg(sem_ctx* ctx, int degree, int coarse_degree, int min_coarse_dofs, int precision) {
   CK_CTX(ctx);
   if (degree < 1 || degree > 20 || coarse_degree < 1 || coarse_degree > 200 || min_coarse_dofs < 1)

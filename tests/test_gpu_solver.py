@@ -160,6 +160,38 @@ def test_step_host_matches_device_step():
     assert rel(u.numpy(), ud.cpu().numpy()) < 1e-13 and rel(h.numpy(), hd.cpu().numpy()) < 1e-13
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+def test_step_host_out_matches_device_step(pinned):
+    """Separate output arrays, rotated by the caller; page-locked arrays are read and
+    written by the device in place, pageable ones are staged by copies."""
+    s, tissue, g, o = _small(2, "LGL")
+    g.set_ionic()
+    g.set_stimulus("box", (0, 0, 0, 1.5, 1.5, 1.5), 50.0, 0.0, 1.0)
+    st = g.new_state(-85.0, 1.0)
+    st.step(0.05, 4, rtol=1e-12)
+    ud, hd, _ = st.get()
+
+    def arr(v):
+        t = torch.full((o.ndofs,), v, dtype=torch.float64)
+        return t.pin_memory() if pinned else t
+
+    us = [arr(-85.0), arr(-85.0), arr(0.0)]  # u^{n-1}, u^n, free
+    hs = [arr(1.0), arr(1.0), arr(0.0)]
+    for n in range(4):
+        before = (us[0].clone(), us[1].clone(), hs[0].clone(), hs[1].clone())
+        capi.sem_step_host_out(g.ctx, us[1], us[0], hs[1], hs[0], us[2], hs[2], n, 0.05, 1e-12, 0.0, 1000)
+        # the inputs are not modified
+        assert torch.equal(before[0], us[0]) and torch.equal(before[1], us[1])
+        assert torch.equal(before[2], hs[0]) and torch.equal(before[3], hs[1])
+        us = [us[1], us[2], us[0]]
+        hs = [hs[1], hs[2], hs[0]]
+    torch.cuda.synchronize()
+    assert rel(us[1].numpy(), ud.cpu().numpy()) < 1e-13 and rel(hs[1].numpy(), hd.cpu().numpy()) < 1e-13
+    # an output that overlaps an input is refused
+    with pytest.raises(capi.SemError):
+        capi.sem_step_host_out(g.ctx, us[1], us[0], hs[1], hs[0], us[1], hs[2], 4, 0.05, 1e-12, 0.0, 1000)
+
+
 def test_checkpoint_restore_resumes_identically():
     s, tissue, g, o = _small(2, "LGL")
     g.set_ionic()
