@@ -510,10 +510,13 @@ def _slab_ctx(gb, s, p, quad, tissue, dev=0):
 
 
 def run_gmg8m(args):
-    """Full FP64-accurate monodomain run on a 40 x 20 x 6 mm slab at p = 4
-    (128 x 64 x 16 elements, 8.57 M DOFs), rotating fibres, 200 steps of
-    0.05 ms (10 ms), seeded stimulus ball r = 1.5 mm; flexible FP64 PCG with the
-    p-then-h multigrid (Chebyshev 3) in FP32."""
+    """Monodomain run on a 40 x 20 x 6 mm slab at p = 4 (128 x 64 x 16 elements,
+    8.57 M DOFs), rotating fibres, 200 steps of 0.05 ms (10 ms), seeded stimulus
+    ball r = 1.5 mm, flexible PCG with the p-then-h multigrid (p 4 -> 2 -> 1, then
+    h-levels down to 2,000 nodes; Chebyshev 3, coarsest level Chebyshev 10), in two
+    arms on the same hierarchy: all FP64 (operator and V-cycle), and mixed
+    (double-float outer operator, bf16-metric FP32 V-cycle); relative L2 / Linf
+    differences of u and h between the two after the run."""
     import torch
     import paper_2205_05136_gb300 as gb
     from paper_2205_05136_gb300 import build as gbuild, capi
@@ -524,31 +527,41 @@ def run_gmg8m(args):
     slab = _slab_ctx(gb, s, 4, args.quad, tissue)
     centre = W.seeded_point(s.lengths, STIM_RADIUS, seed=W.SEED_STIM)
     slab.set_stimulus("sphere", (*centre, STIM_RADIUS), STIM_AMP, 0.0, STIM_T_OFF)
-    capi.sem_set_gmg(slab.ctx, 3, 10, 2000, gb.SEM_PREC_FP32)
-    info = capi.sem_gmg_info(slab.ctx, 1.5 / DT)
     slab.set_timing(True)
     nsteps = args.steps if args.steps != 20 else 200
-    st = slab.new_state(-85.0, 1.0)
-    st.step(DT, 3, rtol=RTOL, maxit=MAXIT, precond=gb.SEM_PC_GMG)
-    st.restore({"u": torch.full((slab.ndofs,), -85.0, dtype=torch.float64, device="cuda"),
-                "u_prev": torch.full((slab.ndofs,), -85.0, dtype=torch.float64, device="cuda"),
-                "h": torch.ones(slab.ndofs, dtype=torch.float64, device="cuda"),
-                "h_prev": torch.ones(slab.ndofs, dtype=torch.float64, device="cuda"), "n": 0})
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    stats = st.step(DT, nsteps, rtol=RTOL, maxit=MAXIT, precond=gb.SEM_PC_GMG)
-    torch.cuda.synchronize()
-    el = time.perf_counter() - t0
-    u, h, n = st.get()
-    print(json.dumps({
-        "workload": "gmg8m: 40x20x6 mm slab, 128x64x16 Q4 elements, 10 ms of activation",
-        "ndofs": slab.ndofs, "steps": nsteps, "seconds": el, "steps_per_s": nsteps / el,
-        "gdof_steps_per_s": slab.ndofs * nsteps / el / 1e9,
-        "cg_iters_per_step": stats.cg_iters / nsteps,
-        "levels": {"p": info["p"], "dims": info["dims"], "ndofs": info["ndofs"]},
-        "u_max_mV": float(u.max()), "activated_fraction": float((u > -40.0).double().mean()),
-        "apply_ms": stats.apply_ms / max(stats.n_apply, 1)}), flush=True)
-    st.close()
+    out = {"workload": "gmg8m: 40x20x6 mm slab, 128x64x16 Q4 elements, 10 ms of activation",
+           "ndofs": slab.ndofs, "steps": nsteps}
+    finals = {}
+    for name, op, prec in (("fp64", gb.SEM_PREC_FP64, gb.SEM_PREC_FP64),
+                           ("mixed", gb.SEM_PREC_DF64, gb.SEM_PREC_FP32_BF16)):
+        capi.sem_set_operator_precision(slab.ctx, op)
+        capi.sem_set_gmg(slab.ctx, 3, 10, 2000, prec)
+        info = capi.sem_gmg_info(slab.ctx, 1.5 / DT)
+        st = slab.new_state(-85.0, 1.0)
+        st.step(DT, 3, rtol=RTOL, maxit=MAXIT, precond=gb.SEM_PC_GMG)
+        st.restore({"u": torch.full((slab.ndofs,), -85.0, dtype=torch.float64, device="cuda"),
+                    "u_prev": torch.full((slab.ndofs,), -85.0, dtype=torch.float64, device="cuda"),
+                    "h": torch.ones(slab.ndofs, dtype=torch.float64, device="cuda"),
+                    "h_prev": torch.ones(slab.ndofs, dtype=torch.float64, device="cuda"), "n": 0})
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        stats = st.step(DT, nsteps, rtol=RTOL, maxit=MAXIT, precond=gb.SEM_PC_GMG)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        u, h, n = st.get()
+        finals[name] = (u, h)
+        out["levels"] = {"p": info["p"], "dims": info["dims"], "ndofs": info["ndofs"]}
+        out[name] = {"seconds": el, "steps_per_s": nsteps / el, "gdof_steps_per_s": slab.ndofs * nsteps / el / 1e9,
+                     "cg_iters_per_step": stats.cg_iters / nsteps,
+                     "u_max_mV": float(u.max()), "activated_fraction": float((u > -40.0).double().mean()),
+                     "outer_apply_ms": stats.apply_ms / max(stats.n_apply, 1)}
+        st.close()
+    (u64, h64), (umx, hmx) = finals["fp64"], finals["mixed"]
+    out["mixed"]["u_rel_l2_vs_fp64"] = float(torch.linalg.norm(umx - u64) / torch.linalg.norm(u64))
+    out["mixed"]["u_rel_linf_vs_fp64"] = float((umx - u64).abs().max() / u64.abs().max())
+    out["mixed"]["h_rel_l2_vs_fp64"] = float(torch.linalg.norm(hmx - h64) / torch.linalg.norm(h64))
+    out["mixed"]["speedup_vs_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    print(json.dumps(out), flush=True)
     slab.close()
 
 
@@ -585,11 +598,17 @@ def run_mixed30m(args):
                "apply_rel_err_fp64_vs_oracle_sampled": op_err,
                "apply_rel_l2_fp32_vs_fp64": rel(y32, y64), "apply_rel_l2_bf16_vs_fp64": rel(y16, y64)}
         results = {}
+        # the FP32- and bf16-metric V-cycles under the FP64 outer CG (Chebyshev 3), and the
+        # fastest configuration of the 2 M DOF benchmark: double-float outer operator,
+        # bf16-metric V-cycle, Chebyshev 6, coarsening down to 300,000 nodes
         for name, pc, prec in (("fp64_jacobi", gb.SEM_PC_JACOBI, None),
                                ("gmg_fp32", gb.SEM_PC_GMG, gb.SEM_PREC_FP32),
-                               ("gmg_bf16", gb.SEM_PC_GMG, gb.SEM_PREC_FP32_BF16)):
+                               ("gmg_bf16", gb.SEM_PC_GMG, gb.SEM_PREC_FP32_BF16),
+                               ("gmg_bf16_df64_cheb6", gb.SEM_PC_GMG, gb.SEM_PREC_FP32_BF16)):
+            tuned = name.endswith("cheb6")
+            capi.sem_set_operator_precision(slab.ctx, gb.SEM_PREC_DF64 if tuned else gb.SEM_PREC_FP64)
             if prec is not None:
-                capi.sem_set_gmg(slab.ctx, 3, 8, 40000, prec)
+                capi.sem_set_gmg(slab.ctx, 6 if tuned else 3, 6 if tuned else 8, 300000 if tuned else 40000, prec)
             st = slab.new_state(-85.0, 1.0)
             st.step(DT, 1, rtol=RTOL, maxit=MAXIT * 4, precond=pc)  # warm-up (BDF1)
             torch.cuda.synchronize()
@@ -602,7 +621,7 @@ def run_mixed30m(args):
             out[name] = {"ms_per_step": el / nsteps * 1e3, "cg_iters_per_step": stt.cg_iters / nsteps}
             st.close()
         u64, h64 = results["fp64_jacobi"]
-        for name in ("gmg_fp32", "gmg_bf16"):
+        for name in ("gmg_fp32", "gmg_bf16", "gmg_bf16_df64_cheb6"):
             u, h = results[name]
             out[name]["u_rel_l2"] = float(torch.linalg.norm(u - u64) / torch.linalg.norm(u64))
             out[name]["u_rel_linf"] = float((u - u64).abs().max() / u64.abs().max())
