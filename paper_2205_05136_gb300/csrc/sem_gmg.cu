@@ -93,11 +93,36 @@ int grid1d(int64_t n) {
 
 __device__ __forceinline__ bool skip(const int* done) { return done != nullptr && *done; }
 
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
 // ---------------------------------------------------------------- vectors
+// Streaming vector kernels: consecutive entries are handled in 16-byte groups
+// (4 floats or 2 doubles) by vector loads and stores, which keeps enough bytes
+// in flight per thread to stream at HBM speed; the remaining n % K entries go
+// one by one.  Level and workspace vectors come from cudaMalloc (256-byte
+// aligned); kernels that also touch a caller's vector take a VEC flag that the
+// host sets from the pointers' alignment.
+template <typename T, int K>
+struct alignas(K * sizeof(T)) Pk {
+  T e[K];
+};
+template <typename T>
+__host__ __device__ constexpr int k16() { return 16 / (int)sizeof(T); }
+
+#define GRID_CHUNKS(c, nc)                                                         \
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < (nc);     \
+       c += (int64_t)gridDim.x * blockDim.x)
+#define GRID_TAIL(i, start, n)                                                     \
+  for (int64_t i = (start) + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); \
+       i += (int64_t)gridDim.x * blockDim.x)
+
 template <typename T>
 __global__ void k_zero(int64_t n, T* x, const int* done) {
   if (skip(done)) return;
-  GRID_LOOP(i, n) x[i] = T(0);
+  constexpr int K = k16<T>();
+  const int64_t nc = n / K;
+  GRID_CHUNKS(c, nc) reinterpret_cast<Pk<T, K>*>(x)[c] = Pk<T, K>{};
+  GRID_TAIL(i, nc * K, n) x[i] = T(0);
 }
 
 template <typename T>
@@ -116,7 +141,19 @@ __global__ void k_cheb_zero_start(int64_t n, const T* __restrict__ b, const T* _
                                   T* __restrict__ x, T* __restrict__ d, T* __restrict__ t,
                                   T inv_theta, const int* done) {
   if (skip(done)) return;
-  GRID_LOOP(i, n) {
+  constexpr int K = k16<T>();
+  using V = Pk<T, K>;
+  const int64_t nc = n / K;
+  GRID_CHUNKS(c, nc) {
+    const V bb = reinterpret_cast<const V*>(b)[c], ii = reinterpret_cast<const V*>(invd)[c];
+    V dd;
+#pragma unroll
+    for (int k = 0; k < K; ++k) dd.e[k] = ii.e[k] * bb.e[k] * inv_theta;
+    reinterpret_cast<V*>(d)[c] = dd;
+    reinterpret_cast<V*>(x)[c] = dd;
+    reinterpret_cast<V*>(t)[c] = V{};
+  }
+  GRID_TAIL(i, nc * K, n) {
     const T di = invd[i] * b[i] * inv_theta;
     d[i] = di;
     x[i] = di;
@@ -127,13 +164,35 @@ __global__ void k_cheb_zero_start(int64_t n, const T* __restrict__ b, const T* _
 // Chebyshev step with t = A x: d = c1 d + c2 D^{-1}(b - t), x += d, t = 0
 // (first: d = c2 D^{-1}(b - t)).
 template <typename T>
+__device__ __forceinline__ T cheb_d(T b, T t, T invd, T d, T c1, T c2, bool first) {
+  const T ri = b - t;
+  return first ? c2 * invd * ri : fma(c1, d, c2 * invd * ri);
+}
+
+template <typename T>
 __global__ void k_cheb_step(int64_t n, const T* __restrict__ b, const T* __restrict__ invd,
                             T* __restrict__ x, T* __restrict__ d, T* __restrict__ t, T c1, T c2,
                             int first, const int* done) {
   if (skip(done)) return;
-  GRID_LOOP(i, n) {
-    const T ri = b[i] - t[i];
-    const T di = first ? c2 * invd[i] * ri : fma(c1, d[i], c2 * invd[i] * ri);
+  constexpr int K = k16<T>();
+  using V = Pk<T, K>;
+  const int64_t nc = n / K;
+  GRID_CHUNKS(c, nc) {
+    const V bb = reinterpret_cast<const V*>(b)[c], tt = reinterpret_cast<const V*>(t)[c];
+    const V ii = reinterpret_cast<const V*>(invd)[c];
+    V xx = reinterpret_cast<const V*>(x)[c];
+    V dd = first ? V{} : reinterpret_cast<const V*>(d)[c];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      dd.e[k] = cheb_d(bb.e[k], tt.e[k], ii.e[k], dd.e[k], c1, c2, first != 0);
+      xx.e[k] += dd.e[k];
+    }
+    reinterpret_cast<V*>(d)[c] = dd;
+    reinterpret_cast<V*>(x)[c] = xx;
+    reinterpret_cast<V*>(t)[c] = V{};
+  }
+  GRID_TAIL(i, nc * K, n) {
+    const T di = cheb_d(b[i], t[i], invd[i], first ? T(0) : d[i], c1, c2, first != 0);
     d[i] = di;
     x[i] += di;
     t[i] = T(0);
@@ -291,14 +350,32 @@ __device__ __forceinline__ bool grid_sums_k(double (&v)[K], double* partials, in
   return threadIdx.x == 0;
 }
 
-// r = b - Ap, Ap = 0, b0 = (T) r; r.r, b.b; stopping threshold.
-template <typename T>
+// r = b - Ap, Ap = 0, b0 = (T) r; r.r, b.b; stopping threshold.  VEC: b is
+// 16-byte aligned (pairs of entries by 16-byte accesses).
+template <typename T, bool VEC>
 __global__ void k_fpcg_init(int64_t n, const double* __restrict__ b, double* __restrict__ Ap,
                             double* __restrict__ r, T* __restrict__ b0, CgScalars* cg,
                             double* partials, int stride, unsigned int* ticket, double rtol,
                             double atol) {
   double v[2] = {0.0, 0.0};
-  GRID_LOOP(i, n) {
+  const int64_t nc = VEC ? n / 2 : 0;
+  GRID_CHUNKS(c, nc) {
+    const Pk<double, 2> bb = reinterpret_cast<const Pk<double, 2>*>(b)[c];
+    const Pk<double, 2> aa = reinterpret_cast<const Pk<double, 2>*>(Ap)[c];
+    Pk<double, 2> rr;
+    Pk<T, 2> rb;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      rr.e[k] = bb.e[k] - aa.e[k];
+      rb.e[k] = (T)rr.e[k];
+      v[0] = fma(rr.e[k], rr.e[k], v[0]);
+      v[1] = fma(bb.e[k], bb.e[k], v[1]);
+    }
+    reinterpret_cast<Pk<double, 2>*>(r)[c] = rr;
+    reinterpret_cast<Pk<double, 2>*>(Ap)[c] = Pk<double, 2>{};
+    reinterpret_cast<Pk<T, 2>*>(b0)[c] = rb;
+  }
+  GRID_TAIL(i, nc * 2, n) {
     const double bi = b[i];
     const double ri = bi - Ap[i];
     r[i] = ri;
@@ -322,7 +399,7 @@ __global__ void k_fpcg_init(int64_t n, const double* __restrict__ b, double* __r
 
 // z_new = (double) x0; first iteration (no iteration finished yet): p = z_new,
 // rz = r.z_new; else beta = (r.z_new - r.z_old) / rz, rz = r.z_new (z holds
-// z_old on entry).
+// z_old on entry).  Pairs of entries by 16-byte (8-byte for float x0) accesses.
 template <typename T>
 __global__ void k_fpcg_z(int64_t n, const T* __restrict__ x0, double* __restrict__ z,
                          const double* __restrict__ r, double* __restrict__ p, CgScalars* cg,
@@ -330,7 +407,23 @@ __global__ void k_fpcg_z(int64_t n, const T* __restrict__ x0, double* __restrict
   if (cg->done) return;
   const bool first = cg->iters == 0;
   double v[2] = {0.0, 0.0};
-  GRID_LOOP(i, n) {
+  using D2 = Pk<double, 2>;
+  const int64_t nc = n / 2;
+  GRID_CHUNKS(c, nc) {
+    const Pk<T, 2> xx = reinterpret_cast<const Pk<T, 2>*>(x0)[c];
+    const D2 rr = reinterpret_cast<const D2*>(r)[c];
+    const D2 zo = first ? D2{} : reinterpret_cast<const D2*>(z)[c];
+    D2 zn;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      zn.e[k] = (double)xx.e[k];
+      if (!first) v[1] = fma(rr.e[k], zo.e[k], v[1]);
+      v[0] = fma(rr.e[k], zn.e[k], v[0]);
+    }
+    if (first) reinterpret_cast<D2*>(p)[c] = zn;
+    reinterpret_cast<D2*>(z)[c] = zn;
+  }
+  GRID_TAIL(i, nc * 2, n) {
     const double zi = (double)x0[i];
     const double ri = r[i];
     if (first) {
@@ -360,18 +453,48 @@ __global__ void k_fpcg_p(int64_t n, const double* __restrict__ z, double* __rest
                          const CgScalars* cg) {
   if (cg->done || cg->iters == 0) return;  // first iteration: k_fpcg_z set p = z
   const double beta = cg->beta;
-  GRID_LOOP(i, n) p[i] = fma(beta, p[i], z[i]);
+  using D2 = Pk<double, 2>;
+  const int64_t nc = n / 2;
+  GRID_CHUNKS(c, nc) {
+    const D2 zz = reinterpret_cast<const D2*>(z)[c];
+    D2 pp = reinterpret_cast<const D2*>(p)[c];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) pp.e[k] = fma(beta, pp.e[k], zz.e[k]);
+    reinterpret_cast<D2*>(p)[c] = pp;
+  }
+  GRID_TAIL(i, nc * 2, n) p[i] = fma(beta, p[i], z[i]);
 }
 
-// x += alpha p, r -= alpha Ap, Ap = 0, b0 = (T) r; r.r; convergence.
-template <typename T>
+// x += alpha p, r -= alpha Ap, Ap = 0, b0 = (T) r; r.r; convergence.  VEC: x is
+// 16-byte aligned.
+template <typename T, bool VEC>
 __global__ void k_fpcg_xr(int64_t n, double* __restrict__ x, const double* __restrict__ p,
                           double* __restrict__ Ap, double* __restrict__ r, T* __restrict__ b0,
                           CgScalars* cg, double* partials, int stride, unsigned int* ticket) {
   if (cg->done) return;
   const double alpha = cg->alpha;
   double v[1] = {0.0};
-  GRID_LOOP(i, n) {
+  using D2 = Pk<double, 2>;
+  const int64_t nc = VEC ? n / 2 : 0;
+  GRID_CHUNKS(c, nc) {
+    D2 xx = reinterpret_cast<const D2*>(x)[c];
+    const D2 pp = reinterpret_cast<const D2*>(p)[c];
+    const D2 aa = reinterpret_cast<const D2*>(Ap)[c];
+    D2 rr = reinterpret_cast<const D2*>(r)[c];
+    Pk<T, 2> rb;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      xx.e[k] = fma(alpha, pp.e[k], xx.e[k]);
+      rr.e[k] = fma(-alpha, aa.e[k], rr.e[k]);
+      rb.e[k] = (T)rr.e[k];
+      v[0] = fma(rr.e[k], rr.e[k], v[0]);
+    }
+    reinterpret_cast<D2*>(x)[c] = xx;
+    reinterpret_cast<D2*>(r)[c] = rr;
+    reinterpret_cast<D2*>(Ap)[c] = D2{};
+    reinterpret_cast<Pk<T, 2>*>(b0)[c] = rb;
+  }
+  GRID_TAIL(i, nc * 2, n) {
     x[i] = fma(alpha, p[i], x[i]);
     const double ri = fma(-alpha, Ap[i], r[i]);
     r[i] = ri;
@@ -833,8 +956,12 @@ int pcg_init_seq(sem_ctx* ctx, Gmg& g, double alpha, const double* b, const doub
     a.mass_coef = alpha; a.out_scale = 1.0; a.scale_out = 0;
     GMG_CK(launch_operator(ctx, a, s));
   }
-  k_fpcg_init<T><<<gr, kThreads, 0, s>>>(n, b, w.Ap, w.r, b0, w.cg, g.partials, stride, g.tickets,
-                                         rtol, atol);
+  if (aligned16(b))
+    k_fpcg_init<T, true><<<gr, kThreads, 0, s>>>(n, b, w.Ap, w.r, b0, w.cg, g.partials, stride, g.tickets,
+                                               rtol, atol);
+  else
+    k_fpcg_init<T, false><<<gr, kThreads, 0, s>>>(n, b, w.Ap, w.r, b0, w.cg, g.partials, stride, g.tickets,
+                                                rtol, atol);
   GMG_CK(cudaGetLastError());
   return SEM_OK;
 }
@@ -861,8 +988,12 @@ int pcg_iter_seq(sem_ctx* ctx, Gmg& g, double alpha, double* x, cudaStream_t s) 
   GMG_CK(cudaEventRecordWithFlags(g.ev0, s, cudaEventRecordExternal));
   GMG_CK(launch_operator(ctx, ap, s));
   GMG_CK(cudaEventRecordWithFlags(g.ev1, s, cudaEventRecordExternal));
-  k_fpcg_xr<T><<<gr, kThreads, 0, s>>>(n, x, w.p, w.Ap, w.r, (T*)g.lv[0].b, w.cg, g.partials,
-                                       stride, g.tickets + 2);
+  if (aligned16(x))
+    k_fpcg_xr<T, true><<<gr, kThreads, 0, s>>>(n, x, w.p, w.Ap, w.r, (T*)g.lv[0].b, w.cg, g.partials,
+                                             stride, g.tickets + 2);
+  else
+    k_fpcg_xr<T, false><<<gr, kThreads, 0, s>>>(n, x, w.p, w.Ap, w.r, (T*)g.lv[0].b, w.cg, g.partials,
+                                              stride, g.tickets + 2);
   GMG_CK(cudaGetLastError());
   return SEM_OK;
 }
