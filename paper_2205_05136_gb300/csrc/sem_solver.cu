@@ -118,7 +118,14 @@ __global__ void __launch_bounds__(kVecThreads)
   }
 }
 
+// Pairs of consecutive entries as one 16-byte access (the workspace vectors come
+// from cudaMalloc; a caller's x is checked for alignment on the host: VEC).
+struct alignas(16) D2 {
+  double e[2];
+};
+
 // x += alpha p, r -= alpha Ap, z = Jacobi(r); r.z, r.r; beta, convergence.
+template <bool VEC>
 __global__ void __launch_bounds__(kVecThreads)
     k_cg_xr(int64_t n, double* __restrict__ x, const double* __restrict__ p,
             const double* __restrict__ Ap, double* __restrict__ r, const double* __restrict__ inv,
@@ -126,8 +133,30 @@ __global__ void __launch_bounds__(kVecThreads)
   if (cg->done) return;
   const double alpha = cg->alpha;
   double v[2] = {0.0, 0.0};
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t g0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t gs = (int64_t)gridDim.x * blockDim.x;
+  const int64_t nc = VEC ? n / 2 : 0;
+  for (int64_t c = g0; c < nc; c += gs) {
+    D2 xx = reinterpret_cast<const D2*>(x)[c];
+    const D2 pp = reinterpret_cast<const D2*>(p)[c];
+    const D2 aa = reinterpret_cast<const D2*>(Ap)[c];
+    D2 rr = reinterpret_cast<const D2*>(r)[c];
+    D2 ii;
+    if (inv) ii = reinterpret_cast<const D2*>(inv)[c];
+    D2 zz;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      xx.e[k] = fma(alpha, pp.e[k], xx.e[k]);
+      rr.e[k] = fma(-alpha, aa.e[k], rr.e[k]);
+      zz.e[k] = inv ? ii.e[k] * rr.e[k] : rr.e[k];
+      v[0] = fma(rr.e[k], zz.e[k], v[0]);
+      v[1] = fma(rr.e[k], rr.e[k], v[1]);
+    }
+    reinterpret_cast<D2*>(x)[c] = xx;
+    reinterpret_cast<D2*>(r)[c] = rr;
+    reinterpret_cast<D2*>(z)[c] = zz;
+  }
+  for (int64_t i = nc * 2 + g0; i < n; i += gs) {
     x[i] = fma(alpha, p[i], x[i]);
     const double ri = fma(-alpha, Ap[i], r[i]);
     const double zi = inv ? inv[i] * ri : ri;
@@ -158,8 +187,18 @@ __global__ void __launch_bounds__(kVecThreads)
            double* __restrict__ Ap, const CgScalars* cg) {
   if (cg->done) return;
   const double beta = cg->beta;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t g0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t gs = (int64_t)gridDim.x * blockDim.x;
+  const int64_t nc = n / 2;
+  for (int64_t c = g0; c < nc; c += gs) {
+    const D2 zz = reinterpret_cast<const D2*>(z)[c];
+    D2 pp = reinterpret_cast<const D2*>(p)[c];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) pp.e[k] = fma(beta, pp.e[k], zz.e[k]);
+    reinterpret_cast<D2*>(p)[c] = pp;
+    reinterpret_cast<D2*>(Ap)[c] = D2{};
+  }
+  for (int64_t i = nc * 2 + g0; i < n; i += gs) {
     p[i] = fma(beta, p[i], z[i]);
     Ap[i] = 0.0;
   }
@@ -427,8 +466,12 @@ int cg_solve(sem_ctx* ctx, double alpha, const double* b, double* x, double rtol
         if (tm.enabled) SEM_CK(cudaEventRecord(evs[2 * c], s));
         SEM_CK(launch_operator(ctx, ap, s));
         if (tm.enabled) SEM_CK(cudaEventRecord(evs[2 * c + 1], s));
-        k_cg_xr<<<vg, kVecThreads, 0, s>>>(n, x, w.p, w.Ap, w.r, inv, w.z, w.cg, w.vec_partials,
-                                           w.tickets + 0);
+        if ((reinterpret_cast<uintptr_t>(x) & 15u) == 0)
+          k_cg_xr<true><<<vg, kVecThreads, 0, s>>>(n, x, w.p, w.Ap, w.r, inv, w.z, w.cg, w.vec_partials,
+                                                   w.tickets + 0);
+        else
+          k_cg_xr<false><<<vg, kVecThreads, 0, s>>>(n, x, w.p, w.Ap, w.r, inv, w.z, w.cg, w.vec_partials,
+                                                    w.tickets + 0);
         k_cg_p<<<vg, kVecThreads, 0, s>>>(n, w.z, w.p, w.Ap, w.cg);
       }
       SEM_CK(cudaGetLastError());

@@ -126,11 +126,12 @@ __global__ void __launch_bounds__(kTThreads)
     if (e < nelem) {
       const int i = loc % NF, j = (loc / NF) % NF, k = loc / (NF * NF);
       const int ex = e % nx, ey = (e / nx) % ny, ez = e / (nx * ny);
-      const int m = (((i == 0 && ex > 0) || (i == NF - 1 && ex < nx - 1)) ? 2 : 1) *
-                    (((j == 0 && ey > 0) || (j == NF - 1 && ey < ny - 1)) ? 2 : 1) *
-                    (((k == 0 && ez > 0) || (k == NF - 1 && ez < nz - 1)) ? 2 : 1);
+      // 1 / multiplicity of the node (elements sharing it): a power of two, exact
+      const T w = (((i == 0 && ex > 0) || (i == NF - 1 && ex < nx - 1)) ? T(0.5) : T(1)) *
+                  (((j == 0 && ey > 0) || (j == NF - 1 && ey < ny - 1)) ? T(0.5) : T(1)) *
+                  (((k == 0 && ez > 0) || (k == NF - 1 && ez < nz - 1)) ? T(0.5) : T(1));
       const int g = map_f[(size_t)e * NF3 + loc];
-      v = (bf[g] - tf[g]) / (T)m;
+      v = (bf[g] - tf[g]) * w;
     }
     f0[idx] = v;
   }
