@@ -113,6 +113,38 @@ def test_low_precision_apply_error_bound(prec, tol, quad):
     assert e < tol, e
 
 
+@pytest.mark.parametrize("prec,tol", [(gb.SEM_PREC_FP32, 2e-6), (gb.SEM_PREC_FP32_BF16, 2e-2)])
+@pytest.mark.parametrize("quad", QUADS)
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6])
+def test_low_precision_apply_ragged_units(p, prec, tol, quad):
+    """35 elements: a partial last group of elements in the FP32 kernels at every
+    degree (groups of 8, 3, 2, 1 elements per warp at p = 1..4)."""
+    s = W.slab(7, 5, 1, (20.0, 7.0, 3.0), perturb=0.1, seed=1)
+    tissue = _tissue(s)
+    g, o = _pair(s, p, quad, tissue)
+    u = W.uniform_vector(o.ndofs, -1.0, 1.0, seed=2)
+    A = Mh.assemble(o, tissue, 30.0, 1.0)
+    y = g.apply(torch.tensor(u, device="cuda", dtype=torch.float32), 30.0, 1.0, precision=prec)
+    e = rel(y.double().cpu().numpy(), A @ u)
+    assert e < tol, e
+
+
+@pytest.mark.parametrize("prec,tol", [(gb.SEM_PREC_FP32, 2e-6), (gb.SEM_PREC_FP32_BF16, 2e-2)])
+@pytest.mark.parametrize("p,dims", [(1, (40, 30, 41)), (2, (37, 30, 25)), (4, (40, 30, 31))])
+def test_low_precision_apply_many_groups_per_warp(p, dims, prec, tol):
+    """Meshes with several element groups per warp of the persistent FP32 kernel
+    (its cp.async pipeline runs over many groups), against the FP64 apply, which
+    the oracle checks at every degree."""
+    s = W.slab(*dims, (20.0, 7.0, 3.0), perturb=0.1, seed=1)
+    g = gb.Slab(s.flat_vertices(), s.nx, s.ny, s.nz, p, "LGL")
+    g.set_tissue(*_tissue(s))
+    u = torch.tensor(W.uniform_vector(g.ndofs, -1.0, 1.0, seed=2), device="cuda")
+    y64 = g.apply(u, 30.0, 1.0)
+    y = g.apply(u.float(), 30.0, 1.0, precision=prec).double()
+    assert rel(y.cpu().numpy(), y64.cpu().numpy()) < tol
+    g.close()
+
+
 def test_sweep_workload_sampled_rows():
     """Full-size perturbed ~2 M DOF slabs with rotating fibres (the operator
     sweep), in the launch configuration the benchmark times: sampled outputs
