@@ -361,8 +361,8 @@ def run_gpu(args):
     outer_is_df = args.arms != "fp64" and args.op_precision == "df64"
     outer = {
         "kernel": f"sem_apply_kernel<P={p},{quad},{'df64' if outer_is_df else 'f64'},dot> (outer CG operator)",
-        "launches": int(stats.n_apply), "avg_ms": apply_ms,
-        "total_ms": apply_ms * stats.n_apply,
+        "launches": int(stats.cg_iters), "timed": int(stats.n_apply), "avg_ms": apply_ms,
+        "total_ms": apply_ms * stats.cg_iters,
         "fp64_equivalent_tflops": achieved_tf,
         "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": algo_bytes,
     }
@@ -371,12 +371,12 @@ def run_gpu(args):
     if stats.n_smoother_apply > 0:
         sm_ms = stats.smoother_apply_ms / stats.n_smoother_apply
         sm_bytes = n_e * apply_bytes_per_element_fp32(p, args.mg_precision)
-        per_vcycle = 2 * args.mg_degree  # fine-level applies per V-cycle
+        per_vcycle = 2 * args.mg_degree  # fine-level applies per V-cycle (one V-cycle per PCG iteration)
         kernels["smoother_apply"] = {
             "kernel": (f"{'sem_apply_pipe_kernel' if p <= 4 else 'sem_apply_kernel'}<P={p},{quad},f32,"
                        f"{'bf16' if args.mg_precision == 'bf16' else 'f32'} metric> (fine-level V-cycle apply)"),
             "timed": int(stats.n_smoother_apply), "avg_ms": sm_ms,
-            "total_ms_est": sm_ms * per_vcycle * stats.n_smoother_apply,
+            "total_ms_est": sm_ms * per_vcycle * stats.cg_iters,
             "algorithmic_bytes_per_launch": sm_bytes,
             "achieved_gbs": sm_bytes / (sm_ms * 1e-3) / 1e9,
         }
