@@ -209,6 +209,22 @@ int sem_state_get(sem_state* st, double* u, double* u_prev, double* h, double* h
 int sem_state_restore(sem_state* st, const double* u, const double* u_prev, const double* h,
                       const double* h_prev, int64_t n, void* stream);
 
+/* Activation times (Section 5, Eq. tau): while enabled, every step of
+ * sem_step records per node the largest |du/dt| met so far and the time of the
+ * step that gave it; du/dt at t^{n+1} = (n+1) dt is the time scheme's own
+ * derivative, (u^1 - u^0)/dt for the first step and
+ * (3 u^{n+1} - 4 u^n + u^{n-1})/(2 dt) after; on a tie the earlier time stays.
+ * Enabling (enable != 0) allocates the two arrays on first use (owned by the
+ * state, freed by sem_state_destroy) and resets them (max -1, time NaN);
+ * enable = 0 stops the updates and keeps the values.  SEM_ERR_NOMEM when the
+ * arrays cannot be allocated. */
+int sem_state_track_activation(sem_state* st, int enable, void* stream);
+
+/* Copy the activation times (ms) and the max |du/dt| (mV/ms) into caller-owned
+ * device double[ndofs] arrays (either may be NULL).  SEM_ERR_ARG when tracking
+ * was never enabled or a pointer is not device memory. */
+int sem_state_get_activation(sem_state* st, double* tau, double* dudt_max, void* stream);
+
 /* Advance the state by nsteps time steps of size dt (ms): the first step from
  * n = 0 is BDF1 (u* = u^0, A = M/dt + K), the following ones BDF2
  * (u* = 2u^n - u^{n-1}, A = 3/(2 dt) M + K), each one

@@ -142,6 +142,18 @@ class State:
     def step(self, dt, nsteps=1, rtol=1e-10, atol=0.0, maxit=1000, precond=SEM_PC_JACOBI):
         return capi.sem_step(self.slab.ctx, self._st, dt, nsteps, rtol, atol, maxit, precond)
 
+    def track_activation(self, enable=True):
+        """Record activation times (Eq. tau) from the next step on (enabling resets them)."""
+        capi.sem_state_track_activation(self.slab.ctx, self._st, enable)
+
+    def activation(self):
+        """(tau, max |du/dt|) per node as device tensors: the time of the step with the
+        largest |du/dt| so far and that value."""
+        s = self.slab
+        tau, dmax = s._vec(), s._vec()
+        capi.sem_state_get_activation(s.ctx, self._st, tau, dmax)
+        return tau, dmax
+
     def close(self):
         if getattr(self, "_st", None) is not None:
             capi.sem_state_destroy(self._st)

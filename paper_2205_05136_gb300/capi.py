@@ -46,6 +46,7 @@ EXPORTS = [
     "sem_num_elements", "sem_dof_coords", "sem_set_tissue", "sem_apply", "sem_diagonal",
     "sem_cg_solve", "sem_set_ionic", "sem_set_stimulus", "sem_state_create", "sem_state_destroy",
     "sem_state_set", "sem_state_get", "sem_state_restore", "sem_step", "sem_step_host", "sem_step_host_out",
+    "sem_state_track_activation", "sem_state_get_activation",
     "sem_set_timing", "sem_apply_dot_static", "sem_set_gmg", "sem_vcycle", "sem_gmg_info",
     "sem_forward_record", "sem_adjoint_grad", "sem_set_operator_precision",
 ]
@@ -108,6 +109,8 @@ def lib():
                                    ctypes.POINTER(sem_stats), _P]),
             "sem_step_host_out": (_I, [_P, _P, _P, _P, _P, _P, _P, _I64, _D, _D, _D, _I, _I,
                                        ctypes.POINTER(sem_stats), _P]),
+            "sem_state_track_activation": (_I, [_P, _I, _P]),
+            "sem_state_get_activation": (_I, [_P, _P, _P, _P]),
             "sem_set_timing": (_I, [_P, _I]),
             "sem_apply_dot_static": (_I, [_P, _D, _D, _P, _P, _P, _P]),
             "sem_set_gmg": (_I, [_P, _I, _I, _I, _I]),
@@ -305,6 +308,18 @@ def sem_step_host_out(ctx, u, u_prev, h, h_prev, u_next, h_next, n, dt, rtol, at
                                    int(n), float(dt), float(rtol), float(atol), int(maxit), int(precond),
                                    ctypes.byref(stats), _stream(stream)), ctx)
     return stats
+
+
+def sem_state_track_activation(ctx, st, enable=True, stream=None):
+    return _check(lib().sem_state_track_activation(st, 1 if enable else 0, _stream(stream)), ctx)
+
+
+def sem_state_get_activation(ctx, st, tau, dudt_max, stream=None):
+    """tau, dudt_max: float64 CUDA tensors of ndofs entries (or None)."""
+    n = sem_num_dofs(ctx)
+    t = _dev(tau, torch.float64, n, "tau") if tau is not None else None
+    d = _dev(dudt_max, torch.float64, n, "dudt_max") if dudt_max is not None else None
+    return _check(lib().sem_state_get_activation(st, t, d, _stream(stream)), ctx)
 
 
 def sem_set_timing(ctx, enable: bool):

@@ -357,7 +357,50 @@ int sem_state_destroy(sem_state* st) {
   DeviceGuard guard(st->ctx->device);
   cudaDeviceSynchronize();
   for (int j = 0; j < 3; ++j) { cudaFree(st->U[j]); cudaFree(st->H[j]); }
+  cudaFree(st->act_dmax);
+  cudaFree(st->act_tau);
   delete st;
+  return SEM_OK;
+}
+
+int sem_state_track_activation(sem_state* st, int enable, void* stream) {
+  if (st == nullptr) return SEM_ERR_ARG;
+  sem_ctx* ctx = st->ctx;
+  DeviceGuard guard(ctx->device);
+  if (!enable) {
+    st->act_track = false;
+    return SEM_OK;
+  }
+  const size_t bytes = sizeof(double) * ctx->L.ndofs;
+  if (st->act_dmax == nullptr) {
+    if (cudaMalloc(&st->act_dmax, bytes) != cudaSuccess || cudaMalloc(&st->act_tau, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(st->act_dmax);
+      cudaFree(st->act_tau);
+      st->act_dmax = st->act_tau = nullptr;
+      return fail(ctx, SEM_ERR_NOMEM, "activation arrays: allocation failed");
+    }
+  }
+  SEM_CK(activation_reset(st, as_stream(stream)));
+  st->act_track = true;
+  return SEM_OK;
+}
+
+int sem_state_get_activation(sem_state* st, double* tau, double* dudt_max, void* stream) {
+  if (st == nullptr) return SEM_ERR_ARG;
+  sem_ctx* ctx = st->ctx;
+  DeviceGuard guard(ctx->device);
+  if (st->act_dmax == nullptr) return fail(ctx, SEM_ERR_ARG, "activation tracking was never enabled");
+  const size_t bytes = sizeof(double) * ctx->L.ndofs;
+  cudaStream_t s = as_stream(stream);
+  if (tau != nullptr) {
+    CK_DEV(tau, "tau");
+    SEM_CK(cudaMemcpyAsync(tau, st->act_tau, bytes, cudaMemcpyDeviceToDevice, s));
+  }
+  if (dudt_max != nullptr) {
+    CK_DEV(dudt_max, "dudt_max");
+    SEM_CK(cudaMemcpyAsync(dudt_max, st->act_dmax, bytes, cudaMemcpyDeviceToDevice, s));
+  }
   return SEM_OK;
 }
 

@@ -66,6 +66,10 @@ struct sem_state {
   double* H[3] = {nullptr, nullptr, nullptr};
   int cur = 0, prev = 1, next = 2;
   int64_t n = 0;
+  // activation times (Eq. tau): running max |du/dt| per node and its time
+  double* act_dmax = nullptr;
+  double* act_tau = nullptr;
+  bool act_track = false;
 };
 
 namespace sem {
@@ -87,6 +91,8 @@ int apply_df64(sem_ctx* ctx, double alpha, double beta, const double* u, double*
 // The FP64-vector operator the solvers use (FP64 or df64 arithmetic per ctx->op_precision);
 // prepare_operator makes its metric copy and must run before any stream capture.
 cudaError_t prepare_operator(sem_ctx* ctx, cudaStream_t s);
+// Activation-time arrays of a state to (max |du/dt| = -1, tau = NaN).
+cudaError_t activation_reset(sem_state* st, cudaStream_t s);
 cudaError_t launch_operator(sem_ctx* ctx, const ApplyArgs64& a, cudaStream_t s);
 
 // Geometric multigrid (sem_gmg.cu).

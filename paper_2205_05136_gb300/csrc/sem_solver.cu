@@ -14,6 +14,7 @@
 // chunk of iterations, and kernels of a finished solve return at once.
 #include <algorithm>
 #include <cmath>
+#include <limits>
 #include <vector>
 
 #include "sem_apply_kernel.cuh"
@@ -253,7 +254,41 @@ __global__ void __launch_bounds__(kVecThreads)
   }
 }
 
+__global__ void k_fill_pair(int64_t n, double* a, double va, double* b, double vb) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    a[i] = va;
+    b[i] = vb;
+  }
+}
+
+// Activation time (Eq. tau): du/dt at t1 by the time scheme (BDF1 for the first
+// step, BDF2 after), and where |du/dt| exceeds the node's running maximum the
+// maximum and t1 are replaced (ties keep the earlier time).
+__global__ void __launch_bounds__(kVecThreads)
+    k_activation(int64_t n, const double* __restrict__ u1, const double* __restrict__ u0,
+                 const double* __restrict__ um1, int first, double dt, double t1,
+                 double* __restrict__ dmax, double* __restrict__ tau) {
+  const double inv_dt = 1.0 / dt, inv_2dt = 0.5 / dt;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double d = first ? (u1[i] - u0[i]) * inv_dt : (3.0 * u1[i] - 4.0 * u0[i] + um1[i]) * inv_2dt;
+    const double ad = fabs(d);
+    if (ad > dmax[i]) {
+      dmax[i] = ad;
+      tau[i] = t1;
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t activation_reset(sem_state* st, cudaStream_t s) {
+  const int64_t n = st->ctx->L.ndofs;
+  k_fill_pair<<<vec_grid(n), kVecThreads, 0, s>>>(n, st->act_dmax, -1.0, st->act_tau,
+                                                  std::numeric_limits<double>::quiet_NaN());
+  return cudaGetLastError();
+}
 
 int vec_blocks(int64_t n) { return vec_grid(n); }
 
@@ -555,6 +590,12 @@ int time_steps(sem_ctx* ctx, sem_state* st, double dt, int nsteps, double rtol, 
     st->cur = st->next;
     st->next = old_prev;
     st->n += 1;
+    if (st->act_track) {  // u^{n+1}, u^n, u^{n-1} sit in U[cur], U[prev], U[next] now
+      k_activation<<<vg, kVecThreads, 0, s>>>(n, st->U[st->cur], st->U[st->prev], st->U[st->next],
+                                              first, dt, (double)st->n * dt, st->act_dmax, st->act_tau);
+      SEM_CK(cudaGetLastError());
+      ctx->launches += 1;
+    }
     if (stats) stats->steps += 1;
   }
   return SEM_OK;

@@ -192,6 +192,56 @@ def test_step_host_out_matches_device_step(pinned):
         capi.sem_step_host_out(g.ctx, us[1], us[0], hs[1], hs[0], us[1], hs[2], 4, 0.05, 1e-12, 0.0, 1000)
 
 
+def test_activation_times_match_oracle():
+    """Activation times (Eq. tau) over 60 steps of the small slab with a corner
+    stimulus: max |du/dt| per node to 1e-9 of the largest, and the time wherever
+    the oracle's two largest step derivatives differ by more than 1e-7."""
+    from oracle import activation as ACT
+    s, tissue, g, o = _small(2, "LGL")
+    dt = 0.05
+    box = (0.0, 0.0, 0.0, 1.5, 1.5, 1.5)
+    g.set_ionic()
+    g.set_stimulus("box", box, 50.0, 0.0, 1.0)
+    st = g.new_state(-85.0, 1.0)
+    st.track_activation(True)
+    st.step(dt, 60, rtol=1e-13, maxit=5000)
+    tau, dmax = st.activation()
+    tau, dmax = tau.cpu().numpy(), dmax.cpu().numpy()
+    md = MD.Monodomain(o, tissue, dt, region=("box", box), amplitude=50.0, t_on=0.0, t_off=1.0)
+    # the oracle's derivatives at every step, for the separation test
+    state = MD.rest_state(o.ndofs)
+    ds = []
+    for _ in range(60):
+        new = md.step(state)
+        ds.append(np.abs(ACT.scheme_derivative(new["u"], state["u"], state["u_prev"], new["n"], dt)))
+        state = new
+    ds = np.array(ds)
+    tref = dt * (1 + np.argmax(ds, axis=0))
+    dref = ds.max(axis=0)
+    assert np.abs(dmax - dref).max() <= 1e-9 * dref.max()
+    # unique maxima (the two largest step derivatives well apart, mostly the
+    # activated nodes): the same step; elsewhere (resting nodes with near ties)
+    # the step the GPU chose attains the oracle's maximum
+    top2 = np.sort(ds, axis=0)[-2:]
+    sep = (top2[1] - top2[0]) > 1e-7 * dref.max()
+    assert sep.sum() >= 100
+    assert np.array_equal(tau[sep], tref[sep])
+    k = np.rint(tau / dt).astype(int) - 1
+    assert ((k >= 0) & (k < 60)).all()
+    assert (ds[k, np.arange(o.ndofs)] >= dref - 1e-9 * dref.max()).all()
+    # the front moved: the far corner activates later than the stimulated one
+    assert dref.max() > 10.0 and tref.max() > tref.min()
+    # disabling keeps the values; re-enabling resets them
+    st.track_activation(False)
+    st.step(dt, 2, rtol=1e-13, maxit=5000)
+    tau2, _ = st.activation()
+    assert np.array_equal(tau2.cpu().numpy(), tau, equal_nan=True)
+    st.track_activation(True)
+    _, d3 = st.activation()
+    assert (d3.cpu().numpy() == -1.0).all()
+    st.close()
+
+
 def test_checkpoint_restore_resumes_identically():
     s, tissue, g, o = _small(2, "LGL")
     g.set_ionic()
