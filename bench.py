@@ -605,20 +605,28 @@ def run_gmg8m(args):
                     "u_prev": torch.full((slab.ndofs,), -85.0, dtype=torch.float64, device="cuda"),
                     "h": torch.ones(slab.ndofs, dtype=torch.float64, device="cuda"),
                     "h_prev": torch.ones(slab.ndofs, dtype=torch.float64, device="cuda"), "n": 0})
+        st.track_activation(True)  # activation times (Eq. tau) on the way, inside the timed run
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         stats = st.step(DT, nsteps, rtol=RTOL, maxit=MAXIT, precond=gb.SEM_PC_GMG)
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
         u, h, n = st.get()
-        finals[name] = (u, h)
+        tau, dmax = st.activation()
+        finals[name] = (u, h, tau, dmax)
         out["levels"] = {"p": info["p"], "dims": info["dims"], "ndofs": info["ndofs"]}
         out[name] = {"seconds": el, "steps_per_s": nsteps / el, "gdof_steps_per_s": slab.ndofs * nsteps / el / 1e9,
                      "cg_iters_per_step": stats.cg_iters / nsteps,
                      "u_max_mV": float(u.max()), "activated_fraction": float((u > -40.0).double().mean()),
                      "outer_apply_ms": stats.apply_ms / max(stats.n_apply, 1)}
         st.close()
-    (u64, h64), (umx, hmx) = finals["fp64"], finals["mixed"]
+    (u64, h64, tau64, d64), (umx, hmx, taumx, dmx) = finals["fp64"], finals["mixed"]
+    act = d64 > 10.0  # nodes the front reached (upstroke faster than 10 mV/ms)
+    out["activation"] = {"activated_nodes": int(act.sum()),
+                         "tau_ms_min": float(tau64[act].min()), "tau_ms_max": float(tau64[act].max()),
+                         "mixed_same_tau_fraction": float((taumx[act] == tau64[act]).double().mean()),
+                         "mixed_max_abs_tau_diff_ms": float((taumx[act] - tau64[act]).abs().max()),
+                         "mixed_dudt_max_rel_diff": float(((dmx - d64)[act].abs() / d64[act]).max())}
     out["mixed"]["u_rel_l2_vs_fp64"] = float(torch.linalg.norm(umx - u64) / torch.linalg.norm(u64))
     out["mixed"]["u_rel_linf_vs_fp64"] = float((umx - u64).abs().max() / u64.abs().max())
     out["mixed"]["h_rel_l2_vs_fp64"] = float(torch.linalg.norm(hmx - h64) / torch.linalg.norm(h64))
