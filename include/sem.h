@@ -50,7 +50,7 @@ extern "C" {
 #define SEM_ERR_BAD_MESH (-3)      /* det J <= 0 at some quadrature point */
 #define SEM_ERR_NOT_CONVERGED (-4) /* CG reached maxit; x holds the last iterate */
 #define SEM_ERR_NONFINITE (-5)     /* NaN or Inf met in a CG inner product */
-#define SEM_ERR_UNSUPPORTED (-6)   /* valid request this build does not provide */
+#define SEM_ERR_UNSUPPORTED (-6)   /* valid request that this library does not provide */
 #define SEM_ERR_NOMEM (-7)         /* device allocation failed */
 
 #define SEM_QUAD_LG 0  /* SEM: (p+1)-point Legendre-Gauss quadrature */

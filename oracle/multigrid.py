@@ -8,7 +8,7 @@ Chebyshev parameters come from an estimate of the largest eigenvalue by 10
 CG / Lanczos iterations, the smoothing range is [0.08, 1.2] times that
 estimate; transfers between levels are matrix-vector products.
 
-Level hierarchy (this build's reading; the paper uses h-multigrid at fixed p
+Level hierarchy (the reading taken here; the paper uses h-multigrid at fixed p
 on an octree, the workloads ask for p-coarsening followed by h-coarsening):
 
 * p-levels on the fine mesh: p -> max(1, p // 2) -> ... -> 1, with the nodal
