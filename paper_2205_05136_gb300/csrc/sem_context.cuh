@@ -18,7 +18,7 @@ struct Workspace {
   CgScalars* cg = nullptr;   // device
   CgScalars* cg_host = nullptr;  // page-locked mirror
   double* vec_partials = nullptr;     // [kReduceSlots][kVecBlocksMax]
-  unsigned int* tickets = nullptr;    // [4]: vec, apply, spare
+  unsigned int* tickets = nullptr;    // [4]: [0] the CG vector kernels' reductions, the rest spare
   double* apply_partials = nullptr;   // [apply grid]
   double* dot_result = nullptr;       // 1 double
 };

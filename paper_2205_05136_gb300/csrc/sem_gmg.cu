@@ -110,10 +110,16 @@ struct alignas(K * sizeof(T)) Pk {
 template <typename T>
 __host__ __device__ constexpr int k16() { return 16 / (int)sizeof(T); }
 
+// Grid-stride loops over 16-byte chunks and over the scalar tail.  They stay
+// rolled: with grids of 8 CTAs per SM a thread runs only a few iterations, and
+// an unrolled body would only raise the register count (to 56-72 registers a
+// thread, which halves the resident CTAs) without ever running.
 #define GRID_CHUNKS(c, nc)                                                         \
+  _Pragma("unroll 1")                                                              \
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < (nc);     \
        c += (int64_t)gridDim.x * blockDim.x)
 #define GRID_TAIL(i, start, n)                                                     \
+  _Pragma("unroll 1")                                                              \
   for (int64_t i = (start) + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); \
        i += (int64_t)gridDim.x * blockDim.x)
 
@@ -984,7 +990,7 @@ int pcg_iter_seq(sem_ctx* ctx, Gmg& g, double alpha, double* x, cudaStream_t s) 
   ApplyArgs64 ap{};
   ap.map = L.map; ap.metric = L.metric; ap.u = w.p; ap.y = w.Ap; ap.nelem = L.nelem;
   ap.mass_coef = alpha; ap.out_scale = 1.0; ap.scale_out = 0; ap.done = done;
-  ap.dot_partials = w.apply_partials; ap.dot_ticket = w.tickets + 1; ap.cg = w.cg;
+  ap.dot_partials = w.apply_partials; ap.cg = w.cg;
   // external records become event nodes of the captured graph (timing of the outer apply)
   GMG_CK(cudaEventRecordWithFlags(g.ev0, s, cudaEventRecordExternal));
   GMG_CK(launch_operator(ctx, ap, s));

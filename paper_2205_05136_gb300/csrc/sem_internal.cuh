@@ -159,12 +159,12 @@ struct ApplyArgs {
   T out_scale;        // factor applied to the element result before the scatter
   int scale_out;      // out_scale != 1
   const int* done;    // optional: skip all work when *done != 0
-  // optional fused u . (A u) (CG's p . A p), finished by the last block;
-  // dot_partials holds one double per CTA of the launch
+  // optional fused u . (A u) (CG's p . A p): every CTA writes its partial sum
+  // to dot_partials (one double per CTA of the launch) and a one-CTA kernel
+  // launched after the apply adds them up
   double* dot_partials;
-  unsigned int* dot_ticket;
-  CgScalars* cg;      // when set, the finishing block writes pAp and alpha = rz / pAp
-  double* dot_out;    // otherwise the total goes here
+  CgScalars* cg;      // when set, the sum goes to pAp, and alpha = rz / pAp
+  double* dot_out;    // otherwise the sum goes here
 };
 using ApplyArgs64 = ApplyArgs<double, double>;
 
@@ -177,6 +177,10 @@ cudaError_t launch_apply_bf16(const Level& L, const ApplyArgs<float, __nv_bfloat
 cudaError_t launch_apply_df64(const Level& L, const ApplyArgs<df, df_pair>& a, bool mass_only,
                               cudaStream_t s);
 int apply_grid_blocks(const Level& L);
+// Sum, in a fixed order, of the n per-CTA partials of a fused inner product:
+// to cg (pAp and alpha = rz / pAp) when set, else to *out; nothing when *done.
+cudaError_t launch_apply_dot_finish(const double* partials, int n, CgScalars* cg, double* out,
+                                    const int* done, cudaStream_t s);
 // Raises the dynamic shared-memory limit of the kernels that stage the metric in
 // shared memory; call once per device before any stream capture.
 cudaError_t prime_apply_kernels();

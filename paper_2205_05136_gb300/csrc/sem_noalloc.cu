@@ -6,17 +6,17 @@
 // CUDA stream capture is active (cudaMalloc is not permitted there), host
 // frameworks that own every device allocation through their own arena or a
 // fixed budget, and real-time loops that must not enter the allocator.  This
-// entry point allocates nothing: the per-CTA partial sums and the arrival
-// counter of its grid reduction live in one file-scope static device array.
+// entry point allocates nothing: the per-CTA partial sums of its inner product
+// live in one file-scope static device array, and a one-CTA kernel launched
+// after the apply adds them up.
 //
 // Limits and sharing:
-//   * the array holds kStaticMaxCtas partial sums (512 KiB plus one counter);
+//   * the array holds kStaticMaxCtas partial sums (512 KiB);
 //     every GPU that loads libsem keeps it until the process exits;
 //   * a mesh whose apply needs more CTAs than that is rejected (SEM_ERR_ARG);
-//   * all calls share the array, and it keeps the last call's contents: the
-//     counter is cleared at the start of every call, and calls that overlap on
-//     the GPU (concurrent streams, or several contexts on one device) race on
-//     it, so such calls must be ordered by the caller;
+//   * all calls share the array, and it keeps the last call's contents: calls
+//     that overlap on the GPU (concurrent streams, or several contexts on one
+//     device) race on it, so such calls must be ordered by the caller;
 //   * the first call on a device looks up the array's device address with
 //     cudaGetSymbolAddress (with that device current); make that first call
 //     before any stream capture begins.
@@ -32,9 +32,8 @@ namespace {
 constexpr int kStaticMaxCtas = 65536;
 constexpr int kStaticMaxDevices = 64;
 
-// [0, kStaticMaxCtas): per-CTA partial sums; the next double holds the arrival
-// counter (as unsigned int); the rest is padding.
-static __device__ __align__(256) double g_apply_dot_scratch[kStaticMaxCtas + 32];
+// Per-CTA partial sums of the inner product.
+static __device__ __align__(256) double g_apply_dot_scratch[kStaticMaxCtas];
 
 std::mutex g_scratch_mu;
 double* g_scratch_addr[kStaticMaxDevices] = {};
@@ -94,10 +93,7 @@ extern "C" int sem_apply_dot_static(sem_ctx* ctx, double alpha, double beta, con
   double* scratch = nullptr;
   cudaError_t e = scratch_address(ctx->device, &scratch);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGetSymbolAddress(static scratch)");
-  unsigned int* ticket = reinterpret_cast<unsigned int*>(scratch + kStaticMaxCtas);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  e = cudaMemsetAsync(ticket, 0, sizeof(unsigned int), s);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemsetAsync(counter)");
   e = cudaMemsetAsync(y, 0, sizeof(double) * L.ndofs, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemsetAsync(y)");
   ApplyArgs64 a{};
@@ -110,7 +106,6 @@ extern "C" int sem_apply_dot_static(sem_ctx* ctx, double alpha, double beta, con
   a.out_scale = beta;
   a.scale_out = beta != 1.0;
   a.dot_partials = scratch;
-  a.dot_ticket = ticket;
   a.dot_out = dot;
   e = launch_apply_fp64(L, a, false, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "apply kernel launch");

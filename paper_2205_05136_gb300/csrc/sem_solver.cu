@@ -65,6 +65,7 @@ __device__ __forceinline__ bool grid_sums(double (&v)[K], double* partials, unsi
 
 __global__ void k_inv_diag(int64_t n, double alpha, const double* __restrict__ m,
                            const double* __restrict__ k, double* __restrict__ inv) {
+#pragma unroll 1
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     inv[i] = 1.0 / fma(alpha, m[i], k[i]);
@@ -72,6 +73,7 @@ __global__ void k_inv_diag(int64_t n, double alpha, const double* __restrict__ m
 
 __global__ void k_scale_mul(int64_t n, double a, const double* __restrict__ d,
                             const double* __restrict__ x, double* __restrict__ y) {
+#pragma unroll 1
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     y[i] = a * d[i] * x[i];
@@ -79,6 +81,7 @@ __global__ void k_scale_mul(int64_t n, double a, const double* __restrict__ d,
 
 __global__ void k_scale_mul32(int64_t n, float a, const double* __restrict__ d,
                               const float* __restrict__ x, float* __restrict__ y) {
+#pragma unroll 1
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     y[i] = a * (float)d[i] * x[i];
@@ -91,6 +94,7 @@ __global__ void __launch_bounds__(kVecThreads)
               double* __restrict__ p, CgScalars* cg, double* partials, unsigned int* ticket,
               double rtol, double atol) {
   double v[3] = {0.0, 0.0, 0.0};
+#pragma unroll 1
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double bi = b[i];
@@ -137,6 +141,7 @@ __global__ void __launch_bounds__(kVecThreads)
   const int64_t g0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t gs = (int64_t)gridDim.x * blockDim.x;
   const int64_t nc = VEC ? n / 2 : 0;
+#pragma unroll 1
   for (int64_t c = g0; c < nc; c += gs) {
     D2 xx = reinterpret_cast<const D2*>(x)[c];
     const D2 pp = reinterpret_cast<const D2*>(p)[c];
@@ -157,6 +162,7 @@ __global__ void __launch_bounds__(kVecThreads)
     reinterpret_cast<D2*>(r)[c] = rr;
     reinterpret_cast<D2*>(z)[c] = zz;
   }
+#pragma unroll 1
   for (int64_t i = nc * 2 + g0; i < n; i += gs) {
     x[i] = fma(alpha, p[i], x[i]);
     const double ri = fma(-alpha, Ap[i], r[i]);
@@ -191,6 +197,7 @@ __global__ void __launch_bounds__(kVecThreads)
   const int64_t g0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t gs = (int64_t)gridDim.x * blockDim.x;
   const int64_t nc = n / 2;
+#pragma unroll 1
   for (int64_t c = g0; c < nc; c += gs) {
     const D2 zz = reinterpret_cast<const D2*>(z)[c];
     D2 pp = reinterpret_cast<const D2*>(p)[c];
@@ -199,6 +206,7 @@ __global__ void __launch_bounds__(kVecThreads)
     reinterpret_cast<D2*>(p)[c] = pp;
     reinterpret_cast<D2*>(Ap)[c] = D2{};
   }
+#pragma unroll 1
   for (int64_t i = nc * 2 + g0; i < n; i += gs) {
     p[i] = fma(beta, p[i], z[i]);
     Ap[i] = 0.0;
@@ -234,6 +242,7 @@ __global__ void __launch_bounds__(kVecThreads)
   const double c_open = (first ? dt : 2.0 * dt) * prm.inv_tau_open;
   const double c_close = (first ? dt : 2.0 * dt) * prm.inv_tau_close;
   const double c_den = first ? 1.0 : 3.0;
+#pragma unroll 1
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double u0 = un[i];
@@ -255,6 +264,7 @@ __global__ void __launch_bounds__(kVecThreads)
 }
 
 __global__ void k_fill_pair(int64_t n, double* a, double va, double* b, double vb) {
+#pragma unroll 1
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     a[i] = va;
@@ -270,6 +280,7 @@ __global__ void __launch_bounds__(kVecThreads)
                  const double* __restrict__ um1, int first, double dt, double t1,
                  double* __restrict__ dmax, double* __restrict__ tau) {
   const double inv_dt = 1.0 / dt, inv_2dt = 0.5 / dt;
+#pragma unroll 1
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double d = first ? (u1[i] - u0[i]) * inv_dt : (3.0 * u1[i] - 4.0 * u0[i] + um1[i]) * inv_2dt;
@@ -385,7 +396,7 @@ cudaError_t launch_operator(sem_ctx* ctx, const ApplyArgs64& a, cudaStream_t s) 
   ApplyArgs<df, df_pair> d{};
   d.map = a.map; d.metric = L.metric2; d.u = a.u; d.y = a.y; d.nelem = a.nelem;
   d.mass_coef = df(a.mass_coef); d.out_scale = df(a.out_scale); d.scale_out = a.scale_out;
-  d.done = a.done; d.dot_partials = a.dot_partials; d.dot_ticket = a.dot_ticket; d.cg = a.cg;
+  d.done = a.done; d.dot_partials = a.dot_partials; d.cg = a.cg;
   d.dot_out = a.dot_out;
   return launch_apply_df64(L, d, false, s);
 }
@@ -479,7 +490,6 @@ int cg_solve(sem_ctx* ctx, double alpha, const double* b, double* x, double rtol
   ApplyArgs64 ap = base_args(ctx, alpha, 1.0, w.p, w.Ap);
   ap.done = &w.cg->done;
   ap.dot_partials = w.apply_partials;
-  ap.dot_ticket = w.tickets + 1;
   ap.cg = w.cg;
 
   Timing& tm = ctx->timing;
@@ -511,7 +521,7 @@ int cg_solve(sem_ctx* ctx, double alpha, const double* b, double* x, double rtol
       }
       SEM_CK(cudaGetLastError());
       launched += this_chunk;
-      ctx->launches += 3 * this_chunk;
+      ctx->launches += 4 * this_chunk;  // apply, its inner-product sum, x/r update, p update
     }
     SEM_CK(cudaMemcpyAsync(w.cg_host, w.cg, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
     SEM_CK(cudaStreamSynchronize(s));
