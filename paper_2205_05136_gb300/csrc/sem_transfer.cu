@@ -50,6 +50,29 @@ __device__ __forceinline__ void down_line(const T (&P)[NF][NC], const T (&in)[NF
   }
 }
 
+// Position flags of the CTA's elements, computed once per element (the slab
+// coordinates need divisions by the runtime mesh sizes): bit 0 ex > 0, bit 1
+// ex < nx - 1, bit 2 ey > 0, bit 3 ey < ny - 1, bit 4 ez > 0, bit 5
+// ez < nz - 1, bit 6 the element exists.  The caller synchronises.
+template <int E>
+__device__ __forceinline__ void element_flags(int e0, int nelem, int nx, int ny, int nz,
+                                              unsigned char (&fl)[E]) {
+  if (threadIdx.x < E) {
+    const int e = e0 + threadIdx.x;
+    unsigned f = 0;
+    if (e < nelem) {
+      const int ex = e % nx, ey = (e / nx) % ny, ez = e / (nx * ny);
+      f = (ex > 0 ? 1u : 0u) | (ex < nx - 1 ? 2u : 0u) | (ey > 0 ? 4u : 0u) | (ey < ny - 1 ? 8u : 0u) |
+          (ez > 0 ? 16u : 0u) | (ez < nz - 1 ? 32u : 0u) | 64u;
+    }
+    fl[threadIdx.x] = (unsigned char)f;
+  }
+}
+
+// Loops of the transfer kernels run over compile-time trip counts
+// (kTThreads threads per CTA in every launch), so the per-node index
+// arithmetic divides by constants only and the gathers of all iterations are
+// in flight together.
 template <int NF, int NC, typename T>
 __global__ void __launch_bounds__(kTThreads)
     k_prolong_sf(int nelem, int nx, int ny, int nz, const int* __restrict__ map_c,
@@ -61,13 +84,21 @@ __global__ void __launch_bounds__(kTThreads)
   __shared__ T c0[E * NC3];
   __shared__ T s1[E * NC * NC * NF];  // [k_c][j_c][i_f]
   __shared__ T s2[E * NC * NF * NF];  // [k_c][j_f][i_f]
+  __shared__ unsigned char fl[E];
   const int e0 = blockIdx.x * E;
-  for (int idx = threadIdx.x; idx < E * NC3; idx += blockDim.x) {
-    const int s = idx / NC3, a = idx - s * NC3, e = e0 + s;
-    c0[idx] = e < nelem ? xc[map_c[(size_t)e * NC3 + a]] : T(0);
+  element_flags<E>(e0, nelem, nx, ny, nz, fl);
+  {
+    const int nv = min(E, nelem - e0) * NC3;  // coarse values of the CTA's elements
+    const int* gm = map_c + (size_t)e0 * NC3;
+    constexpr int IT = (E * NC3 + kTThreads - 1) / kTThreads;
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+      const int idx = threadIdx.x + it * kTThreads;
+      if (IT * kTThreads == E * NC3 || idx < E * NC3) c0[idx] = idx < nv ? xc[__ldg(gm + idx)] : T(0);
+    }
   }
   __syncthreads();
-  for (int w = threadIdx.x; w < E * NC * NC; w += blockDim.x) {  // x-lines (j_c, k_c)
+  for (int w = threadIdx.x; w < E * NC * NC; w += kTThreads) {  // x-lines (j_c, k_c)
     const int s = w / (NC * NC), l = w - s * NC * NC;
     T in[NC], out[NF];
 #pragma unroll
@@ -77,7 +108,7 @@ __global__ void __launch_bounds__(kTThreads)
     for (int i = 0; i < NF; ++i) s1[s * NC * NC * NF + l * NF + i] = out[i];
   }
   __syncthreads();
-  for (int w = threadIdx.x; w < E * NC * NF; w += blockDim.x) {  // y-lines (i_f, k_c)
+  for (int w = threadIdx.x; w < E * NC * NF; w += kTThreads) {  // y-lines (i_f, k_c)
     const int s = w / (NC * NF), l = w - s * NC * NF, i = l % NF, k = l / NF;
     T in[NC], out[NF];
 #pragma unroll
@@ -87,20 +118,23 @@ __global__ void __launch_bounds__(kTThreads)
     for (int j = 0; j < NF; ++j) s2[s * NC * NF * NF + (k * NF + j) * NF + i] = out[j];
   }
   __syncthreads();
-  for (int w = threadIdx.x; w < E * NF * NF; w += blockDim.x) {  // z-lines (i_f, j_f)
-    const int s = w / (NF * NF), l = w - s * NF * NF, i = l % NF, j = l / NF, e = e0 + s;
-    if (e >= nelem) continue;
+  for (int w = threadIdx.x; w < E * NF * NF; w += kTThreads) {  // z-lines (i_f, j_f)
+    const int s = w / (NF * NF), l = w - s * NF * NF, i = l % NF, j = l / NF;
+    const unsigned f = fl[s];
+    if (!(f & 64u)) continue;
     T in[NC], out[NF];
 #pragma unroll
     for (int c = 0; c < NC; ++c) in[c] = s2[s * NC * NF * NF + (c * NF + j) * NF + i];
     up_line<NF, NC>(pm.P, in, out);
-    const int ex = e % nx, ey = (e / nx) % ny, ez = e / (nx * ny);
-    const bool own_xy = (i < NF - 1 || ex == nx - 1) && (j < NF - 1 || ey == ny - 1);
+    // the element owns its nodes except those on its upper faces that a next
+    // element shares (ex < nx - 1 at i = NF - 1, and likewise in y and z)
+    const bool own_xy = (i < NF - 1 || !(f & 2u)) && (j < NF - 1 || !(f & 8u));
     if (!own_xy) continue;
+    const int* gm = map_f + (size_t)(e0 + s) * NF3 + j * NF + i;
 #pragma unroll
     for (int k = 0; k < NF; ++k) {
-      if (k == NF - 1 && ez != nz - 1) continue;
-      const int g = map_f[(size_t)e * NF3 + (k * NF + j) * NF + i];
+      if (k == NF - 1 && (f & 32u)) continue;
+      const int g = __ldg(gm + k * NF * NF);
       xf[g] += out[k];
       tf[g] = T(0);
     }
@@ -119,24 +153,35 @@ __global__ void __launch_bounds__(kTThreads)
   __shared__ T f0[E * NF3];
   __shared__ T s1[E * NF * NF * NC];  // [k_f][j_f][a]
   __shared__ T s2[E * NF * NC * NC];  // [k_f][b][a]
+  __shared__ unsigned char fl[E];
   const int e0 = blockIdx.x * E;
-  for (int idx = threadIdx.x; idx < E * NF3; idx += blockDim.x) {
-    const int s = idx / NF3, loc = idx - s * NF3, e = e0 + s;
-    T v = T(0);
-    if (e < nelem) {
-      const int i = loc % NF, j = (loc / NF) % NF, k = loc / (NF * NF);
-      const int ex = e % nx, ey = (e / nx) % ny, ez = e / (nx * ny);
-      // 1 / multiplicity of the node (elements sharing it): a power of two, exact
-      const T w = (((i == 0 && ex > 0) || (i == NF - 1 && ex < nx - 1)) ? T(0.5) : T(1)) *
-                  (((j == 0 && ey > 0) || (j == NF - 1 && ey < ny - 1)) ? T(0.5) : T(1)) *
-                  (((k == 0 && ez > 0) || (k == NF - 1 && ez < nz - 1)) ? T(0.5) : T(1));
-      const int g = map_f[(size_t)e * NF3 + loc];
-      v = (bf[g] - tf[g]) * w;
+  element_flags<E>(e0, nelem, nx, ny, nz, fl);
+  __syncthreads();
+  {
+    const int* gm = map_f + (size_t)e0 * NF3;
+    constexpr int IT = (E * NF3 + kTThreads - 1) / kTThreads;
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+      const int idx = threadIdx.x + it * kTThreads;
+      if (IT * kTThreads == E * NF3 || idx < E * NF3) {
+        const int s = idx / NF3, loc = idx - s * NF3;
+        const unsigned f = fl[s];
+        T v = T(0);
+        if (f & 64u) {
+          const int i = loc % NF, j = (loc / NF) % NF, k = loc / (NF * NF);
+          // 1 / multiplicity of the node (elements sharing it): a power of two, exact
+          const T w = (((i == 0 && (f & 1u)) || (i == NF - 1 && (f & 2u))) ? T(0.5) : T(1)) *
+                      (((j == 0 && (f & 4u)) || (j == NF - 1 && (f & 8u))) ? T(0.5) : T(1)) *
+                      (((k == 0 && (f & 16u)) || (k == NF - 1 && (f & 32u))) ? T(0.5) : T(1));
+          const int g = __ldg(gm + idx);
+          v = (bf[g] - tf[g]) * w;
+        }
+        f0[idx] = v;
+      }
     }
-    f0[idx] = v;
   }
   __syncthreads();
-  for (int w = threadIdx.x; w < E * NF * NF; w += blockDim.x) {  // x-lines (j_f, k_f)
+  for (int w = threadIdx.x; w < E * NF * NF; w += kTThreads) {  // x-lines (j_f, k_f)
     const int s = w / (NF * NF), l = w - s * NF * NF;
     T in[NF], out[NC];
 #pragma unroll
@@ -146,7 +191,7 @@ __global__ void __launch_bounds__(kTThreads)
     for (int a = 0; a < NC; ++a) s1[s * NF * NF * NC + l * NC + a] = out[a];
   }
   __syncthreads();
-  for (int w = threadIdx.x; w < E * NF * NC; w += blockDim.x) {  // y-lines (a, k_f)
+  for (int w = threadIdx.x; w < E * NF * NC; w += kTThreads) {  // y-lines (a, k_f)
     const int s = w / (NF * NC), l = w - s * NF * NC, a = l % NC, k = l / NC;
     T in[NF], out[NC];
 #pragma unroll
@@ -156,15 +201,16 @@ __global__ void __launch_bounds__(kTThreads)
     for (int b = 0; b < NC; ++b) s2[s * NF * NC * NC + (k * NC + b) * NC + a] = out[b];
   }
   __syncthreads();
-  for (int w = threadIdx.x; w < E * NC * NC; w += blockDim.x) {  // z-lines (a, b)
-    const int s = w / (NC * NC), l = w - s * NC * NC, a = l % NC, b = l / NC, e = e0 + s;
-    if (e >= nelem) continue;
+  for (int w = threadIdx.x; w < E * NC * NC; w += kTThreads) {  // z-lines (a, b)
+    const int s = w / (NC * NC), l = w - s * NC * NC, a = l % NC, b = l / NC;
+    if (!(fl[s] & 64u)) continue;
     T in[NF], out[NC];
 #pragma unroll
     for (int k = 0; k < NF; ++k) in[k] = s2[s * NF * NC * NC + (k * NC + b) * NC + a];
     down_line<NF, NC>(pm.P, in, out);
+    const int* gm = map_c + (size_t)(e0 + s) * NC3 + b * NC + a;
 #pragma unroll
-    for (int c = 0; c < NC; ++c) atomicAdd(bc + map_c[(size_t)e * NC3 + (c * NC + b) * NC + a], out[c]);
+    for (int c = 0; c < NC; ++c) atomicAdd(bc + __ldg(gm + c * NC * NC), out[c]);
   }
 }
 
