@@ -50,7 +50,7 @@ FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64: 152 SMs x 2 DFMA/clk x 2 flop x ~
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel on this
 # slab; an entry is removed whenever its kernel changes.
 #   FP64 CG apply: profiles/sem_apply_fp64_p4_semni_2M.md
-NCU_TRAFFIC = {(4, "LGL"): 273.100032e6 + 13.966848e6}
+NCU_TRAFFIC = {(4, "LGL"): 273.056256e6 + 13.388544e6}
 #   FP32 smoother apply (bf16 metric, pipelined warp kernel): profiles/sem_apply_pipe_bf16_p4_semni_2M.md
 NCU_TRAFFIC_SMOOTHER = {(4, "LGL", "bf16"): 94.769664e6 + 2.867968e6}
 
