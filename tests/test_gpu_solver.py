@@ -296,3 +296,62 @@ def test_df64_operator_in_cg_and_time_steps(quad, precond):
     u, _, _ = st.get()
     ref = _oracle_run(o, tissue, 0.05, 20, ("box", box), 50.0, 1.0)
     assert rel(u.cpu().numpy(), ref["u"]) < 1e-10
+
+
+def test_benchmark_time_step_full_size():
+    """The benchmarked mixed-precision time step on its full-size workload
+    (83 x 29 x 13 perturbed Q4 elements, 2,064,933 DOFs, SEM-NI, rotating
+    fibres, sphere stimulus): flexible FP64 PCG with the double-float operator,
+    bf16-metric V-cycle with Chebyshev(6) down to the first level of at most
+    300,000 nodes, rtol 1e-10.  After 20 steps (the stimulus has just ended)
+    one more step is checked:
+      - the gate update at every node against the oracle's BDF2 gate (Eq.
+        ionic_discr);
+      - the FP64 residual of the solved system (Eq. linsys) over all nodes, with
+        b from the oracle's right-hand side (Eq. matrix_rhs) and the mass
+        diagonal, and A u from the FP64 apply, whose rows at this size are
+        pinned to the oracle by test_sweep_workload_sampled_rows;
+      - the solution against the plain FP64 path's (FP64 operator, Jacobi-CG)
+        from the same state."""
+    dt, rtol = 0.05, 1e-10
+    s = W.sweep_slab(4)
+    ne = s.n_elements
+    tissue = (np.full(ne, 0.12), np.full(ne, 0.03), W.transmural_fiber_angles(s))
+    centre = W.seeded_point(s.lengths, 1.5, seed=W.SEED_STIM)
+    g = gb.Slab(s.flat_vertices(), s.nx, s.ny, s.nz, 4, "LGL")
+    g.set_tissue(*tissue)
+    g.set_ionic()
+    g.set_stimulus("sphere", (*centre, 1.5), 50.0, 0.0, 1.0)
+    capi.sem_set_gmg(g.ctx, 6, 6, 300000, gb.SEM_PREC_FP32_BF16)
+    capi.sem_set_operator_precision(g.ctx, gb.SEM_PREC_DF64)
+    st = g.new_state(-85.0, 1.0)
+    st.step(dt, 20, rtol=rtol, maxit=2000, precond=gb.SEM_PC_GMG)
+    ck = st.checkpoint()
+    assert ck["n"] == 20
+    st.step(dt, 1, rtol=rtol, maxit=2000, precond=gb.SEM_PC_GMG)  # t = 1.05 ms: no stimulus
+    u1, h1, n1 = st.get()
+    assert n1 == 21
+    un, unm1, hn, hnm1 = (ck[k].cpu().numpy() for k in ("u", "u_prev", "h", "h_prev"))
+    assert un.max() > -40.0  # the stimulated region has depolarised: the step is nonlinear
+
+    prm = ionic.DEFAULT_PARAMS
+    us = 2.0 * un - unm1
+    h_ref = ionic.gate_bdf2(hn, hnm1, us, dt, prm)
+    assert np.abs(h1.cpu().numpy() - h_ref).max() < 1e-13
+
+    alpha = 1.5 / dt
+    mdiag = g.diagonal(1.0, 0.0).cpu().numpy()
+    b = mdiag * ((4.0 * un - unm1) / (2.0 * dt) - ionic.i_ion(us, h_ref, prm))
+    r = b - g.apply(u1, alpha, 1.0).cpu().numpy()
+    assert np.linalg.norm(r) <= 2.0 * rtol * np.linalg.norm(b)
+
+    capi.sem_set_operator_precision(g.ctx, gb.SEM_PREC_FP64)
+    st64 = g.new_state(-85.0, 1.0)
+    st64.restore(ck)
+    st64.step(dt, 1, rtol=rtol, maxit=2000, precond=gb.SEM_PC_JACOBI)
+    u64, _, _ = st64.get()
+    assert rel(u1.cpu().numpy(), u64.cpu().numpy()) < 1e-8
+    st64.close()
+    st.close()
+    g.close()
+    torch.cuda.empty_cache()
