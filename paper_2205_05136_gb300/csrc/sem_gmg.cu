@@ -88,6 +88,16 @@ int grid1d(int64_t n) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 8));
 }
 
+// Grid of a kernel that moves K entries per thread and iteration (16-byte
+// chunks): one thread per chunk up to 8 CTAs per SM.  On a small level a grid
+// sized by entries would launch 4x the CTAs, most of them without work.
+template <typename T>
+int grid_chunks(int64_t n) {
+  constexpr int K = 16 / (int)sizeof(T);
+  const int64_t g = (n / K + kThreads - 1) / kThreads;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 8));
+}
+
 #define GRID_LOOP(i, n)                                                          \
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); \
        i += (int64_t)gridDim.x * blockDim.x)
@@ -632,7 +642,7 @@ template <typename T>
 int restrict_to(sem_ctx* ctx, Gmg& g, int l, const int* done, cudaStream_t s) {
   GmgLevel& F = g.lv[l];
   GmgLevel& C = g.lv[l + 1];
-  k_zero<T><<<grid1d(C.L->ndofs), kThreads, 0, s>>>(C.L->ndofs, (T*)C.b, done);
+  k_zero<T><<<grid_chunks<T>(C.L->ndofs), kThreads, 0, s>>>(C.L->ndofs, (T*)C.b, done);
   if (F.to_next == 0) {
     const PTab tab = make_ptab(*F.L, *C.L);
     GMG_CK(p_transfer<T>(false, *F.L, *C.L, tab.P, (const T*)F.b, (const T*)F.t, (T*)C.b, nullptr,
@@ -679,7 +689,7 @@ int chebyshev(sem_ctx* ctx, Gmg& g, int l, int degree, bool zero_start, const in
   T* b = (T*)V.b; T* x = (T*)V.x; T* t = (T*)V.t; T* d = (T*)V.d; const T* invd = (const T*)V.invd;
   int k0 = 0;
   if (zero_start) {
-    k_cheb_zero_start<T><<<grid1d(n), kThreads, 0, s>>>(n, b, invd, x, d, t, (T)(1.0 / theta), done);
+    k_cheb_zero_start<T><<<grid_chunks<T>(n), kThreads, 0, s>>>(n, b, invd, x, d, t, (T)(1.0 / theta), done);
     GMG_CK(cudaGetLastError());
     ctx->launches += 1;
     k0 = 1;
@@ -688,11 +698,12 @@ int chebyshev(sem_ctx* ctx, Gmg& g, int l, int degree, bool zero_start, const in
     int rc = level_apply(ctx, L, g.precision, g.alpha, x, t, done, s);
     if (rc != SEM_OK) return rc;
     if (k == 0) {
-      k_cheb_step<T><<<grid1d(n), kThreads, 0, s>>>(n, b, invd, x, d, t, (T)0, (T)(1.0 / theta), 1, done);
+      k_cheb_step<T><<<grid_chunks<T>(n), kThreads, 0, s>>>(n, b, invd, x, d, t, (T)0, (T)(1.0 / theta), 1,
+                                                           done);
     } else {
       const double rho = 1.0 / (2.0 * sigma - rho_old);
-      k_cheb_step<T><<<grid1d(n), kThreads, 0, s>>>(n, b, invd, x, d, t, (T)(rho * rho_old),
-                                                    (T)(2.0 * rho / delta), 0, done);
+      k_cheb_step<T><<<grid_chunks<T>(n), kThreads, 0, s>>>(n, b, invd, x, d, t, (T)(rho * rho_old),
+                                                           (T)(2.0 * rho / delta), 0, done);
       rho_old = rho;
     }
     GMG_CK(cudaGetLastError());
