@@ -1074,10 +1074,10 @@ int pcg_t(sem_ctx* ctx, Gmg& g, double alpha, const double* b, double* x, double
   bool done_h = false;
   int launched = 0;
   // Successive solves (time steps) take about the same number of iterations:
-  // launch all but the last of the previous count before reading the scalars,
-  // which saves host round trips.  An iteration launched after convergence runs
-  // kernels that return at once.
-  const int ahead = std::min(maxit, std::max(0, gr->last_iters - 1));
+  // launch the previous count before reading the scalars, so that a solve that
+  // needs no more costs one host round trip.  An iteration launched after
+  // convergence runs kernels that return at once.
+  const int ahead = std::min(maxit, std::max(0, gr->last_iters));
   for (; launched < ahead; ++launched) {
     GMG_CK(cudaGraphLaunch(gr->iter, s));
     ctx->launches += gr->iter_kernels;
