@@ -829,9 +829,10 @@ def main():
     ap.add_argument("--mg-degree", type=int, default=6)
     # tuned on the 2 M DOF slab at dt = 0.05 ms (mass-dominated operator): a degree-6
     # Chebyshev smoother on the p = 4 level and the p = 2 level (266,085 nodes) as the
-    # coarsest level, smoothed by Chebyshev(6), give 3 PCG iterations per step and the
-    # shortest step time
-    ap.add_argument("--mg-coarse-degree", type=int, default=6)
+    # coarsest level, smoothed by Chebyshev(5), give 3 PCG iterations per step and the
+    # shortest step time with that count (coarse degrees 2..8: 3.13, 4, 3.17, 3, 3, -, 3
+    # iterations)
+    ap.add_argument("--mg-coarse-degree", type=int, default=5)
     ap.add_argument("--mg-min-coarse-dofs", type=int, default=300000)
     ap.add_argument("--workload", default="timestep", choices=["timestep", "gmg8m", "mixed30m", "adjoint"],
                     help="extra measurements of the multigrid, mixed-precision and adjoint workloads")
