@@ -144,6 +144,13 @@ class ClockSampler:
                 "samples": len(mhz)}
 
 
+def workload_name(p, quad, s, ndofs):
+    """The workload string of the JSON line's config (the same for both arms)."""
+    return (f"monodomain BDF2 time step, {'SEM-NI' if quad == 'LGL' else 'SEM'} Q{p} slab "
+            f"20x7x3 mm, {s.nx}x{s.ny}x{s.nz} hexahedra, {ndofs} DOFs, +-10% vertex perturbation, "
+            f"fibres -60..+60 deg, dt {DT} ms, CG rtol {RTOL}")
+
+
 def workload(p=4):
     s = W.sweep_slab(p)
     ne = s.n_elements
@@ -457,9 +464,7 @@ def run_gpu(args):
                   f"{MG_DTYPE[args.mg_precision]} multigrid V-cycle"),
         "data": "synthetic",
         "config": {
-            "workload": (f"monodomain BDF2 time step, {'SEM-NI' if quad == 'LGL' else 'SEM'} Q{p} slab "
-                         f"20x7x3 mm, {s.nx}x{s.ny}x{s.nz} hexahedra, {n_d} DOFs, +-10% vertex perturbation, "
-                         f"fibres -60..+60 deg, dt {DT} ms, CG rtol {RTOL}"),
+            "workload": workload_name(p, quad, s, n_d),
             "solver": (f"flexible FP64 PCG ({args.op_precision} operator) + {args.mg_precision} GMG V-cycle "
                        f"(p-then-h coarsening down to {args.mg_min_coarse_dofs} nodes, "
                        f"Chebyshev({args.mg_degree}), coarse Chebyshev({args.mg_coarse_degree}))"),
@@ -795,12 +800,12 @@ def run_reference(args):
               f"at once, ~{per_step:.0f} s each over this slab's {nel} elements, scaled to a full time step of "
               f"{applies} applies")
     line = {
-        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0,
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"monodomain time step, SEM-NI Q{p} slab {s.nx}x{s.ny}x{s.nz}, {ndofs} DOFs",
-                   "p": p, "quadrature": quad},
+        "config": {"workload": workload_name(p, quad, s, ndofs), "p": p, "quadrature": quad,
+                   "ndofs": ndofs, "nelem": nel},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
