@@ -15,6 +15,10 @@ itself:
 * The printed Niederer DOF and cell counts.
 * Assembled sparse operator (Algorithm 2) == element-by-element apply ==
   sampled rows.
+* The conductivity tensor (Eq. diffusiontensor): eigenvalue sigma_l along the
+  fibre (cos theta, sin theta, 0) and sigma_t across it, diagonal at theta = 0
+  and pi/2; and through the assembled K, the energy of a linear field along
+  and across the fibre is the volume times sigma_l and sigma_t.
 """
 import os
 
@@ -219,3 +223,42 @@ def test_global_stiffness_annihilates_constants():
         sp_ = _space(s, 3, quad)
         K = Mh.assemble(sp_, tissue, 0.0, 1.0)
         assert np.abs(K @ np.ones(sp_.ndofs)).max() < 1e-14 * abs(K).max()
+
+
+def test_diffusion_tensor_eigenstructure():
+    """Eq. (diffusiontensor), transversely isotropic: the fibre direction
+    f = (cos theta, sin theta, 0) is an eigenvector with eigenvalue sigma_l, and
+    the plane normal to it (the sheet direction and the z axis) carries sigma_t.
+    The axis-aligned angles fix the orientation convention."""
+    sl, st = 0.12, 0.03
+    assert np.allclose(E.diffusion_tensor(sl, st, 0.0), np.diag([sl, st, st]), atol=1e-17)
+    assert np.allclose(E.diffusion_tensor(sl, st, np.pi / 2), np.diag([st, sl, st]), atol=1e-17)
+    for theta in (0.3, -1.1, 2.5):
+        D = E.diffusion_tensor(sl, st, theta)
+        assert np.abs(D - D.T).max() == 0.0
+        w, V = np.linalg.eigh(D)
+        assert np.allclose(w, [st, st, sl], atol=1e-16)
+        lead = V[:, 2] * np.sign(V[0, 2])
+        ref = np.array([np.cos(theta), np.sin(theta), 0.0]) * np.sign(np.cos(theta))
+        assert np.allclose(lead, ref, atol=1e-14)
+
+
+@pytest.mark.parametrize("quad", ["LG", "LGL"])
+def test_linear_field_energy_follows_the_fibre(quad):
+    """For u = a . x on a box with a constant fibre angle, u^T K u is the volume
+    times a^T D a: sigma_l along the fibre, sigma_t across it in the plane and
+    along z.  This ties the per-element angle of the tissue arrays, through the
+    assembled stiffness, to the physical fibre direction."""
+    L = (2.0, 1.5, 1.0)
+    vol = L[0] * L[1] * L[2]
+    s = W.slab(2, 2, 1, L)
+    sl, st, theta = 0.12, 0.03, 0.6
+    for p in (1, 2):
+        sp_ = _space(s, p, quad)
+        _, K = Mh.assemble_mass_stiffness(sp_, W.constant_tissue(s, sl, st, theta))
+        xyz = sp_.dof_coordinates()
+        along = np.array([np.cos(theta), np.sin(theta), 0.0])
+        across = np.array([-np.sin(theta), np.cos(theta), 0.0])
+        for a, sigma in ((along, sl), (across, st), (np.array([0.0, 0.0, 1.0]), st)):
+            u = xyz @ a
+            assert abs(u @ (K @ u) - vol * sigma) < 1e-12 * vol * sigma, (p, a)
