@@ -7,7 +7,11 @@ the paper is unpinned; what is pinned here is the scheme around it:
   (checked with scipy's bracketing root finder on the residual);
 * the single-cell partitioned scheme converges to a fine RK4 solution with
   order 2 in dt;
-* rest state: I_ion(u_rest, h) = 0.
+* rest state: I_ion(u_rest, h) = 0;
+* the excitation threshold is the smaller root of the open-gate rate (closed
+  form), with return to rest below it and an upstroke above it;
+* the gate opens with tau_open below the gate voltage and closes with
+  tau_close above it.
 """
 import numpy as np
 import pytest
@@ -58,3 +62,30 @@ def test_action_potential_fires():
     """A supra-threshold start produces an upstroke towards u_rest + u_amp."""
     y = ionic.single_cell_semi_implicit(-60.0, 1.0, 2.0, 0.01, PRM)
     assert y[0] > -10.0
+
+
+def test_excitation_threshold_is_the_model_root():
+    """With the gate open (h = 1) the normalised potential's rate is
+    v^2 (1 - v) / tau_in - v / tau_out, which vanishes at the threshold
+    v_th = (1 - sqrt(1 - 4 tau_in / tau_out)) / 2 (the smaller nonzero root).
+    Starting just below it the cell returns to rest; just above it, it fires."""
+    tin, tout = PRM["tau_in"], PRM["tau_out"]
+    v_th = 0.5 * (1.0 - np.sqrt(1.0 - 4.0 * tin / tout))
+    u_th = PRM["u_rest"] + PRM["u_amp"] * v_th
+    assert abs(float(ionic.i_ion(u_th, 1.0, PRM))) < 1e-12 * PRM["u_amp"]
+    # near the unstable root the motion is slow: 40 ms to settle, 20 ms to fire
+    below = ionic.single_cell_semi_implicit(u_th - 1.0, 1.0, 40.0, 0.01, PRM)
+    above = ionic.single_cell_semi_implicit(u_th + 1.0, 1.0, 20.0, 0.01, PRM)
+    assert abs(below[0] - PRM["u_rest"]) < 0.5
+    assert above[0] > PRM["u_rest"] + 0.7 * PRM["u_amp"]
+
+
+def test_gate_opens_below_and_closes_above_the_gate_voltage():
+    """dh/dt -> (1 - h) / tau_open well below v_gate (the gate opens) and
+    -h / tau_close well above it (the gate closes), up to the logistic switch's
+    exponentially small overlap."""
+    for h in (0.1, 0.6, 0.95):
+        low = float(ionic.gate_rhs(PRM["u_rest"], h, PRM))
+        high = float(ionic.gate_rhs(PRM["u_rest"] + PRM["u_amp"] * 0.6, h, PRM))
+        assert abs(low - (1.0 - h) / PRM["tau_open"]) < 1e-7
+        assert abs(high + h / PRM["tau_close"]) < 1e-7

@@ -1,17 +1,25 @@
-"""Planted mistakes in the oracle's operator, on the CPU.
+"""Planted mistakes in the oracle, on the CPU.
 
-Each mutation is a plausible slip in the definition the oracle writes out
-(Sections 2-4): a transposed inverse Jacobian, a dropped |det J|, a flipped
-fibre angle, a sheet direction that is not orthogonal to the fibre, a
-transposed derivative table.  With the mutation in place, at least one pin of
-test_oracle_operator must fail; without it, all of them pass.  The test
-measures the pins, not the oracle, and leaves the oracle as it found it.
+Each mutation is a plausible slip in a definition the oracle writes out.
+- Operator (Sections 2-4): a transposed inverse Jacobian, a dropped |det J|,
+  a flipped fibre angle, a sheet direction that is not orthogonal to the
+  fibre, a transposed derivative table.
+- Stand-in ionic model and its gate update (Eq. ionic_discr): a wrong sign of
+  the outward current, swapped gate time constants, a wrong sign of the BDF2
+  history term.
+With the mutation in place at least one pin of test_oracle_operator or
+test_oracle_ionic must fail; without it all of them pass.  The test measures
+the pins, not the oracle, and leaves the oracle as it found it.
 """
+import warnings
+
 import numpy as np
 import pytest
 
+import test_oracle_ionic as TI
 import test_oracle_operator as T
 from oracle import element as E
+from oracle import ionic as I
 from oracle import mesh as Mh
 
 
@@ -90,6 +98,61 @@ def _patch(monkeypatch, name, fn):
 def test_pins_pass_on_the_oracle():
     E.basis_tables.cache_clear()
     assert _pins() == []
+    assert _ionic_pins() == []
+
+
+# ---------------------------------------------------------------- ionic model
+def _ionic_pins():
+    checks = [("BDF gate u=%g" % u, (lambda u=u: TI.test_gate_updates_solve_bdf_equations(u)))
+              for u in (-85.0, -60.0, 10.0)]
+    checks += [("rest", TI.test_rest_state_is_equilibrium_of_the_potential),
+               ("threshold", TI.test_excitation_threshold_is_the_model_root),
+               ("gate direction", TI.test_gate_opens_below_and_closes_above_the_gate_voltage),
+               ("fires", TI.test_action_potential_fires)]
+    failed = []
+    for name, fn in checks:
+        try:
+            with warnings.catch_warnings(), np.errstate(all="ignore"):
+                warnings.simplefilter("ignore")  # a planted mistake may blow the single cell up
+                fn()
+        except (AssertionError, ValueError, FloatingPointError):
+            failed.append(name)
+    return failed
+
+
+_i_ion = I.i_ion
+_gate_rates = I.gate_rates
+
+
+def _i_ion_outward_sign(u, h, prm):  # planted: the outward term with the wrong sign
+    v = I.normalised(u, prm)
+    return -prm["u_amp"] * (h * v * v * (1.0 - v) / prm["tau_in"] + v / prm["tau_out"])
+
+
+def _gate_rates_swapped(u, prm):  # planted: opening and closing time constants swapped
+    s_ = I.switch(u, prm)
+    return (1.0 - s_) / prm["tau_close"], s_ / prm["tau_open"]
+
+
+def _gate_bdf2_history_sign(h_n, h_nm1, u_star, dt, prm):  # planted: + h^{n-1}
+    a, b = _gate_rates(u_star, prm)
+    return (4.0 * h_n + h_nm1 + 2.0 * dt * a) / (3.0 + 2.0 * dt * (a + b))
+
+
+IONIC_MUTATIONS = {
+    "outward current sign": ("i_ion", _i_ion_outward_sign),
+    "gate time constants swapped": ("gate_rates", _gate_rates_swapped),
+    "BDF2 gate history sign": ("gate_bdf2", _gate_bdf2_history_sign),
+}
+
+
+@pytest.mark.parametrize("mutation", sorted(IONIC_MUTATIONS))
+def test_each_planted_ionic_mistake_fails_a_pin(mutation, monkeypatch):
+    name, fn = IONIC_MUTATIONS[mutation]
+    with monkeypatch.context() as m:
+        m.setattr(I, name, fn)
+        failed = _ionic_pins()
+    assert failed, f"no pin caught: {mutation}"
 
 
 @pytest.mark.parametrize("mutation", sorted(MUTATIONS))
