@@ -7,8 +7,12 @@ Each mutation is a plausible slip in a definition the oracle writes out.
 - Stand-in ionic model and its gate update (Eq. ionic_discr): a wrong sign of
   the outward current, swapped gate time constants, a wrong sign of the BDF2
   history term.
-With the mutation in place at least one pin of test_oracle_operator or
-test_oracle_ionic must fail; without it all of them pass.  The test measures
+- Time step (Eqs. monodomain_discr - linsys): the ionic current at u^n
+  instead of the extrapolated u*, the BDF1 matrix in BDF2 steps, a wrong sign
+  of the history term, an applied current without the mass weighting.
+With the mutation in place at least one pin of test_oracle_operator,
+test_oracle_ionic or test_oracle_convergence must fail; without it all of
+them pass.  The test measures
 the pins, not the oracle, and leaves the oracle as it found it.
 """
 import warnings
@@ -16,11 +20,13 @@ import warnings
 import numpy as np
 import pytest
 
+import test_oracle_convergence as TC
 import test_oracle_ionic as TI
 import test_oracle_operator as T
 from oracle import element as E
 from oracle import ionic as I
 from oracle import mesh as Mh
+from oracle import monodomain as MD
 
 
 def _pins():
@@ -166,3 +172,60 @@ def test_each_planted_mistake_fails_a_pin(mutation, monkeypatch):
     finally:
         E.basis_tables.cache_clear()
     assert failed, f"no pin caught: {mutation}"
+
+
+# ---------------------------------------------------------------- time step
+
+
+def _step_with(slip):
+    """Monodomain.step (Eqs. ionic_discr - linsys) with one planted slip."""
+    def step(self, state):
+        dt, model = self.dt, self.model
+        u_n, u_nm1, h_n, h_nm1, n = state["u"], state["u_prev"], state["h"], state["h_prev"], state["n"]
+        t1 = (n + 1) * dt
+        if n == 0:
+            us = u_n
+            h1 = model.gate_first(h_n, us, dt)
+            alpha = 1.0 / dt
+            hist = self.M @ (u_n / dt)
+        else:
+            us = u_n if slip == "no extrapolation" else 2.0 * u_n - u_nm1
+            h1 = model.gate(h_n, h_nm1, us, dt)
+            alpha = 1.0 / dt if slip == "BDF1 matrix in BDF2 steps" else 3.0 / (2.0 * dt)
+            sgn = 1.0 if slip == "history sign" else -1.0
+            hist = self.M @ ((4.0 * u_n + sgn * u_nm1) / (2.0 * dt))
+        s = -(self.M @ model.current(us, h1))
+        f = self.i_app(t1) if slip == "unweighted applied current" else self.M @ self.i_app(t1)
+        u1 = self._solve(alpha, hist + s + f)
+        return dict(u=u1, u_prev=u_n.copy(), h=h1, h_prev=h_n.copy(), n=n + 1)
+    return step
+
+
+STEP_SLIPS = ["no extrapolation", "BDF1 matrix in BDF2 steps", "history sign", "unweighted applied current"]
+
+
+def _step_pins():
+    failed = []
+    for name, fn in (("BDF2 order LG", lambda: TC.test_bdf2_time_order("LG")),
+                     ("uniform state", TC.test_uniform_state_reduces_to_single_cell)):
+        try:
+            with warnings.catch_warnings(), np.errstate(all="ignore"):
+                warnings.simplefilter("ignore")
+                fn()
+        except (AssertionError, ValueError, FloatingPointError):
+            failed.append(name)
+    return failed
+
+
+def test_step_pins_pass_on_the_oracle(monkeypatch):
+    with monkeypatch.context() as m:
+        m.setattr(MD.Monodomain, "step", _step_with(None))  # the copy above, unplanted
+        assert _step_pins() == []
+
+
+@pytest.mark.parametrize("slip", STEP_SLIPS)
+def test_each_planted_time_step_mistake_fails_a_pin(slip, monkeypatch):
+    with monkeypatch.context() as m:
+        m.setattr(MD.Monodomain, "step", _step_with(slip))
+        failed = _step_pins()
+    assert failed, f"no pin caught: {slip}"
