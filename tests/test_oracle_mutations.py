@@ -10,9 +10,11 @@ Each mutation is a plausible slip in a definition the oracle writes out.
 - Time step (Eqs. monodomain_discr - linsys): the ionic current at u^n
   instead of the extrapolated u*, the BDF1 matrix in BDF2 steps, a wrong sign
   of the history term, an applied current without the mass weighting.
-With the mutation in place at least one pin of test_oracle_operator,
-test_oracle_ionic or test_oracle_convergence must fail; without it all of
-them pass.  The test measures
+- Multigrid (Section 4.3): a wrong Chebyshev momentum coefficient, one
+  post-smoothing step too many, the Lanczos off-diagonal without its square
+  root.
+With the mutation in place at least one pin of the oracle's tests must fail;
+without it all of them pass.  The test measures
 the pins, not the oracle, and leaves the oracle as it found it.
 """
 import warnings
@@ -22,11 +24,13 @@ import pytest
 
 import test_oracle_convergence as TC
 import test_oracle_ionic as TI
+import test_oracle_multigrid as TG
 import test_oracle_operator as T
 from oracle import element as E
 from oracle import ionic as I
 from oracle import mesh as Mh
 from oracle import monodomain as MD
+from oracle import multigrid as MG
 
 
 def _pins():
@@ -229,3 +233,98 @@ def test_each_planted_time_step_mistake_fails_a_pin(slip, monkeypatch):
         m.setattr(MD.Monodomain, "step", _step_with(slip))
         failed = _step_pins()
     assert failed, f"no pin caught: {slip}"
+
+
+# ---------------------------------------------------------------- multigrid
+
+_chebyshev = MG.chebyshev
+
+
+def _chebyshev_slipped(A, dinv, b, x0, degree, lo, hi):  # planted: rho for rho * rho_old
+    theta, delta = 0.5 * (hi + lo), 0.5 * (hi - lo)
+    sigma = theta / delta
+    x = np.zeros_like(b) if x0 is None else x0.copy()
+    r = b - A @ x if x0 is not None else b.copy()
+    d = dinv * r / theta
+    x += d
+    rho_old = 1.0 / sigma
+    for _ in range(1, degree):
+        r = b - A @ x
+        rho = 1.0 / (2.0 * sigma - rho_old)
+        d = rho * d + (2.0 * rho / delta) * (dinv * r)
+        x += d
+        rho_old = rho
+    return x
+
+
+def _vcycle_post_off_by_one(self, b, level=0):  # planted: one more post-smoothing step
+    A, dinv = self.A[level], self.dinv[level]
+    lo, hi = self.range[level]
+    if level == self.nlevels - 1:
+        return _chebyshev(A, dinv, b, None, self.coarse_degree, lo, hi)
+    x = _chebyshev(A, dinv, b, None, self.degree, lo, hi)
+    r = b - A @ x
+    xc = self.vcycle(self.P[level].T @ r, level + 1)
+    x = x + self.P[level] @ xc
+    return _chebyshev(A, dinv, b, x, self.degree + 1, lo, hi)
+
+
+def _lanczos_no_sqrt(A, dinv, iters=10):  # planted: beta for sqrt(beta) off the diagonal
+    n = A.shape[0]
+    r = MG.start_vector(n)
+    z = dinv * r
+    p = z.copy()
+    rz = r @ z
+    alphas, betas = [], []
+    for _ in range(min(iters, n)):
+        Ap = A @ p
+        alpha = rz / (p @ Ap)
+        r = r - alpha * Ap
+        z = dinv * r
+        rz_new = r @ z
+        beta = rz_new / rz
+        alphas.append(alpha)
+        betas.append(beta)
+        rz = rz_new
+        p = z + beta * p
+    k = len(alphas)
+    T = np.zeros((k, k))
+    for j in range(k):
+        T[j, j] = 1.0 / alphas[j] + (betas[j - 1] / alphas[j - 1] if j > 0 else 0.0)
+        if j + 1 < k:
+            T[j, j + 1] = T[j + 1, j] = betas[j] / alphas[j]
+    return float(np.linalg.eigvalsh(T).max())
+
+
+MG_MUTATIONS = {
+    "Chebyshev momentum coefficient": (MG, "chebyshev", _chebyshev_slipped),
+    "post-smoothing degree off by one": (MG.Hierarchy, "vcycle", _vcycle_post_off_by_one),
+    "Lanczos off-diagonal without the square root": (MG, "lanczos_lambda_max", _lanczos_no_sqrt),
+}
+
+
+def _mg_pins():
+    failed = []
+    for name, fn in (("Chebyshev polynomial", lambda: TG.test_chebyshev_error_polynomial(3)),
+                     ("Lanczos bounds", TG.test_lanczos_estimate_bounds_lambda_max),
+                     ("V-cycle symmetric, PCG", lambda: TG.test_vcycle_symmetric_and_pcg_converges("LGL"))):
+        try:
+            with warnings.catch_warnings(), np.errstate(all="ignore"):
+                warnings.simplefilter("ignore")
+                fn()
+        except (AssertionError, ValueError, FloatingPointError, np.linalg.LinAlgError):
+            failed.append(name)
+    return failed
+
+
+def test_mg_pins_pass_on_the_oracle():
+    assert _mg_pins() == []
+
+
+@pytest.mark.parametrize("mutation", sorted(MG_MUTATIONS))
+def test_each_planted_multigrid_mistake_fails_a_pin(mutation, monkeypatch):
+    target, name, fn = MG_MUTATIONS[mutation]
+    with monkeypatch.context() as m:
+        m.setattr(target, name, fn)
+        failed = _mg_pins()
+    assert failed, f"no pin caught: {mutation}"
