@@ -13,19 +13,23 @@ Each mutation is a plausible slip in a definition the oracle writes out.
 - Multigrid (Section 4.3): a wrong Chebyshev momentum coefficient, one
   post-smoothing step too many, the Lanczos off-diagonal without its square
   root.
+- Activation times (Eq. tau): a wrong BDF2 derivative coefficient, ties that
+  keep the latest step, the derivative attached to the older time level.
 With the mutation in place at least one pin of the oracle's tests must fail;
-without it all of them pass.  The test measures
-the pins, not the oracle, and leaves the oracle as it found it.
+without it all of them pass.  The test measures the pins, not the oracle, and
+leaves the oracle as it found it.
 """
 import warnings
 
 import numpy as np
 import pytest
 
+import test_oracle_activation as TA
 import test_oracle_convergence as TC
 import test_oracle_ionic as TI
 import test_oracle_multigrid as TG
 import test_oracle_operator as T
+from oracle import activation as ACT
 from oracle import element as E
 from oracle import ionic as I
 from oracle import mesh as Mh
@@ -327,4 +331,60 @@ def test_each_planted_multigrid_mistake_fails_a_pin(mutation, monkeypatch):
     with monkeypatch.context() as m:
         m.setattr(target, name, fn)
         failed = _mg_pins()
+    assert failed, f"no pin caught: {mutation}"
+
+
+# ---------------------------------------------------------------- activation times
+
+_scheme_derivative = ACT.scheme_derivative
+
+
+def _derivative_bdf2_coefficient(u_new, u_cur, u_old, n_new, dt):  # planted: 3, -4, +1 -> 3, -4, -1
+    if n_new == 1:
+        return (u_new - u_cur) / dt
+    return (3.0 * u_new - 4.0 * u_cur - u_old) / (2.0 * dt)
+
+
+def _update_ties_latest(self, u_new, u_cur, u_old, n_new, dt):  # planted: >= keeps the latest tie
+    d = np.abs(ACT.scheme_derivative(u_new, u_cur, u_old, n_new, dt))
+    later = d >= self.dmax
+    self.dmax[later] = d[later]
+    self.tau[later] = n_new * dt
+
+
+def _update_time_of_older_level(self, u_new, u_cur, u_old, n_new, dt):  # planted: t^n for t^{n+1}
+    d = np.abs(ACT.scheme_derivative(u_new, u_cur, u_old, n_new, dt))
+    later = d > self.dmax
+    self.dmax[later] = d[later]
+    self.tau[later] = (n_new - 1) * dt
+
+
+ACT_MUTATIONS = {
+    "BDF2 derivative coefficient": (ACT, "scheme_derivative", _derivative_bdf2_coefficient),
+    "ties keep the latest step": (ACT.ActivationTracker, "update", _update_ties_latest),
+    "derivative attached to the older time": (ACT.ActivationTracker, "update", _update_time_of_older_level),
+}
+
+
+def _act_pins():
+    failed = []
+    for name, fn in (("quadratics", TA.test_bdf_derivatives_exact_on_quadratics),
+                     ("front brute force", TA.test_front_arrival_brute_force)):
+        try:
+            fn()
+        except AssertionError:
+            failed.append(name)
+    return failed
+
+
+def test_activation_pins_pass_on_the_oracle():
+    assert _act_pins() == []
+
+
+@pytest.mark.parametrize("mutation", sorted(ACT_MUTATIONS))
+def test_each_planted_activation_mistake_fails_a_pin(mutation, monkeypatch):
+    target, name, fn = ACT_MUTATIONS[mutation]
+    with monkeypatch.context() as m:
+        m.setattr(target, name, fn)
+        failed = _act_pins()
     assert failed, f"no pin caught: {mutation}"
