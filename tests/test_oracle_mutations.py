@@ -15,6 +15,8 @@ Each mutation is a plausible slip in a definition the oracle writes out.
   root.
 - Activation times (Eq. tau): a wrong BDF2 derivative coefficient, ties that
   keep the latest step, the derivative attached to the older time level.
+- Adjoint: the conductivity tensor's theta derivative with the wrong sign,
+  the sigma_l and sigma_t derivatives swapped.
 With the mutation in place at least one pin of the oracle's tests must fail;
 without it all of them pass.  The test measures the pins, not the oracle, and
 leaves the oracle as it found it.
@@ -25,11 +27,13 @@ import numpy as np
 import pytest
 
 import test_oracle_activation as TA
+import test_oracle_adjoint as TAD
 import test_oracle_convergence as TC
 import test_oracle_ionic as TI
 import test_oracle_multigrid as TG
 import test_oracle_operator as T
 from oracle import activation as ACT
+from oracle import adjoint as AD
 from oracle import element as E
 from oracle import ionic as I
 from oracle import mesh as Mh
@@ -387,4 +391,44 @@ def test_each_planted_activation_mistake_fails_a_pin(mutation, monkeypatch):
     with monkeypatch.context() as m:
         m.setattr(target, name, fn)
         failed = _act_pins()
+    assert failed, f"no pin caught: {mutation}"
+
+
+# ---------------------------------------------------------------- adjoint
+_tissue_tensors = AD._tissue_tensors
+
+
+def _tensors_theta_sign(sl, st, th):  # planted: dD/dtheta with the wrong sign
+    ff, rest, dth = _tissue_tensors(sl, st, th)
+    return ff, rest, -dth
+
+
+def _tensors_swapped(sl, st, th):  # planted: dD/dsigma_l and dD/dsigma_t swapped
+    ff, rest, dth = _tissue_tensors(sl, st, th)
+    return rest, ff, dth
+
+
+AD_MUTATIONS = {
+    "dD/dtheta sign": _tensors_theta_sign,
+    "conductivity derivatives swapped": _tensors_swapped,
+}
+
+
+def _ad_pins():
+    try:
+        TAD.test_adjoint_gradient_matches_central_differences("LGL")
+    except AssertionError:
+        return ["central differences"]
+    return []
+
+
+def test_adjoint_pins_pass_on_the_oracle():
+    assert _ad_pins() == []
+
+
+@pytest.mark.parametrize("mutation", sorted(AD_MUTATIONS))
+def test_each_planted_adjoint_mistake_fails_a_pin(mutation, monkeypatch):
+    with monkeypatch.context() as m:
+        m.setattr(AD, "_tissue_tensors", AD_MUTATIONS[mutation])
+        failed = _ad_pins()
     assert failed, f"no pin caught: {mutation}"
