@@ -1,6 +1,8 @@
 """Planted mistakes in the oracle, on the CPU.
 
 Each mutation is a plausible slip in a definition the oracle writes out.
+- 1-D rules (Section 3): the GLL weight normalisation, Gauss weights without
+  their (1 - x^2) factor, a sign slip in the Lagrange derivative.
 - Operator (Sections 2-4): a transposed inverse Jacobian, a dropped |det J|,
   a flipped fibre angle, a sheet direction that is not orthogonal to the
   fibre, a transposed derivative table.
@@ -32,6 +34,7 @@ import test_oracle_convergence as TC
 import test_oracle_ionic as TI
 import test_oracle_multigrid as TG
 import test_oracle_operator as T
+import test_oracle_quadrature as TQ
 from oracle import activation as ACT
 from oracle import adjoint as AD
 from oracle import element as E
@@ -39,6 +42,7 @@ from oracle import ionic as I
 from oracle import mesh as Mh
 from oracle import monodomain as MD
 from oracle import multigrid as MG
+from oracle import quadrature as Q
 
 
 def _pins():
@@ -431,4 +435,72 @@ def test_each_planted_adjoint_mistake_fails_a_pin(mutation, monkeypatch):
     with monkeypatch.context() as m:
         m.setattr(AD, "_tissue_tensors", AD_MUTATIONS[mutation])
         failed = _ad_pins()
+    assert failed, f"no pin caught: {mutation}"
+
+
+# ---------------------------------------------------------------- quadrature
+_gll_rule = Q.gll_rule
+_gauss_rule = Q.gauss_rule
+_lagrange_deriv_q = Q.lagrange_deriv
+
+
+def _gll_weights_off(p):  # planted: 2 / (p (p - 1) P_p^2) instead of 2 / (p (p + 1) P_p^2)
+    x, w = _gll_rule(p)
+    return x, w * (p + 1) / max(p - 1, 1)
+
+
+def _gauss_weights_no_jacobian(n):  # planted: 2 / P'_n^2, the (1 - x^2) factor dropped
+    x, w = _gauss_rule(n)
+    return x, w * (1.0 - x * x)
+
+
+def _lagrange_deriv_wrong_factor(nodes, x):  # planted: one factor of each term inverted
+    nodes = np.asarray(nodes, dtype=np.float64)
+    x = np.atleast_1d(np.asarray(x, dtype=np.float64))
+    n = nodes.size
+    dL = np.zeros((n, x.size))
+    for i in range(n):
+        for m in range(n):
+            if m == i:
+                continue
+            term = np.full(x.size, 1.0 / (nodes[m] - nodes[i]))
+            for l in range(n):
+                if l != i and l != m:
+                    term *= (x - nodes[l]) / (nodes[i] - nodes[l])
+            dL[i] += term
+    return dL
+
+
+Q_MUTATIONS = {
+    "GLL weight normalisation": ("gll_rule", _gll_weights_off),
+    "Gauss weights without 1 - x^2": ("gauss_rule", _gauss_weights_no_jacobian),
+    "Lagrange derivative sign": ("lagrange_deriv", _lagrange_deriv_wrong_factor),
+}
+
+
+def _q_pins():
+    checks = [("GLL textbook", TQ.test_gll_textbook_values),
+              ("Gauss textbook", TQ.test_gauss_textbook_values),
+              ("derivative vs polyfit", TQ.test_lagrange_derivative_matches_numpy_polyfit)]
+    checks += [("LG exact p=%d" % p, (lambda p=p: TQ.test_lg_exactness_degree(p))) for p in (2, 4)]
+    checks += [("LGL exact p=%d" % p, (lambda p=p: TQ.test_lgl_exactness_degree(p))) for p in (2, 4)]
+    failed = []
+    for name, fn in checks:
+        try:
+            fn()
+        except AssertionError:
+            failed.append(name)
+    return failed
+
+
+def test_quadrature_pins_pass_on_the_oracle():
+    assert _q_pins() == []
+
+
+@pytest.mark.parametrize("mutation", sorted(Q_MUTATIONS))
+def test_each_planted_quadrature_mistake_fails_a_pin(mutation, monkeypatch):
+    name, fn = Q_MUTATIONS[mutation]
+    with monkeypatch.context() as m:
+        m.setattr(Q, name, fn)
+        failed = _q_pins()
     assert failed, f"no pin caught: {mutation}"
