@@ -5,7 +5,8 @@ Each mutation is a plausible slip in a definition the oracle writes out.
   their (1 - x^2) factor, a sign slip in the Lagrange derivative.
 - Operator (Sections 2-4): a transposed inverse Jacobian, a dropped |det J|,
   a flipped fibre angle, a sheet direction that is not orthogonal to the
-  fibre, a transposed derivative table.
+  fibre, a transposed derivative table; in the numbering, local i and j
+  exchanged, an element's y and z corners exchanged.
 - Stand-in ionic model and its gate update (Eq. ionic_discr): a wrong sign of
   the outward current, swapped gate time constants, a wrong sign of the BDF2
   history term.
@@ -503,4 +504,42 @@ def test_each_planted_quadrature_mistake_fails_a_pin(mutation, monkeypatch):
     with monkeypatch.context() as m:
         m.setattr(Q, name, fn)
         failed = _q_pins()
+    assert failed, f"no pin caught: {mutation}"
+
+
+# ---------------------------------------------------------------- numbering
+_element_dofs = Mh.SlabSpace.element_dofs
+
+
+def _element_dofs_i_j_swapped(self, e):  # planted: local i and j exchanged
+    ex, ey, ez = self.element_ijk(e)
+    n, p = self.n, self.p
+    k, j, i = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    g = (ex * p + j) + self.NX * ((ey * p + i) + self.NY * (ez * p + k))
+    return g.reshape(-1)
+
+
+def _element_vertices_b_c_swapped(self, e):  # planted: the y and z corners exchanged
+    ex, ey, ez = self.element_ijk(e)
+    X = np.empty((8, 3))
+    for c in range(2):
+        for b in range(2):
+            for a in range(2):
+                X[a + 2 * b + 4 * c] = self.V[ez + b, ey + c, ex + a]
+    return X
+
+
+NUMBERING_MUTATIONS = {
+    "local i and j exchanged": ("element_dofs", _element_dofs_i_j_swapped),
+    "element corners y and z exchanged": ("element_vertices", _element_vertices_b_c_swapped),
+}
+
+
+@pytest.mark.parametrize("mutation", sorted(NUMBERING_MUTATIONS))
+def test_each_planted_numbering_mistake_fails_a_pin(mutation, monkeypatch):
+    name, fn = NUMBERING_MUTATIONS[mutation]
+    E.basis_tables.cache_clear()
+    with monkeypatch.context() as m:
+        m.setattr(Mh.SlabSpace, name, fn)
+        failed = _pins()
     assert failed, f"no pin caught: {mutation}"
