@@ -63,3 +63,12 @@ def test_product_package_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".cpp", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without libsem.so the binding raises; it has no CPU fallback."""
+    from paper_2205_05136_gb300 import capi
+    monkeypatch.setattr(capi, "_LIB", None)
+    monkeypatch.setattr(capi, "LIB_PATH", str(tmp_path / "libsem.so"))
+    with pytest.raises(ImportError):
+        capi.lib()
