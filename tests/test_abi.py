@@ -72,3 +72,16 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(capi, "LIB_PATH", str(tmp_path / "libsem.so"))
     with pytest.raises(ImportError):
         capi.lib()
+
+
+def test_binding_rejects_host_and_mistyped_tensors():
+    """The binding checks vectors before any library call: CUDA memory,
+    contiguous, the right dtype and length."""
+    import torch
+    from paper_2205_05136_gb300 import capi
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        capi._dev(torch.zeros(4, dtype=torch.float64), torch.float64, 4, "u")
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        capi._dev([0.0] * 4, torch.float64, 4, "u")
+    with pytest.raises(ValueError, match="vertices"):
+        capi.sem_create(1, 1, 1, [0.0] * 23, 2, 1)
