@@ -18,7 +18,7 @@ def test_perturbed_slab_keeps_the_box():
     assert np.all(d[:, 0, :, 1] == 0) and np.all(d[:, -1, :, 1] == 0)
     assert np.all(d[0, :, :, 2] == 0) and np.all(d[-1, :, :, 2] == 0)
     # and the interior moves
-    assert np.abs(d[1:-1, 1:-1, 1:-1]).min() >= 0.0 and np.abs(d[1:-1, 1:-1, 1:-1]).max() > 0.05 * h.min()
+    assert np.abs(d[1:-1, 1:-1, 1:-1]).max() > 0.05 * h.min()
 
 
 def test_seeded_inputs_are_reproducible():
