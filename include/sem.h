@@ -283,19 +283,24 @@ int sem_adjoint_grad(sem_ctx* ctx, const double* trace_bar, double* g_sigma_l, d
 
 /* y = alpha M u + beta K u and *dot = u . y (FP64), without allocating.
  * The paper has no counterpart: this is a variant of the operator apply for
- * callers that cannot call cudaMalloc -- code running while a CUDA stream
- * capture is active, hosts that own every device allocation through their own
- * arena or budget, real-time loops that must not enter the allocator
- * (sem_cg_solve and sem_step allocate work vectors on first use; this call
- * never does).  u, y: device double[ndofs]; dot: device double[1]; the caller
- * passes all inputs and outputs.  beta must be finite and nonzero.
+ * callers that cannot let a library allocate device memory -- host frameworks
+ * that own every device allocation through their own arena or a fixed budget,
+ * and real-time loops that must not enter the allocator, whose calls can
+ * synchronise the device (sem_cg_solve and sem_step allocate work vectors on
+ * first use; this call never allocates).  u, y: device double[ndofs]; dot:
+ * device double[1]; the caller passes all inputs and outputs, and none of the
+ * three may overlap another (SEM_ERR_ARG).  beta must be finite and nonzero.
  * The grid reduction's scratch is one static device array of 65,536 per-CTA
- * partial sums (512 KiB per device that loads libsem, held until the process
- * exits); meshes needing more CTAs (more than 65,536 x E elements, E = 64,
- * 28, 16, 10, 7, 5 for p = 1..6) are rejected with SEM_ERR_ARG.  All calls
- * share that array: overlapping calls on the GPU race, so order them.  The
- * first call on a device looks up the array's address; make it before any
- * stream capture begins.  Asynchronous on stream. */
+ * partial sums (512 KiB in every CUDA context that loads libsem, held until
+ * the process exits); meshes needing more CTAs (more than 65,536 x E
+ * elements, E = 64, 28, 16, 10, 7, 5 for p = 1..6) are rejected with
+ * SEM_ERR_ARG.  The calls made in one CUDA context share that array and it
+ * keeps the last call's contents: calls that overlap on the GPU race on it,
+ * so order them.  The first call on a context looks up the array's address
+ * (the context's device current) and keeps it in ctx; make that first call
+ * before any stream capture begins.  After a cudaDeviceReset the contexts of
+ * that device, and the address, are invalid: create new ones.
+ * Asynchronous on stream. */
 int sem_apply_dot_static(sem_ctx* ctx, double alpha, double beta, const double* u, double* y,
                          double* dot, void* stream);
 
