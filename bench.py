@@ -4,22 +4,29 @@ One benchmark step = one full time step of the partitioned scheme
 (Section 3, Algorithm 1) on the ~2 M DOF operator-sweep slab at p = 4
 (20 x 7 x 3 mm, 83 x 29 x 13 hexahedra, 2,064,933 nodes, vertices perturbed by
 +-10 % of h, fibre angle rotating -60 -> +60 degrees through z):
-  fused ionic update + right-hand side  ->  Jacobi-CG to ||r|| <= 1e-10 ||b||
-  with one matrix-free operator apply per iteration.
+  fused ionic update + right-hand side  ->  flexible FP64 PCG to
+  ||r|| <= 1e-10 ||b|| with the mixed-precision multigrid V-cycle.
 
 Prints ONE JSON line (rank 0).  ``value`` is whole-job DOF-steps per second
-(nodes advanced by one time step per second, summed over ranks);
-``roofline`` describes the operator-apply kernel, timed live with CUDA events
-on its launching stream inside the timed region; ``cpu_baseline`` is the CPU
-oracle timed on a bounded sample of the same workload.
+(nodes advanced by one time step per second, summed over ranks) of the
+mixed-precision solver.  The same line carries
+  - the plain FP64 paths on the same slab from the same state: Jacobi-CG, and
+    multigrid PCG with an all-FP64 V-cycle on the same hierarchy (so the
+    precision speed-up is measured at equal preconditioning);
+  - ``roofline`` for the kernel that takes the most time in the step, timed
+    live with CUDA events on its launching stream inside the timed region;
+  - ``configs``: the other workloads, timed by CUDA events in the same run --
+    the p = 1..6 operator sweep (~2 M DOFs each), the 8.57 M DOF FP64-GMG
+    monodomain run, and the ~30 M DOF mixed-precision runs at p = 4 and 6;
+  - ``cpu_baseline``: the CPU oracle on the machine's host cores.
 
 ``--impl reference`` times the CPU oracle itself as the reference arm.
-``--sweep`` prints one extra JSON line per (p, quadrature) of the operator
-sweep (apply GDOF/s and roofline), not used by the default run.
+``--sweep`` / ``--workload`` run one of the extra workloads alone.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -47,12 +54,34 @@ SLAB_LENGTHS = W.SLAB_LENGTHS_MM
 MG_DTYPE = {"fp32": "f32", "bf16": "f32 arithmetic / bf16 metric", "fp64": "f64"}
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64: 152 SMs x 2 DFMA/clk x 2 flop x ~2.06 GHz
 
-# DRAM bytes (read + write) per launch from one ncu capture of the kernel on this
-# slab; an entry is removed whenever its kernel changes.
-#   FP64 CG apply: profiles/sem_apply_fp64_p4_semni_2M.md
-NCU_TRAFFIC = {(4, "LGL"): 273.056256e6 + 13.388544e6}
-#   FP32 smoother apply (bf16 metric, pipelined warp kernel): profiles/sem_apply_pipe_bf16_p4_semni_2M.md
-NCU_TRAFFIC_SMOOTHER = {(4, "LGL", "bf16"): 94.769664e6 + 2.867968e6}
+# DRAM bytes (read + write) per launch from one ncu capture of the kernel on the
+# p = 4 SEM-NI slab of 2,064,933 nodes, each with the hash of the kernel sources it
+# was taken from: a figure whose kernel sources have changed since is reported as
+# null (kernel_source_hash below).
+NCU_TRAFFIC = {(4, "LGL"): (273.056256e6 + 13.388544e6, "apply")}
+NCU_TRAFFIC_SMOOTHER = {(4, "LGL", "bf16"): (94.769664e6 + 2.867968e6, "apply")}
+NCU_SOURCE_HASH = {"apply": "a6f8611967d84547"}
+KERNEL_SOURCES = {"apply": ("sem_apply_kernel.cuh", "sem_apply_fp32.cu", "sem_apply_fp64.cu",
+                            "sem_internal.cuh")}
+
+
+def kernel_source_hash(kind: str) -> str:
+    """First 16 hex digits of the sha256 of the CUDA sources of a kernel family."""
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[kind]:
+        with open(os.path.join(ROOT, "paper_2205_05136_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(table, key):
+    """DRAM bytes per launch of the captured kernel, or None when there is no
+    capture or its kernel sources changed after it."""
+    ent = table.get(key)
+    if ent is None:
+        return None
+    val, kind = ent
+    return val if kernel_source_hash(kind) == NCU_SOURCE_HASH.get(kind) else None
 
 
 def peaks():
@@ -307,8 +336,41 @@ def time_arm(slab, precond, args, dist, dev, clocks=False):
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    u, _, _ = state.get()
-    return ms, stats, u, state, (clk.summary() if clk else None)
+    u, h, _ = state.get()
+    return ms, stats, (u, h), state, (clk.summary() if clk else None)
+
+
+def field_errors(u, h, u_ref, h_ref):
+    """Relative L2 and Linf differences of u and h against a reference run."""
+    import torch
+    return {"u_rel_l2": float(torch.linalg.norm(u - u_ref) / torch.linalg.norm(u_ref)),
+            "u_rel_linf": float((u - u_ref).abs().max() / u_ref.abs().max()),
+            "h_rel_l2": float(torch.linalg.norm(h - h_ref) / torch.linalg.norm(h_ref)),
+            "h_rel_linf": float((h - h_ref).abs().max() / h_ref.abs().max())}
+
+
+def oracle_step_config1(nsteps=100):
+    """The oracle's own time step (Section 3, Algorithm 1: ionic update, right-hand
+    side, exact sparse solve) on the small slab workload -- 8 x 4 x 2 Q2 SEM-NI
+    elements, 765 DOFs, corner stimulus, dt 0.05 ms -- timed end to end on one host
+    core for `nsteps` steps."""
+    from oracle import mesh as Mh
+    from oracle import monodomain as MD
+    s = W.slab(8, 4, 2, SLAB_LENGTHS, perturb=0.0, seed=W.SEED_MESH)
+    tissue = W.constant_tissue(s, 0.12, 0.03, 0.0)
+    o = Mh.SlabSpace(s.flat_vertices(), s.nx, s.ny, s.nz, 2, "LGL")
+    box = (0.0, 0.0, 0.0, 1.5, 1.5, 1.5)
+    t0 = time.perf_counter()
+    md = MD.Monodomain(o, tissue, DT, region=("box", box), amplitude=STIM_AMP, t_on=0.0, t_off=STIM_T_OFF)
+    t1 = time.perf_counter()
+    md.run(MD.rest_state(o.ndofs), nsteps)
+    t2 = time.perf_counter()
+    return {"workload": "monodomain BDF2 steps, SEM-NI Q2 slab 20x7x3 mm, 8x4x2 hexahedra, 765 DOFs, "
+                        "corner stimulus 50 mV/ms for 1 ms, dt 0.05 ms",
+            "steps": nsteps, "cores": 1, "setup_s": t1 - t0, "seconds": t2 - t1,
+            "steps_per_s": nsteps / (t2 - t1), "value": o.ndofs * nsteps / (t2 - t1) / 1e9,
+            "unit": UNIT, "kind": "oracle",
+            "sample": "oracle.monodomain.Monodomain.run: assembled M and K, sparse LU solves (numpy/scipy fp64)"}
 
 
 def run_gpu(args):
@@ -332,28 +394,34 @@ def run_gpu(args):
     slab.set_timing(True)
     n_d, n_e = slab.ndofs, slab.nelem
     prec = {"fp32": gb.SEM_PREC_FP32, "bf16": gb.SEM_PREC_FP32_BF16, "fp64": gb.SEM_PREC_FP64}[args.mg_precision]
-    capi.sem_set_gmg(slab.ctx, args.mg_degree, args.mg_coarse_degree, args.mg_min_coarse_dofs, prec)
+    mg = (args.mg_degree, args.mg_coarse_degree, args.mg_min_coarse_dofs)
 
     # plain FP64 path: Jacobi-CG with the FP64 operator
     capi.sem_set_operator_precision(slab.ctx, gb.SEM_PREC_FP64)
-    if args.arms in ("both", "fp64"):
-        ms64, st64, u64, state64, clk64 = time_arm(slab, gb.SEM_PC_JACOBI, args, dist, dev,
+    capi.sem_set_gmg(slab.ctx, *mg, prec)
+    ms64 = msg64 = float("nan")
+    if args.arms in ("all", "fp64"):
+        ms64, st64, f64, state64, clk64 = time_arm(slab, gb.SEM_PC_JACOBI, args, dist, dev,
                                                    clocks=args.arms == "fp64")
         state64.close()
+        # all-FP64 multigrid PCG on the hierarchy of the mixed path (FP64 operator and V-cycle)
+        capi.sem_set_gmg(slab.ctx, *mg, gb.SEM_PREC_FP64)
+        msg64, stg64, fg64, stateg64, _ = time_arm(slab, gb.SEM_PC_GMG, args, dist, dev)
+        stateg64.close()
     if args.arms == "fp64":  # report the plain FP64 path alone
-        msmx, stats, umx, clk = ms64, st64, u64, clk64
+        msmx, stats, fmx, clk = ms64, st64, f64, clk64
         state = slab.new_state(-85.0, 1.0)
         state.step(DT, 2, rtol=RTOL, maxit=MAXIT)
     else:
         # mixed-precision path: flexible FP64 CG (operator in double-float arithmetic unless
-        # --op-precision fp64) preconditioned by the FP32 multigrid V-cycle
+        # --op-precision fp64) preconditioned by the low-precision multigrid V-cycle
         capi.sem_set_operator_precision(
             slab.ctx, gb.SEM_PREC_DF64 if args.op_precision == "df64" else gb.SEM_PREC_FP64)
-        capi.sem_set_gmg(slab.ctx, args.mg_degree, args.mg_coarse_degree, args.mg_min_coarse_dofs, prec)
-        msmx, stats, umx, state, clk = time_arm(slab, gb.SEM_PC_GMG, args, dist, dev, clocks=True)
+        capi.sem_set_gmg(slab.ctx, *mg, prec)
+        msmx, stats, fmx, state, clk = time_arm(slab, gb.SEM_PC_GMG, args, dist, dev, clocks=True)
     if args.arms == "mixed":
-        ms64, st64, u64 = float("nan"), stats, umx
-    diff = float(torch.linalg.norm(umx - u64) / torch.linalg.norm(u64))
+        st64 = stg64 = stats
+        f64 = fg64 = fmx
 
     ms = msmx
     value = ws * n_d * args.steps / (ms * 1e-3) / 1e9
@@ -380,8 +448,7 @@ def run_gpu(args):
         sm_bytes = n_e * apply_bytes_per_element_fp32(p, args.mg_precision)
         per_vcycle = 2 * args.mg_degree  # fine-level applies per V-cycle (one V-cycle per PCG iteration)
         kernels["smoother_apply"] = {
-            "kernel": (f"{'sem_apply_pipe_kernel' if p <= 4 else 'sem_apply_kernel'}<P={p},{quad},f32,"
-                       f"{'bf16' if args.mg_precision == 'bf16' else 'f32'} metric> (fine-level V-cycle apply)"),
+            "kernel": smoother_kernel_name(p, quad, args.mg_precision),
             "timed": int(stats.n_smoother_apply), "avg_ms": sm_ms,
             "total_ms_est": sm_ms * per_vcycle * stats.cg_iters,
             "algorithmic_bytes_per_launch": sm_bytes,
@@ -393,7 +460,8 @@ def run_gpu(args):
         ksm = kernels["smoother_apply"]
         roofline = {"bound": "hbm", "achieved": ksm["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
                     "frac": ksm["achieved_gbs"] / hbm_peak,
-                    "traffic": NCU_TRAFFIC_SMOOTHER.get((p, quad, args.mg_precision)), "kernel": ksm["kernel"],
+                    "traffic": ncu_traffic(NCU_TRAFFIC_SMOOTHER, (p, quad, args.mg_precision)),
+                    "kernel": ksm["kernel"],
                     "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs), burst figure"}
     elif outer_is_df:
         roofline = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -403,7 +471,7 @@ def run_gpu(args):
     else:
         roofline = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": achieved_tf / FP64_PEAK_TFLOPS,
-                    "traffic": args.traffic if args.traffic is not None else NCU_TRAFFIC.get((p, quad)),
+                    "traffic": args.traffic if args.traffic is not None else ncu_traffic(NCU_TRAFFIC, (p, quad)),
                     "kernel": outer["kernel"],
                     "peak_note": "nominal FP64 1.25 TFLOP/s (no FP64 figure in MEASURED_PEAKS.json; DFMA probe measured 1.19)"}
     roofline["algorithmic_flops_per_launch"] = flops if dominant == "outer_apply" else None
@@ -431,6 +499,18 @@ def run_gpu(args):
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e_value = n_d * n_e2e / e2e_s / 1e9 * ws
+    state.close()
+    slab.close()
+    torch.cuda.empty_cache()
+
+    # the other workloads, in the same run (each timed by CUDA events)
+    configs = None
+    if not args.no_extra:
+        t_extra = time.perf_counter()
+        configs = {"sweep_2m": sweep_records(args, steps=args.extra_apply_steps),
+                   "gmg8m": gmg8m_record(args, nsteps=args.gmg8m_steps),
+                   "mixed30m": mixed30m_records(args, nsteps=args.mixed30m_steps)}
+        configs["wall_s"] = time.perf_counter() - t_extra
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -440,14 +520,21 @@ def run_gpu(args):
             applies = st64.cg_iters / max(args.steps, 1) + 1.0
             step_s = n_e * applies / rate
             cpu = {"value": n_d / step_s / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
-                   "sample": (f"oracle element-by-element apply (dense local matrices, numpy fp64) in {cores} "
-                              f"single-thread processes at once, {args.cpu_seconds:.0f} s each, "
+                   "sample": (f"apply-rate extrapolation: oracle element-by-element apply (dense local matrices, "
+                              f"numpy fp64) in {cores} single-thread processes at once, {args.cpu_seconds:.0f} s each, "
                               f"{sum(d for d, _ in res)} of this slab's {n_e} elements in all "
                               f"({rate:.0f} elements/s together, {res[0][0] / res[0][1]:.0f} per process); "
-                              f"scaled to one Jacobi-CG time step of {applies:.2f} applies ({step_s:.0f} s/step)")}
+                              f"scaled to one Jacobi-CG time step of {applies:.2f} applies, the FP64 Jacobi-CG "
+                              f"count measured above ({step_s:.0f} s/step)")}
         except Exception as exc:  # report, never fail the GPU line
             cpu = {"value": None, "unit": UNIT, "cores": host_cores(), "kind": "oracle", "sample": f"failed: {exc}"}
+        try:
+            cpu["step_config1"] = oracle_step_config1()
+        except Exception as exc:
+            cpu["step_config1"] = {"failed": str(exc)}
 
+    speed_j = ms64 / msmx
+    speed_g = msg64 / msmx
     line = {
         "metric": METRIC,
         "value": value,
@@ -480,93 +567,107 @@ def run_gpu(args):
                       "unit": UNIT, "ms_per_step": ms64 / args.steps,
                       "cg_iters_per_step": st64.cg_iters / max(args.steps, 1),
                       "apply_ms": apply64_ms, "apply_gdofs": n_d / (apply64_ms * 1e-3) / 1e9},
-        "mixed_vs_fp64": {"speedup": ms64 / msmx, "rel_l2_u_diff": diff,
-                          "note": "u after warm-up + timed steps of both paths, same start state"},
+        "fp64_gmg_path": {"solver": (f"flexible PCG, FP64 operator + FP64 GMG V-cycle on the same hierarchy "
+                                     f"(Chebyshev({args.mg_degree}), coarse Chebyshev({args.mg_coarse_degree}))"),
+                          "value": ws * n_d * args.steps / (msg64 * 1e-3) / 1e9, "unit": UNIT,
+                          "ms_per_step": msg64 / args.steps,
+                          "cg_iters_per_step": stg64.cg_iters / max(args.steps, 1)},
+        "mixed_vs_fp64": {"speedup": speed_g, "speedup_vs_fp64_gmg": speed_g, "speedup_vs_fp64_jacobi": speed_j,
+                          "vs_fp64_gmg": field_errors(fmx[0], fmx[1], fg64[0], fg64[1]),
+                          "vs_fp64_jacobi": field_errors(fmx[0], fmx[1], f64[0], f64[1]),
+                          "rel_l2_u_diff": field_errors(fmx[0], fmx[1], fg64[0], fg64[1])["u_rel_l2"],
+                          "note": ("speedup = FP64-GMG step time / mixed step time (same hierarchy, so the "
+                                   "precision alone); u and h after warm-up + timed steps of each path from the "
+                                   "same start state")},
         "roofline": roofline,
         "kernels": kernels,
         "fp64_apply_roofline": {"bound": "alu", "kernel": f"sem_apply_kernel<P={p},{quad},f64,dot> (plain FP64 path)",
                                 "achieved": flops / (apply64_ms * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
                                 "unit": "TFLOP/s", "frac": flops / (apply64_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
-                                "traffic": NCU_TRAFFIC.get((p, quad))} if args.arms != "mixed" else None,
+                                "traffic": ncu_traffic(NCU_TRAFFIC, (p, quad))} if args.arms != "mixed" else None,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * 8 * n_d,
                 "d2h_bytes_per_step": 2 * 8 * n_d, "steps": n_e2e,
                 "call": "sem_step_host_out (page-locked host arrays, rotated by the caller)"},
         "gpu_launches": int(stats.kernel_launches),
         "clocks": clk,
+        "configs": configs,
         "cpu_baseline": cpu,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
-    state.close()
-    slab.close()
     if dist is not None:
         dist.destroy_process_group()
 
 
-def run_sweep(args):
-    """Operator-apply sweep: p = 1..6, SEM and SEM-NI, ~2 M DOFs each."""
+def smoother_kernel_name(p, quad, mg_precision):
+    return (f"{'sem_apply_pipe_kernel' if p <= 4 else 'sem_apply_kernel'}<P={p},{quad},f32,"
+            f"{'bf16' if mg_precision == 'bf16' else 'f32'} metric> (fine-level V-cycle apply)")
+
+
+def _timed_applies(slab, u, y, steps, precision, flush):
+    """Median CUDA-event time (s) of `steps` applies y = (30 M + K) u, each after an
+    L2 flush (a 256 MB write), after 3 untimed applies."""
+    import torch
+    for _ in range(3):
+        slab.apply(u, 30.0, 1.0, precision=precision, out=y)
+    ts = []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        slab.apply(u, 30.0, 1.0, precision=precision, out=y)
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b) * 1e-3)
+    return statistics.median(ts)
+
+
+def sweep_records(args, steps=10, ps=(1, 2, 3, 4, 5, 6)):
+    """Operator-apply sweep, p = 1..6, SEM-NI and SEM, ~2 M DOFs each, 20 x 7 x 3 mm,
+    perturbed, rotating fibres, u ~ U[-1, 1]: FP64 (and double-float, FP32, FP32 +
+    bf16 metric) apply times, GDOF/s and the FP64 fraction of peak."""
     import torch
     import paper_2205_05136_gb300 as gb
-    from paper_2205_05136_gb300 import build as gbuild
-    gbuild.build()
-    for p in args.sweep_p:
+    out = []
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    for p in ps:
         for quad in ("LGL", "LG"):
             s, tissue, _ = workload(p)
             slab = gb.Slab(s.flat_vertices(), s.nx, s.ny, s.nz, p, quad)
             slab.set_tissue(*tissue)
             u = torch.tensor(W.uniform_vector(slab.ndofs, seed=W.SEED_U), device="cuda")
             y = torch.empty_like(u)
-            for _ in range(3):
-                slab.apply(u, 30.0, 1.0, out=y)
-            torch.cuda.synchronize()
-            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                   for _ in range(args.steps)]
-            for a, b in evs:
-                a.record()
-                slab.apply(u, 30.0, 1.0, out=y)
-                b.record()
-            torch.cuda.synchronize()
-            t = statistics.median(a.elapsed_time(b) for a, b in evs) * 1e-3
+            t = _timed_applies(slab, u, y, steps, gb.SEM_PREC_FP64, flush)
             flops = slab.nelem * apply_flops_per_element(p, quad)
-            out = {"sweep": True, "p": p, "quad": quad, "ndofs": slab.ndofs, "nelem": slab.nelem,
+            rec = {"p": p, "quad": quad, "ndofs": slab.ndofs, "nelem": slab.nelem,
                    "apply_ms": t * 1e3, "gdofs": slab.ndofs / t / 1e9,
                    "tflops_algorithmic": flops / t / 1e12,
                    "frac_fp64_peak": flops / t / 1e12 / FP64_PEAK_TFLOPS,
                    "gbs_algorithmic": slab.nelem * apply_bytes_per_element(p) / t / 1e9}
             ydf = torch.empty_like(u)
-            slab.apply(u, 30.0, 1.0, precision=gb.SEM_PREC_DF64, out=ydf)
-            torch.cuda.synchronize()
-            tdf = []
-            for _ in range(args.steps):
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record()
-                slab.apply(u, 30.0, 1.0, precision=gb.SEM_PREC_DF64, out=ydf)
-                b.record()
-                torch.cuda.synchronize()
-                tdf.append(a.elapsed_time(b) * 1e-3)
-            tdf = statistics.median(tdf)
-            out["df64_gdofs"] = slab.ndofs / tdf / 1e9
-            out["df64_apply_ms"] = tdf * 1e3
-            out["df64_rel_diff_vs_fp64"] = float(torch.linalg.norm(ydf - y) / torch.linalg.norm(y))
+            tdf = _timed_applies(slab, u, ydf, steps, gb.SEM_PREC_DF64, flush)
+            rec["df64_apply_ms"] = tdf * 1e3
+            rec["df64_gdofs"] = slab.ndofs / tdf / 1e9
+            rec["df64_rel_diff_vs_fp64"] = float(torch.linalg.norm(ydf - y) / torch.linalg.norm(y))
+            u32 = u.float()
             for prec, name in ((gb.SEM_PREC_FP32, "fp32"), (gb.SEM_PREC_FP32_BF16, "fp32_bf16")):
-                u32 = u.float()
                 y32 = torch.empty_like(u32)
-                slab.apply(u32, 30.0, 1.0, precision=prec, out=y32)
-                torch.cuda.synchronize()
-                ts = []
-                for _ in range(args.steps):
-                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    a.record()
-                    slab.apply(u32, 30.0, 1.0, precision=prec, out=y32)
-                    b.record()
-                    torch.cuda.synchronize()
-                    ts.append(a.elapsed_time(b) * 1e-3)
-                t32 = statistics.median(ts)
-                out[f"{name}_gdofs"] = slab.ndofs / t32 / 1e9
-                out[f"{name}_apply_ms"] = t32 * 1e3
-            print(json.dumps(out), flush=True)
+                t32 = _timed_applies(slab, u32, y32, steps, prec, flush)
+                rec[f"{name}_apply_ms"] = t32 * 1e3
+                rec[f"{name}_gdofs"] = slab.ndofs / t32 / 1e9
+                rec[f"{name}_rel_diff_vs_fp64"] = float(torch.linalg.norm(y32.double() - y) / torch.linalg.norm(y))
+            out.append(rec)
             slab.close()
+            del u, y, ydf, u32
             torch.cuda.empty_cache()
+    return out
+
+
+def run_sweep(args):
+    from paper_2205_05136_gb300 import build as gbuild
+    gbuild.build()
+    for rec in sweep_records(args, steps=args.steps, ps=args.sweep_p):
+        print(json.dumps(dict(sweep=True, **rec)), flush=True)
 
 
 def _slab_ctx(gb, s, p, quad, tissue, dev=0):
@@ -576,18 +677,30 @@ def _slab_ctx(gb, s, p, quad, tissue, dev=0):
     return slab
 
 
-def run_gmg8m(args):
+def _timed_run(st, nsteps, precond, maxit=MAXIT):
+    """nsteps time steps on the current stream between two CUDA events; (s, stats)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    stats = st.step(DT, nsteps, rtol=RTOL, maxit=maxit, precond=precond)
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) * 1e-3, stats
+
+
+def gmg8m_record(args, nsteps=200):
     """Monodomain run on a 40 x 20 x 6 mm slab at p = 4 (128 x 64 x 16 elements,
-    8.57 M DOFs), rotating fibres, 200 steps of 0.05 ms (10 ms), seeded stimulus
-    ball r = 1.5 mm, flexible PCG with the p-then-h multigrid (p 4 -> 2 -> 1, then
-    h-levels down to 2,000 nodes; Chebyshev 3, coarsest level Chebyshev 10), in two
+    8.57 M DOFs), rotating fibres, `nsteps` steps of 0.05 ms (200: 10 ms), seeded
+    stimulus ball r = 1.5 mm, flexible PCG with the p-then-h multigrid (p 4 -> 2 -> 1,
+    then h-levels down to 2,000 nodes; Chebyshev 3, coarsest level Chebyshev 10), in two
     arms on the same hierarchy: all FP64 (operator and V-cycle), and mixed
-    (double-float outer operator, bf16-metric FP32 V-cycle); relative L2 / Linf
-    differences of u and h between the two after the run."""
+    (double-float outer operator, bf16-metric FP32 V-cycle); activation times tracked
+    inside the timed run; relative L2 / Linf differences of u and h after the run."""
     import torch
     import paper_2205_05136_gb300 as gb
-    from paper_2205_05136_gb300 import build as gbuild, capi
-    gbuild.build()
+    from paper_2205_05136_gb300 import capi
     s = W.slab(128, 64, 16, (40.0, 20.0, 6.0), perturb=0.1, seed=W.SEED_MESH)
     ne = s.n_elements
     tissue = (np.full(ne, 0.12), np.full(ne, 0.03), W.transmural_fiber_angles(s))
@@ -595,27 +708,25 @@ def run_gmg8m(args):
     centre = W.seeded_point(s.lengths, STIM_RADIUS, seed=W.SEED_STIM)
     slab.set_stimulus("sphere", (*centre, STIM_RADIUS), STIM_AMP, 0.0, STIM_T_OFF)
     slab.set_timing(True)
-    nsteps = args.steps if args.steps != 20 else 200
-    out = {"workload": "gmg8m: 40x20x6 mm slab, 128x64x16 Q4 elements, 10 ms of activation",
-           "ndofs": slab.ndofs, "steps": nsteps}
+    out = {"workload": (f"40x20x6 mm slab, 128x64x16 Q4 SEM-NI elements, {slab.ndofs} DOFs, +-10% perturbation, "
+                        f"fibres -60..+60 deg, {nsteps} steps of {DT} ms from rest, stimulus ball r 1.5 mm"),
+           "ndofs": slab.ndofs, "steps": nsteps,
+           "solver": "flexible PCG rtol 1e-10, GMG p 4->2->1 then h down to 2,000 nodes, Chebyshev(3), coarse Chebyshev(10)"}
     finals = {}
+    rest = {"u": torch.full((slab.ndofs,), -85.0, dtype=torch.float64, device="cuda"),
+            "u_prev": torch.full((slab.ndofs,), -85.0, dtype=torch.float64, device="cuda"),
+            "h": torch.ones(slab.ndofs, dtype=torch.float64, device="cuda"),
+            "h_prev": torch.ones(slab.ndofs, dtype=torch.float64, device="cuda"), "n": 0}
     for name, op, prec in (("fp64", gb.SEM_PREC_FP64, gb.SEM_PREC_FP64),
                            ("mixed", gb.SEM_PREC_DF64, gb.SEM_PREC_FP32_BF16)):
         capi.sem_set_operator_precision(slab.ctx, op)
         capi.sem_set_gmg(slab.ctx, 3, 10, 2000, prec)
         info = capi.sem_gmg_info(slab.ctx, 1.5 / DT)
         st = slab.new_state(-85.0, 1.0)
-        st.step(DT, 3, rtol=RTOL, maxit=MAXIT, precond=gb.SEM_PC_GMG)
-        st.restore({"u": torch.full((slab.ndofs,), -85.0, dtype=torch.float64, device="cuda"),
-                    "u_prev": torch.full((slab.ndofs,), -85.0, dtype=torch.float64, device="cuda"),
-                    "h": torch.ones(slab.ndofs, dtype=torch.float64, device="cuda"),
-                    "h_prev": torch.ones(slab.ndofs, dtype=torch.float64, device="cuda"), "n": 0})
+        st.step(DT, 3, rtol=RTOL, maxit=MAXIT, precond=gb.SEM_PC_GMG)  # warm-up, then back to rest
+        st.restore(rest)
         st.track_activation(True)  # activation times (Eq. tau) on the way, inside the timed run
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        stats = st.step(DT, nsteps, rtol=RTOL, maxit=MAXIT, precond=gb.SEM_PC_GMG)
-        torch.cuda.synchronize()
-        el = time.perf_counter() - t0
+        el, stats = _timed_run(st, nsteps, gb.SEM_PC_GMG)
         u, h, n = st.get()
         tau, dmax = st.activation()
         finals[name] = (u, h, tau, dmax)
@@ -627,86 +738,97 @@ def run_gmg8m(args):
         st.close()
     (u64, h64, tau64, d64), (umx, hmx, taumx, dmx) = finals["fp64"], finals["mixed"]
     act = d64 > 10.0  # nodes the front reached (upstroke faster than 10 mV/ms)
-    out["activation"] = {"activated_nodes": int(act.sum()),
-                         "tau_ms_min": float(tau64[act].min()), "tau_ms_max": float(tau64[act].max()),
-                         "mixed_same_tau_fraction": float((taumx[act] == tau64[act]).double().mean()),
-                         "mixed_max_abs_tau_diff_ms": float((taumx[act] - tau64[act]).abs().max()),
-                         "mixed_dudt_max_rel_diff": float(((dmx - d64)[act].abs() / d64[act]).max())}
-    out["mixed"]["u_rel_l2_vs_fp64"] = float(torch.linalg.norm(umx - u64) / torch.linalg.norm(u64))
-    out["mixed"]["u_rel_linf_vs_fp64"] = float((umx - u64).abs().max() / u64.abs().max())
-    out["mixed"]["h_rel_l2_vs_fp64"] = float(torch.linalg.norm(hmx - h64) / torch.linalg.norm(h64))
+    if bool(act.any()):
+        out["activation"] = {"activated_nodes": int(act.sum()),
+                             "tau_ms_min": float(tau64[act].min()), "tau_ms_max": float(tau64[act].max()),
+                             "mixed_same_tau_fraction": float((taumx[act] == tau64[act]).double().mean()),
+                             "mixed_max_abs_tau_diff_ms": float((taumx[act] - tau64[act]).abs().max()),
+                             "mixed_dudt_max_rel_diff": float(((dmx - d64)[act].abs() / d64[act]).max())}
+    out["mixed"].update(field_errors(umx, hmx, u64, h64))
     out["mixed"]["speedup_vs_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
-    print(json.dumps(out), flush=True)
     slab.close()
+    del finals, rest
+    torch.cuda.empty_cache()
+    return out
 
 
-def run_mixed30m(args):
-    """Mixed precision at ~30 M DOFs (p = 4: 207 x 72 x 31; p = 6: 137 x 48 x 21):
-    per-field relative L2 and Linf errors of u and h after K steps with the FP32
-    and bf16-metric multigrid against the plain FP64 path, sampled operator rows
-    against the oracle, and step times."""
+def run_gmg8m(args):
+    from paper_2205_05136_gb300 import build as gbuild
+    gbuild.build()
+    print(json.dumps(gmg8m_record(args, nsteps=args.steps if args.steps != 200 else 200)), flush=True)
+
+
+def mixed30m_records(args, nsteps=5, cases=((4, (207, 72, 31)), (6, (137, 48, 21))), sampled_rows=True):
+    """Mixed precision at ~30 M DOFs (p = 4: 207 x 72 x 31; p = 6: 137 x 48 x 21), each
+    arm from the rest state with the stimulus on: one untimed BDF1 step, then `nsteps`
+    timed steps.  Arms: FP64 Jacobi-CG; flexible PCG with an all-FP64 GMG V-cycle; the
+    mixed solver (double-float outer operator, bf16-metric FP32 V-cycle) on the same
+    hierarchy (Chebyshev 6, coarse Chebyshev 6, coarsening down to 300,000 nodes).
+    Per-field relative L2 and Linf of u and h against the FP64-GMG arm; sampled
+    operator rows against the oracle."""
     import torch
     import paper_2205_05136_gb300 as gb
-    from paper_2205_05136_gb300 import build as gbuild, capi
+    from paper_2205_05136_gb300 import capi
     from oracle import mesh as Mh
-    gbuild.build()
-    nsteps = args.steps if args.steps != 20 else 10
-    for p, dims in ((4, (207, 72, 31)), (6, (137, 48, 21))):
+    recs = []
+    for p, dims in cases:
         s = W.slab(*dims, SLAB_LENGTHS, perturb=0.1, seed=W.SEED_MESH)
         ne = s.n_elements
         tissue = (np.full(ne, 0.12), np.full(ne, 0.03), W.transmural_fiber_angles(s))
         slab = _slab_ctx(gb, s, p, args.quad, tissue)
         centre = W.seeded_point(s.lengths, STIM_RADIUS, seed=W.SEED_STIM)
         slab.set_stimulus("sphere", (*centre, STIM_RADIUS), STIM_AMP, 0.0, STIM_T_OFF)
-        # sampled operator rows against the oracle
-        o = Mh.SlabSpace(s.flat_vertices(), *dims, p, args.quad)
+        out = {"workload": (f"mixed precision, {'SEM-NI' if args.quad == 'LGL' else 'SEM'} Q{p} slab 20x7x3 mm, "
+                            f"{dims[0]}x{dims[1]}x{dims[2]} hexahedra, {slab.ndofs} DOFs, +-10% perturbation, "
+                            f"fibres -60..+60 deg, 1 + {nsteps} steps of {DT} ms from rest"),
+               "p": p, "ndofs": slab.ndofs, "nelem": ne, "steps": nsteps}
         uvec = W.uniform_vector(slab.ndofs, seed=W.SEED_U)
         ut = torch.tensor(uvec, device="cuda")
-        y64 = slab.apply(ut, 30.0, 1.0).cpu().numpy()
-        idx = W.seeded_indices(slab.ndofs, 16, seed=7)
-        ref = Mh.sampled_rows(o, tissue, uvec, idx, 30.0, 1.0)
-        op_err = float(np.abs(y64[idx] - ref).max() / np.abs(ref).max())
-        y32 = slab.apply(ut.float(), 30.0, 1.0, precision=gb.SEM_PREC_FP32).double().cpu().numpy()
-        y16 = slab.apply(ut.float(), 30.0, 1.0, precision=gb.SEM_PREC_FP32_BF16).double().cpu().numpy()
-        rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))  # noqa: E731
-        out = {"workload": f"mixed30m p={p}", "ndofs": slab.ndofs, "nelem": ne, "steps": nsteps,
-               "apply_rel_err_fp64_vs_oracle_sampled": op_err,
-               "apply_rel_l2_fp32_vs_fp64": rel(y32, y64), "apply_rel_l2_bf16_vs_fp64": rel(y16, y64)}
+        y64 = slab.apply(ut, 30.0, 1.0)
+        if sampled_rows:
+            o = Mh.SlabSpace(s.flat_vertices(), *dims, p, args.quad)
+            idx = W.seeded_indices(slab.ndofs, 16, seed=7)
+            ref = Mh.sampled_rows(o, tissue, uvec, idx, 30.0, 1.0)
+            yi = y64[torch.tensor(idx, device="cuda")].cpu().numpy()
+            out["apply_rel_err_fp64_vs_oracle_sampled"] = float(np.abs(yi - ref).max() / np.abs(ref).max())
+        for prec, name in ((gb.SEM_PREC_FP32, "fp32"), (gb.SEM_PREC_FP32_BF16, "bf16")):
+            yl = slab.apply(ut.float(), 30.0, 1.0, precision=prec).double()
+            out[f"apply_rel_l2_{name}_vs_fp64"] = float(torch.linalg.norm(yl - y64) / torch.linalg.norm(y64))
+            del yl
+        del ut, y64
         results = {}
-        # the FP32- and bf16-metric V-cycles under the FP64 outer CG (Chebyshev 3), and the
-        # fastest configuration of the 2 M DOF benchmark: double-float outer operator,
-        # bf16-metric V-cycle, Chebyshev 6, coarsening down to 300,000 nodes
-        for name, pc, prec in (("fp64_jacobi", gb.SEM_PC_JACOBI, None),
-                               ("gmg_fp32", gb.SEM_PC_GMG, gb.SEM_PREC_FP32),
-                               ("gmg_bf16", gb.SEM_PC_GMG, gb.SEM_PREC_FP32_BF16),
-                               ("gmg_bf16_df64_cheb6", gb.SEM_PC_GMG, gb.SEM_PREC_FP32_BF16)):
-            tuned = name.endswith("cheb6")
-            capi.sem_set_operator_precision(slab.ctx, gb.SEM_PREC_DF64 if tuned else gb.SEM_PREC_FP64)
+        for name, pc, op, prec in (("fp64_jacobi", gb.SEM_PC_JACOBI, gb.SEM_PREC_FP64, None),
+                                   ("fp64_gmg", gb.SEM_PC_GMG, gb.SEM_PREC_FP64, gb.SEM_PREC_FP64),
+                                   ("mixed", gb.SEM_PC_GMG, gb.SEM_PREC_DF64, gb.SEM_PREC_FP32_BF16)):
+            capi.sem_set_operator_precision(slab.ctx, op)
             if prec is not None:
-                capi.sem_set_gmg(slab.ctx, 6 if tuned else 3, 6 if tuned else 8, 300000 if tuned else 40000, prec)
+                capi.sem_set_gmg(slab.ctx, 6, 6, 300000, prec)
             st = slab.new_state(-85.0, 1.0)
             st.step(DT, 1, rtol=RTOL, maxit=MAXIT * 4, precond=pc)  # warm-up (BDF1)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            stt = st.step(DT, nsteps, rtol=RTOL, maxit=MAXIT * 4, precond=pc)
-            torch.cuda.synchronize()
-            el = time.perf_counter() - t0
+            el, stt = _timed_run(st, nsteps, pc, maxit=MAXIT * 4)
             u, h, _ = st.get()
             results[name] = (u, h)
-            out[name] = {"ms_per_step": el / nsteps * 1e3, "cg_iters_per_step": stt.cg_iters / nsteps}
+            out[name] = {"ms_per_step": el / nsteps * 1e3, "cg_iters_per_step": stt.cg_iters / nsteps,
+                         "gdof_steps_per_s": slab.ndofs * nsteps / el / 1e9}
             st.close()
-        u64, h64 = results["fp64_jacobi"]
-        for name in ("gmg_fp32", "gmg_bf16", "gmg_bf16_df64_cheb6"):
+        ug, hg = results["fp64_gmg"]
+        for name in ("mixed", "fp64_jacobi"):
             u, h = results[name]
-            out[name]["u_rel_l2"] = float(torch.linalg.norm(u - u64) / torch.linalg.norm(u64))
-            out[name]["u_rel_linf"] = float((u - u64).abs().max() / u64.abs().max())
-            out[name]["h_rel_l2"] = float(torch.linalg.norm(h - h64) / torch.linalg.norm(h64))
-            out[name]["h_rel_linf"] = float((h - h64).abs().max() / h64.abs().max())
-            out[name]["speedup_vs_fp64"] = out["fp64_jacobi"]["ms_per_step"] / out[name]["ms_per_step"]
-        print(json.dumps(out), flush=True)
+            out[name].update({f"{k}_vs_fp64_gmg": v for k, v in field_errors(u, h, ug, hg).items()})
+        out["mixed"]["speedup_vs_fp64_gmg"] = out["fp64_gmg"]["ms_per_step"] / out["mixed"]["ms_per_step"]
+        out["mixed"]["speedup_vs_fp64_jacobi"] = out["fp64_jacobi"]["ms_per_step"] / out["mixed"]["ms_per_step"]
+        recs.append(out)
         slab.close()
         del results
         torch.cuda.empty_cache()
+    return recs
+
+
+def run_mixed30m(args):
+    from paper_2205_05136_gb300 import build as gbuild
+    gbuild.build()
+    for rec in mixed30m_records(args, nsteps=args.steps if args.steps != 200 else 10):
+        print(json.dumps(rec), flush=True)
 
 
 def run_adjoint(args):
@@ -784,29 +906,40 @@ def run_reference(args):
     s, _, _ = workload(p)
     nel = s.n_elements
     ndofs = (p * s.nx + 1) * (p * s.ny + 1) * (p * s.nz + 1)
-    # applies per step of the GPU arm's solver on this workload (measured there)
+    # applies per time step: the FP64 Jacobi-CG iterations per step that the GPU arm
+    # measures on this workload (32.6) plus the residual apply
     applies = args.ref_applies_per_step
     per_step = max(1.0, min(8.0, 150.0 / max(args.steps + args.warmup, 1)))
     cores = host_cores()
     vals = []
     for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
         rate, res = run_oracle_parallel(p, quad, per_step, cores)
+        wall = time.perf_counter() - t0
         step_s = nel * applies / rate
         if k >= args.warmup:
-            vals.append((ndofs / step_s / 1e9, step_s))
+            vals.append((ndofs / step_s / 1e9, step_s, wall))
     v = statistics.median(x[0] for x in vals)
-    ms_per_step = statistics.median(x[1] for x in vals) * 1e3
-    sample = (f"each step: oracle element-by-element apply (numpy fp64) in {cores} single-thread processes "
-              f"at once, ~{per_step:.0f} s each over this slab's {nel} elements, scaled to a full time step of "
-              f"{applies} applies")
+    sample = (f"apply-rate extrapolation: each bench step runs the oracle's element-by-element apply (numpy fp64) "
+              f"in {cores} single-thread processes at once for ~{per_step:.0f} s over this slab's {nel} elements; "
+              f"value = DOF-steps/s of a full time step of {applies} applies at that rate "
+              f"(extrapolated {statistics.median(x[1] for x in vals):.0f} s per time step)")
+    cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+           "extrapolated_s_per_time_step": statistics.median(x[1] for x in vals)}
+    try:
+        cpu["step_config1"] = oracle_step_config1()
+    except Exception as exc:
+        cpu["step_config1"] = {"failed": str(exc)}
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": statistics.median(x[2] for x in vals) * 1e3,
+        "ms_per_step_note": "wall time of one bench step (one bounded oracle sample, process start-up included)",
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": workload_name(p, quad, s, ndofs), "p": p, "quadrature": quad,
                    "ndofs": ndofs, "nelem": nel},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "cpu_baseline": cpu,
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -829,8 +962,8 @@ def main():
     ap.add_argument("--mg-precision", default="bf16", choices=["fp32", "bf16", "fp64"])
     ap.add_argument("--op-precision", default="df64", choices=["df64", "fp64"],
                     help="arithmetic of the outer CG operator in the mixed path")
-    ap.add_argument("--arms", default="both", choices=["both", "mixed", "fp64"],
-                    help="time the mixed-precision multigrid path, the plain FP64 path, or both")
+    ap.add_argument("--arms", default="all", choices=["all", "mixed", "fp64"],
+                    help="time the mixed-precision multigrid path, the plain FP64 paths, or all")
     ap.add_argument("--mg-degree", type=int, default=6)
     # tuned on the 2 M DOF slab at dt = 0.05 ms (mass-dominated operator): a degree-6
     # Chebyshev smoother on the p = 4 level and the p = 2 level (266,085 nodes) as the
@@ -841,6 +974,11 @@ def main():
     ap.add_argument("--mg-min-coarse-dofs", type=int, default=300000)
     ap.add_argument("--workload", default="timestep", choices=["timestep", "gmg8m", "mixed30m", "adjoint"],
                     help="extra measurements of the multigrid, mixed-precision and adjoint workloads")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the other workloads (operator sweep, 8.57 M and ~30 M DOF runs)")
+    ap.add_argument("--extra-apply-steps", type=int, default=5, help="timed applies per sweep entry")
+    ap.add_argument("--gmg8m-steps", type=int, default=200)
+    ap.add_argument("--mixed30m-steps", type=int, default=5)
     ap.add_argument("--sweep", action="store_true")
     ap.add_argument("--sweep-p", type=int, nargs="*", default=[1, 2, 3, 4, 5, 6])
     args = ap.parse_args()

@@ -356,3 +356,54 @@ def test_benchmark_time_step_full_size():
     st.close()
     g.close()
     torch.cuda.empty_cache()
+
+
+def test_mixed_precision_30m_matches_fp64_multigrid():
+    """The ~30 M DOF mixed-precision workload at p = 4 (207 x 72 x 31 perturbed Q4
+    elements, 29,947,625 DOFs, SEM-NI, rotating fibres, sphere stimulus): three time
+    steps (BDF1, then BDF2) of the mixed solver -- flexible FP64 PCG with the
+    double-float operator and the bf16-metric V-cycle, Chebyshev(6) on every level,
+    coarsening down to 300,000 nodes -- against three steps of flexible PCG with the
+    FP64 operator and an all-FP64 V-cycle on the same hierarchy, both at rtol 1e-10
+    from the rest state: u and h agree to 1e-8 relative in the 2-norm and the max
+    norm.  The FP64 operator at this size is pinned to the oracle by sampled rows."""
+    dt, rtol, nsteps = 0.05, 1e-10, 3
+    s = W.slab(207, 72, 31, (20.0, 7.0, 3.0), perturb=0.1, seed=W.SEED_MESH)
+    ne = s.n_elements
+    tissue = (np.full(ne, 0.12), np.full(ne, 0.03), W.transmural_fiber_angles(s))
+    centre = W.seeded_point(s.lengths, 1.5, seed=W.SEED_STIM)
+    g = gb.Slab(s.flat_vertices(), s.nx, s.ny, s.nz, 4, "LGL")
+    assert g.ndofs == 829 * 289 * 125  # 29,947,625
+    g.set_tissue(*tissue)
+    g.set_ionic()
+    g.set_stimulus("sphere", (*centre, 1.5), 50.0, 0.0, 1.0)
+
+    o = Mh.SlabSpace(s.flat_vertices(), s.nx, s.ny, s.nz, 4, "LGL")
+    uvec = W.uniform_vector(g.ndofs, seed=W.SEED_U)
+    y = g.apply(torch.tensor(uvec, device="cuda"), 1.5 / dt, 1.0)
+    idx = W.seeded_indices(g.ndofs, 12, seed=7)
+    ref = Mh.sampled_rows(o, tissue, uvec, idx, 1.5 / dt, 1.0)
+    yi = y[torch.tensor(idx, device="cuda")].cpu().numpy()
+    assert np.abs(yi - ref).max() < 1e-12 * np.abs(ref).max()
+    del y
+
+    out = {}
+    for name, op, prec in (("fp64", gb.SEM_PREC_FP64, gb.SEM_PREC_FP64),
+                           ("mixed", gb.SEM_PREC_DF64, gb.SEM_PREC_FP32_BF16)):
+        capi.sem_set_operator_precision(g.ctx, op)
+        capi.sem_set_gmg(g.ctx, 6, 6, 300000, prec)
+        st = g.new_state(-85.0, 1.0)
+        st.step(dt, nsteps, rtol=rtol, maxit=8000, precond=gb.SEM_PC_GMG)
+        u, h, n = st.get()
+        assert n == nsteps
+        out[name] = (u.clone(), h.clone())
+        st.close()
+    (u64, h64), (umx, hmx) = out["fp64"], out["mixed"]
+    assert float(umx.max()) > -85.0 + 1.0  # the stimulus has moved u
+    assert float(torch.linalg.norm(umx - u64) / torch.linalg.norm(u64)) < 1e-8
+    assert float((umx - u64).abs().max() / u64.abs().max()) < 1e-8
+    assert float(torch.linalg.norm(hmx - h64) / torch.linalg.norm(h64)) < 1e-8
+    assert float((hmx - h64).abs().max() / h64.abs().max()) < 1e-8
+    g.close()
+    del out
+    torch.cuda.empty_cache()
