@@ -51,7 +51,8 @@ STIM_RADIUS = 1.5    # mm
 STIM_AMP = 50.0      # mV/ms
 STIM_T_OFF = 1.0     # ms
 SLAB_LENGTHS = W.SLAB_LENGTHS_MM
-MG_DTYPE = {"fp32": "f32", "bf16": "f32 arithmetic / bf16 metric", "fp64": "f64"}
+MG_DTYPE = {"fp32": "f32", "bf16": "f32 arithmetic / bf16 metric", "fp64": "f64",
+            "tc": "f32 vectors / bf16 metric / bf16 tensor-core contractions with f32 accumulation"}
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64: 152 SMs x 2 DFMA/clk x 2 flop x ~2.06 GHz
 
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel on the
@@ -103,10 +104,13 @@ def apply_flops_per_element(p: int, quad: str) -> int:
 def apply_bytes_per_element_fp32(p: int, metric: str = "fp32") -> int:
     """Algorithmic HBM bytes of one FP32 element apply: 7 metric values per
     quadrature point (4 bytes, or 2 with the bf16 metric), the int32 map, and
-    u read + y written once per node (4 bytes each)."""
+    u read + y written once per node (4 bytes each).  The tensor-core kernel
+    ("tc", bf16 metric) takes node indices from the slab's numbering and reads
+    no map."""
     n = p + 1
-    mb = 2 if metric == "bf16" else 4
-    return 7 * mb * n ** 3 + 4 * n ** 3 + 8 * p ** 3
+    mb = 2 if metric in ("bf16", "tc") else 4
+    mapb = 0 if metric == "tc" else 4 * n ** 3
+    return 7 * mb * n ** 3 + mapb + 8 * p ** 3
 
 
 def apply_bytes_per_element(p: int) -> int:
@@ -393,7 +397,8 @@ def run_gpu(args):
     slab.set_stimulus("sphere", (*centre, STIM_RADIUS), STIM_AMP, 0.0, STIM_T_OFF)
     slab.set_timing(True)
     n_d, n_e = slab.ndofs, slab.nelem
-    prec = {"fp32": gb.SEM_PREC_FP32, "bf16": gb.SEM_PREC_FP32_BF16, "fp64": gb.SEM_PREC_FP64}[args.mg_precision]
+    prec = {"fp32": gb.SEM_PREC_FP32, "bf16": gb.SEM_PREC_FP32_BF16, "fp64": gb.SEM_PREC_FP64,
+            "tc": gb.SEM_PREC_BF16_TC}[args.mg_precision]
     mg = (args.mg_degree, args.mg_coarse_degree, args.mg_min_coarse_dofs)
 
     # plain FP64 path: Jacobi-CG with the FP64 operator
@@ -600,8 +605,10 @@ def run_gpu(args):
 
 
 def smoother_kernel_name(p, quad, mg_precision):
+    if mg_precision == "tc" and quad == "LGL" and 2 <= p <= 4:
+        return f"sem_apply_tc_kernel<P={p}> (SEM-NI, bf16 metric, mma.sync bf16 -> f32; fine-level V-cycle apply)"
     return (f"{'sem_apply_pipe_kernel' if p <= 4 else 'sem_apply_kernel'}<P={p},{quad},f32,"
-            f"{'bf16' if mg_precision == 'bf16' else 'f32'} metric> (fine-level V-cycle apply)")
+            f"{'bf16' if mg_precision in ('bf16', 'tc') else 'f32'} metric> (fine-level V-cycle apply)")
 
 
 def _timed_applies(slab, u, y, steps, precision, flush):
@@ -959,7 +966,7 @@ def main():
     ap.add_argument("--traffic", type=float, default=None,
                     help="dram bytes per apply launch from an ncu capture of the current kernel")
     ap.add_argument("--ref-applies-per-step", type=float, default=33.0)
-    ap.add_argument("--mg-precision", default="bf16", choices=["fp32", "bf16", "fp64"])
+    ap.add_argument("--mg-precision", default="bf16", choices=["fp32", "bf16", "fp64", "tc"])
     ap.add_argument("--op-precision", default="df64", choices=["df64", "fp64"],
                     help="arithmetic of the outer CG operator in the mixed path")
     ap.add_argument("--arms", default="all", choices=["all", "mixed", "fp64"],

@@ -61,6 +61,9 @@ extern "C" {
 #define SEM_PREC_FP32_BF16 2 /* float vectors, bfloat16 metric, float arithmetic */
 #define SEM_PREC_DF64 3      /* double vectors, metric split into float pairs, double-float
                                 arithmetic on the FP32 pipe (FP64 results to ~1e-14) */
+#define SEM_PREC_BF16_TC 4   /* float vectors, bfloat16 metric, the sum-factorization
+                                contractions on the tensor cores (bf16 operands, FP32
+                                accumulation): SEM-NI (SEM_QUAD_LGL) at p = 2..4 */
 
 #define SEM_PC_NONE 0
 #define SEM_PC_JACOBI 1
@@ -133,8 +136,9 @@ int sem_set_tissue(sem_ctx* ctx, const double* sigma_l, const double* sigma_t,
 
 /* y = alpha M u + beta K u (Algorithm 1, cell loop with sum factorization).
  * precision SEM_PREC_FP64 or SEM_PREC_DF64: u, y are device double[ndofs].
- * precision SEM_PREC_FP32 / SEM_PREC_FP32_BF16: u, y are device float[ndofs].
- * y is overwritten; u and y must not overlap. */
+ * precision SEM_PREC_FP32 / SEM_PREC_FP32_BF16 / SEM_PREC_BF16_TC: u, y are
+ * device float[ndofs]; SEM_PREC_BF16_TC returns SEM_ERR_UNSUPPORTED outside
+ * SEM-NI at p = 2..4.  y is overwritten; u and y must not overlap. */
 int sem_apply(sem_ctx* ctx, double alpha, double beta, const void* u, void* y, int precision,
               void* stream);
 
@@ -166,7 +170,9 @@ int sem_cg_solve(sem_ctx* ctx, double alpha, const double* b, double* x, double 
  * [0.08, 1.2] x lambda_max(D^{-1} A), lambda_max from 10 Lanczos (CG) steps;
  * coarse_degree Chebyshev steps on the coarsest level.  precision: the
  * V-cycle's arithmetic -- SEM_PREC_FP32 (FP32 metric), SEM_PREC_FP32_BF16
- * (bf16 metric) or SEM_PREC_FP64; the outer CG is flexible and stays FP64.
+ * (bf16 metric), SEM_PREC_BF16_TC (bf16 metric, tensor-core contractions on
+ * the SEM-NI levels of degree 2..4, the bf16-metric FP32 kernel on the others)
+ * or SEM_PREC_FP64; the outer CG is flexible and stays FP64.
  * Defaults: degree 3, coarse_degree 10, min_coarse_dofs 2000, FP32.  The
  * hierarchy is (re)built on first use after this call or sem_set_tissue. */
 int sem_set_gmg(sem_ctx* ctx, int degree, int coarse_degree, int min_coarse_dofs, int precision);

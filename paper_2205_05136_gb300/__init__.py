@@ -17,7 +17,7 @@ import torch
 
 from . import capi
 from .autograd import traces  # noqa: F401
-from .capi import (SEM_PC_GMG, SEM_PC_JACOBI, SEM_PC_NONE, SEM_PREC_DF64, SEM_PREC_FP32,  # noqa: F401
+from .capi import (SEM_PC_GMG, SEM_PC_JACOBI, SEM_PC_NONE, SEM_PREC_BF16_TC, SEM_PREC_DF64, SEM_PREC_FP32,  # noqa: F401
                    SEM_PREC_FP32_BF16,
                    SEM_PREC_FP64, SEM_QUAD_LG, SEM_QUAD_LGL, SEM_REGION_BOX, SEM_REGION_SPHERE,
                    SemError)

@@ -28,6 +28,7 @@ SOURCES = [
     "sem_solver.cu",
     "sem_api.cu",
     "sem_noalloc.cu",
+    "sem_apply_tc.cu",
     "sem_gmg.cu",
     "sem_adjoint.cu",
     "sem_transfer.cu",

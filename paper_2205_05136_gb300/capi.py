@@ -28,6 +28,7 @@ SEM_PREC_FP64 = 0
 SEM_PREC_FP32 = 1
 SEM_PREC_FP32_BF16 = 2
 SEM_PREC_DF64 = 3
+SEM_PREC_BF16_TC = 4
 SEM_PC_NONE = 0
 SEM_PC_JACOBI = 1
 SEM_PC_GMG = 2

@@ -266,6 +266,8 @@ int sem_apply(sem_ctx* ctx, double alpha, double beta, const void* u, void* y, i
       return apply_fp32(ctx, alpha, beta, static_cast<const float*>(u), static_cast<float*>(y), false, s);
     case SEM_PREC_FP32_BF16:
       return apply_fp32(ctx, alpha, beta, static_cast<const float*>(u), static_cast<float*>(y), true, s);
+    case SEM_PREC_BF16_TC:
+      return apply_tc(ctx, alpha, beta, static_cast<const float*>(u), static_cast<float*>(y), s);
     default:
       return fail(ctx, SEM_ERR_ARG, "unknown precision");
   }
@@ -585,8 +587,11 @@ int sem_set_gmg(sem_ctx* ctx, int degree, int coarse_degree, int min_coarse_dofs
   CK_CTX(ctx);
   if (degree < 1 || degree > 20 || coarse_degree < 1 || coarse_degree > 200 || min_coarse_dofs < 1)
     return fail(ctx, SEM_ERR_ARG, "bad multigrid parameters");
-  if (precision != SEM_PREC_FP64 && precision != SEM_PREC_FP32 && precision != SEM_PREC_FP32_BF16)
+  if (precision != SEM_PREC_FP64 && precision != SEM_PREC_FP32 && precision != SEM_PREC_FP32_BF16 &&
+      precision != SEM_PREC_BF16_TC)
     return fail(ctx, SEM_ERR_ARG, "unknown precision");
+  if (precision == SEM_PREC_BF16_TC && ctx->L.quad != SEM_QUAD_LGL)
+    return fail(ctx, SEM_ERR_UNSUPPORTED, "tensor-core V-cycle needs SEM-NI (SEM_QUAD_LGL)");
   DeviceGuard guard(ctx->device);
   cudaDeviceSynchronize();
   gmg_free(ctx);

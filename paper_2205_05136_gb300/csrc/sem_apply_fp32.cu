@@ -17,7 +17,8 @@ cudaError_t launch_apply_bf16(const Level& L, const ApplyArgs<float, __nv_bfloat
 cudaError_t prime_apply_kernels() {
   cudaError_t e = prime_all<float, float>();
   if (e != cudaSuccess) return e;
-  return prime_all<float, __nv_bfloat16>();
+  if ((e = prime_all<float, __nv_bfloat16>()) != cudaSuccess) return e;
+  return prime_apply_tc();
 }
 
 }  // namespace sem

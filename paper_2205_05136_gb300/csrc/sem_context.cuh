@@ -91,6 +91,8 @@ int apply_fp32(sem_ctx* ctx, double alpha, double beta, const float* u, float* y
                cudaStream_t s);
 int apply_df64(sem_ctx* ctx, double alpha, double beta, const double* u, double* y,
                cudaStream_t s);
+// FP32 vectors, bf16 metric, tensor-core contractions (SEM-NI, p = 2..4).
+int apply_tc(sem_ctx* ctx, double alpha, double beta, const float* u, float* y, cudaStream_t s);
 // The FP64-vector operator the solvers use (FP64 or df64 arithmetic per ctx->op_precision);
 // prepare_operator makes its metric copy and must run before any stream capture.
 cudaError_t prepare_operator(sem_ctx* ctx, cudaStream_t s);

@@ -578,13 +578,6 @@ double tridiag_max_eig(const std::vector<double>& a, const std::vector<double>& 
   return 0.5 * (lo + hi);
 }
 
-template <typename T>
-const void* level_metric(const Level& L, int precision) {
-  if (precision == SEM_PREC_FP64) return L.metric;
-  if (precision == SEM_PREC_FP32_BF16) return L.metric16;
-  return L.metric32;
-}
-
 // y += (alpha M + K) x on one level in the V-cycle's precision.
 int level_apply(sem_ctx* ctx, const Level& L, int precision, double alpha, const void* x, void* y,
                 const int* done, cudaStream_t s) {
@@ -594,11 +587,12 @@ int level_apply(sem_ctx* ctx, const Level& L, int precision, double alpha, const
     a.map = L.map; a.metric = L.metric; a.u = (const double*)x; a.y = (double*)y;
     a.nelem = L.nelem; a.mass_coef = alpha; a.out_scale = 1.0; a.scale_out = 0; a.done = done;
     e = launch_apply_fp64(L, a, false, s);
-  } else if (precision == SEM_PREC_FP32_BF16) {
+  } else if (precision == SEM_PREC_FP32_BF16 || precision == SEM_PREC_BF16_TC) {
     ApplyArgs<float, __nv_bfloat16> a{};
     a.map = L.map; a.metric = L.metric16; a.u = (const float*)x; a.y = (float*)y;
     a.nelem = L.nelem; a.mass_coef = (float)alpha; a.out_scale = 1.f; a.scale_out = 0; a.done = done;
-    e = launch_apply_bf16(L, a, false, s);
+    e = (precision == SEM_PREC_BF16_TC && tc_supported(L)) ? launch_apply_tc(L, a, s)
+                                                           : launch_apply_bf16(L, a, false, s);
   } else {
     ApplyArgs<float, float> a{};
     a.map = L.map; a.metric = L.metric32; a.u = (const float*)x; a.y = (float*)y;
@@ -910,10 +904,13 @@ int build(sem_ctx* ctx, cudaStream_t s) {
       if (!L.metric32) GMG_CK(cudaMalloc(&L.metric32, sizeof(float) * metric_count(L)));
       GMG_CK(setup_metric_lowp(L, false, s));
     }
-    if (g->precision == SEM_PREC_FP32_BF16 && !L.metric16_valid) {
+    const bool tc = g->precision == SEM_PREC_BF16_TC && tc_supported(L);
+    if ((g->precision == SEM_PREC_FP32_BF16 || (g->precision == SEM_PREC_BF16_TC && !tc)) &&
+        !L.metric16_valid) {
       if (!L.metric16) GMG_CK(cudaMalloc(&L.metric16, sizeof(__nv_bfloat16) * metric16_count(L)));
       GMG_CK(setup_metric_lowp(L, true, s));
     }
+    if (tc && !L.metric_tc_valid) GMG_CK(setup_metric_tc(L, s));
     void** vecs[] = {&V.b, &V.x, &V.t, &V.d, &V.invd};
     for (void** v : vecs) GMG_CK(cudaMalloc(v, es * L.ndofs));
     GMG_CK(cudaMemsetAsync(V.t, 0, es * L.ndofs, s));

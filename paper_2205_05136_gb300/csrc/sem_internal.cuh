@@ -113,7 +113,9 @@ struct Level {
   float* metric32 = nullptr;
   __nv_bfloat16* metric16 = nullptr;
   df_pair* metric2 = nullptr;  // FP64 metric split into FP32 pairs (df64 operator)
-  bool metric32_valid = false, metric16_valid = false, metric2_valid = false;
+  uint32_t* metric_tc = nullptr;  // bf16 metric in the tensor-core kernel's order (sem_apply_tc.cu)
+  uint32_t* tc_frag = nullptr;    // constant MMA fragments of the tensor-core kernel
+  bool metric32_valid = false, metric16_valid = false, metric2_valid = false, metric_tc_valid = false;
   double* mdiag = nullptr;
   double* kdiag = nullptr;
   double* xyz = nullptr;
@@ -184,6 +186,15 @@ cudaError_t launch_apply_dot_finish(const double* partials, int n, CgScalars* cg
 // Raises the dynamic shared-memory limit of the kernels that stage the metric in
 // shared memory; call once per device before any stream capture.
 cudaError_t prime_apply_kernels();
+
+// Tensor-core FP32 operator with the bf16 metric (sem_apply_tc.cu): SEM-NI, p = 2..4.
+bool tc_supported(const Level& L);
+size_t tc_metric_words(const Level& L);
+// Builds the level's metric_tc (from the FP64 metric) and constant fragments.
+cudaError_t setup_metric_tc(Level& L, cudaStream_t s);
+// y += (mass_coef M + K) u with a.u, a.y float vectors (a.map, a.metric unused).
+cudaError_t launch_apply_tc(const Level& L, const ApplyArgs<float, __nv_bfloat16>& a, cudaStream_t s);
+cudaError_t prime_apply_tc();
 
 // Level construction (sem_setup.cu): structured numbering of an nx x ny x nz
 // slab with host vertices, device allocation of map, element vertices, metric,

@@ -318,6 +318,8 @@ void level_free(Level& L) {
   cudaFree(L.metric32);
   cudaFree(L.metric16);
   cudaFree(L.metric2);
+  cudaFree(L.metric_tc);
+  cudaFree(L.tc_frag);
   cudaFree(L.mdiag);
   cudaFree(L.kdiag);
   cudaFree(L.xyz);
@@ -333,6 +335,7 @@ cudaError_t setup_geometry(Level& L, const double* sigma_l, const double* sigma_
   L.metric32_valid = false;
   L.metric16_valid = false;
   L.metric2_valid = false;
+  L.metric_tc_valid = false;
   return cudaGetLastError();
 }
 

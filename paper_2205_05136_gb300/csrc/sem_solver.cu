@@ -457,6 +457,25 @@ int apply_fp32(sem_ctx* ctx, double alpha, double beta, const float* u, float* y
   return SEM_OK;
 }
 
+int apply_tc(sem_ctx* ctx, double alpha, double beta, const float* u, float* y, cudaStream_t s) {
+  Level& L = ctx->L;
+  if (!tc_supported(L))
+    return fail(ctx, SEM_ERR_UNSUPPORTED, "the tensor-core apply covers SEM-NI at p = 2..4");
+  if (beta == 0.0) {  // SEM-NI mass: diagonal
+    k_scale_mul32<<<vec_grid(L.ndofs), kVecThreads, 0, s>>>(L.ndofs, (float)alpha, L.mdiag, u, y);
+    SEM_CK(cudaGetLastError());
+    return SEM_OK;
+  }
+  if (!L.metric_tc_valid) SEM_CK(setup_metric_tc(L, s));
+  SEM_CK(cudaMemsetAsync(y, 0, sizeof(float) * L.ndofs, s));
+  ApplyArgs<float, __nv_bfloat16> a{};
+  a.u = u; a.y = y; a.nelem = L.nelem;
+  a.mass_coef = (float)(alpha / beta); a.out_scale = (float)beta; a.scale_out = beta != 1.0;
+  SEM_CK(launch_apply_tc(L, a, s));
+  ctx->launches += 1;
+  return SEM_OK;
+}
+
 int cg_solve(sem_ctx* ctx, double alpha, const double* b, double* x, double rtol, double atol,
              int maxit, int precond, int* iters, double* final_res, sem_stats* stats,
              cudaStream_t s) {

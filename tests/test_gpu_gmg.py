@@ -57,7 +57,12 @@ def test_hierarchy_and_vcycle_fp64(dims, p, min_coarse, quad):
     assert rel(z.cpu().numpy(), ref) < 1e-10
 
 
-@pytest.mark.parametrize("precision,tol", [(capi.SEM_PREC_FP32, 1e-4), (capi.SEM_PREC_FP32_BF16, 5e-2)])
+# V-cycle error bounds against the oracle's FP64 V-cycle, about 3x the error
+# measured on a GB300: FP32 1.4e-7 (unit roundoff 2^-24 through a few
+# applies) -> 5e-7; bf16 metric 1.4e-3 (the metric's 2^-9 rounding) -> 5e-3,
+# shared by the tensor-core smoother, whose operator is the bf16-metric one.
+@pytest.mark.parametrize("precision,tol", [(capi.SEM_PREC_FP32, 5e-7), (capi.SEM_PREC_FP32_BF16, 5e-3),
+                                           (capi.SEM_PREC_BF16_TC, 5e-3)])
 def test_vcycle_low_precision_error(precision, tol):
     s, tissue, g, o, H = _setup((6, 4, 3), 4, "LGL", 30, precision)
     r = W.uniform_vector(o.ndofs, -1.0, 1.0, seed=3)
@@ -67,9 +72,14 @@ def test_vcycle_low_precision_error(precision, tol):
     assert e < tol, e
 
 
-@pytest.mark.parametrize("precision", [capi.SEM_PREC_FP32, capi.SEM_PREC_FP32_BF16, capi.SEM_PREC_FP64])
+@pytest.mark.parametrize("precision", [capi.SEM_PREC_FP32, capi.SEM_PREC_FP32_BF16, capi.SEM_PREC_FP64,
+                                       capi.SEM_PREC_BF16_TC])
 @pytest.mark.parametrize("quad", ["LGL", "LG"])
 def test_gmg_pcg_reaches_fp64_solution(precision, quad):
+    if precision == capi.SEM_PREC_BF16_TC and quad == "LG":
+        with pytest.raises(gb.SemError):
+            _setup((8, 5, 3), 4, quad, 200, precision)
+        return
     s, tissue, g, o, H = _setup((8, 5, 3), 4, quad, 200, precision)
     A = H.A[0]
     b = W.uniform_vector(o.ndofs, -1.0, 1.0, seed=5)
