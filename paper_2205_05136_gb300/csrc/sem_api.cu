@@ -82,7 +82,7 @@ void free_ctx(sem_ctx* ctx) {
   cudaFree(ctx->stim_mask);
   Workspace& w = ctx->ws;
   cudaFree(w.r); cudaFree(w.z); cudaFree(w.p); cudaFree(w.Ap); cudaFree(w.invdiag);
-  cudaFree(w.b); cudaFree(w.g);
+  cudaFree(w.b); cudaFree(w.g); cudaFree(w.p2);
   cudaFree(w.cg);
   if (w.cg_host) cudaFreeHost(w.cg_host);
   cudaFree(w.vec_partials);

@@ -327,9 +327,21 @@ __global__ void __launch_bounds__(kApplyThreads)
 
   // gather u_e = P_e u
   if constexpr (DOT) {
+    // the double-float operator with the fused inner product gathers u as the
+    // float pairs the CG kernel that formed u wrote (a.u2), converting nothing
     for (int idx = tid; idx < E * N3; idx += nth) {
       const int s = idx / N3, loc = idx - s * N3, e = e0 + s;
-      sA[idx] = (e < a.nelem) ? T(a.u[__ldg(a.map + (size_t)e * N3 + loc)]) : T(0);
+      if (e < a.nelem) {
+        const int gi = __ldg(a.map + (size_t)e * N3 + loc);
+        if constexpr (std::is_same<T, df>::value) {
+          const float2 v = __ldg(reinterpret_cast<const float2*>(a.u2) + gi);
+          sA[idx] = df(v.x, v.y);
+        } else {
+          sA[idx] = T(a.u[gi]);
+        }
+      } else {
+        sA[idx] = T(0);
+      }
     }
   } else {
     const int nv = min(E, a.nelem - e0) * N3;  // nodal values of the group's elements
@@ -413,14 +425,32 @@ __global__ void __launch_bounds__(kApplyThreads)
   // scatter-add y += P_e^T y_e, and with DOT the partial u_e . y_e
   double dot = 0.0;
   if constexpr (DOT) {
-    for (int idx = tid; idx < E * N3; idx += nth) {
-      const int s = idx / N3, loc = idx - s * N3, e = e0 + s;
-      if (e < a.nelem) {
-        const int g = __ldg(a.map + (size_t)e * N3 + loc);
-        T v = sA[idx];
-        if (a.scale_out) v *= a.out_scale;
-        scatter_add(a.y + g, v);
-        dot = fma((double)a.u[g], (double)v, dot);
+    if constexpr (std::is_same<T, df>::value) {
+      // the partial u_e . y_e in double-float arithmetic from the float pairs of u
+      // (in L1 since the gather)
+      df dd(0);
+      for (int idx = tid; idx < E * N3; idx += nth) {
+        const int s = idx / N3, loc = idx - s * N3, e = e0 + s;
+        if (e < a.nelem) {
+          const int g = __ldg(a.map + (size_t)e * N3 + loc);
+          T v = sA[idx];
+          if (a.scale_out) v *= a.out_scale;
+          scatter_add(a.y + g, v);
+          const float2 uu = __ldg(reinterpret_cast<const float2*>(a.u2) + g);
+          dd = fma(df(uu.x, uu.y), v, dd);
+        }
+      }
+      dot = (double)dd;
+    } else {
+      for (int idx = tid; idx < E * N3; idx += nth) {
+        const int s = idx / N3, loc = idx - s * N3, e = e0 + s;
+        if (e < a.nelem) {
+          const int g = __ldg(a.map + (size_t)e * N3 + loc);
+          T v = sA[idx];
+          if (a.scale_out) v *= a.out_scale;
+          scatter_add(a.y + g, v);
+          dot = fma((double)a.u[g], (double)v, dot);
+        }
       }
     }
   } else {

@@ -14,6 +14,7 @@ struct Workspace {
   bool ready = false;
   double *r = nullptr, *z = nullptr, *p = nullptr, *Ap = nullptr, *invdiag = nullptr;
   double *b = nullptr, *g = nullptr;
+  df_pair* p2 = nullptr;     // p split into float pairs for the double-float operator's gather
   double inv_alpha = -1.0;   // alpha for which invdiag holds 1 / diag(alpha M + K)
   CgScalars* cg = nullptr;   // device
   CgScalars* cg_host = nullptr;  // page-locked mirror

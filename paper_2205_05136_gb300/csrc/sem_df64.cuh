@@ -79,4 +79,25 @@ __device__ __forceinline__ df operator-(df a, df b) { return a + df(-b.h, -b.l);
 }  // namespace dfx
 using dfx::df;
 using dfx::df_pair;
+
+// x as a float pair (h, l), h + l = x to about 2^-48 relative, with integer and
+// FP32 instructions only (FP64 instructions, conversions included, issue at a
+// small fraction of the FP32 rate on GB300): h is x with its mantissa cut to
+// 23 bits, l the remaining 29 bits, m_low 2^(E - 1075), as a float (the one
+// rounding).  Zeros, tiny (|x| < 2^-63), huge and non-finite values take FP64
+// conversions instead.
+#ifdef __CUDACC__
+__device__ __forceinline__ df_pair split_pair(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7ffull);
+  if (E < 960 || E > 1150) {
+    const float h = (float)x;
+    return df_pair{h, (float)(x - (double)h)};
+  }
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const unsigned hb = sign | ((unsigned)(E - 896) << 23) | (unsigned)((b >> 29) & 0x7fffffull);
+  const float l = (float)(unsigned)(b & ((1ull << 29) - 1)) * __int_as_float((E - 948) << 23);
+  return df_pair{__int_as_float((int)hb), sign ? -l : l};
+}
+#endif
 }  // namespace sem

@@ -417,10 +417,11 @@ __global__ void k_fpcg_init(int64_t n, const double* __restrict__ b, double* __r
 // z_new = (double) x0; first iteration (no iteration finished yet): p = z_new,
 // rz = r.z_new; else beta = (r.z_new - r.z_old) / rz, rz = r.z_new (z holds
 // z_old on entry).  Pairs of entries by 16-byte (8-byte for float x0) accesses.
+// With p2 set, p is also written there as float pairs.
 template <typename T>
 __global__ void k_fpcg_z(int64_t n, const T* __restrict__ x0, double* __restrict__ z,
-                         const double* __restrict__ r, double* __restrict__ p, CgScalars* cg,
-                         double* partials, int stride, unsigned int* ticket) {
+                         const double* __restrict__ r, double* __restrict__ p, df_pair* __restrict__ p2,
+                         CgScalars* cg, double* partials, int stride, unsigned int* ticket) {
   if (cg->done) return;
   const bool first = cg->iters == 0;
   double v[2] = {0.0, 0.0};
@@ -437,7 +438,13 @@ __global__ void k_fpcg_z(int64_t n, const T* __restrict__ x0, double* __restrict
       if (!first) v[1] = fma(rr.e[k], zo.e[k], v[1]);
       v[0] = fma(rr.e[k], zn.e[k], v[0]);
     }
-    if (first) reinterpret_cast<D2*>(p)[c] = zn;
+    if (first) {
+      reinterpret_cast<D2*>(p)[c] = zn;
+      if (p2 != nullptr) {
+        const df_pair a0 = split_pair(zn.e[0]), a1 = split_pair(zn.e[1]);
+        reinterpret_cast<float4*>(p2)[c] = make_float4(a0.h, a0.l, a1.h, a1.l);
+      }
+    }
     reinterpret_cast<D2*>(z)[c] = zn;
   }
   GRID_TAIL(i, nc * 2, n) {
@@ -445,6 +452,7 @@ __global__ void k_fpcg_z(int64_t n, const T* __restrict__ x0, double* __restrict
     const double ri = r[i];
     if (first) {
       p[i] = zi;
+      if (p2 != nullptr) p2[i] = split_pair(zi);
     } else {
       v[1] = fma(ri, z[i], v[1]);
     }
@@ -467,7 +475,7 @@ __global__ void k_fpcg_z(int64_t n, const T* __restrict__ x0, double* __restrict
 }
 
 __global__ void k_fpcg_p(int64_t n, const double* __restrict__ z, double* __restrict__ p,
-                         const CgScalars* cg) {
+                         df_pair* __restrict__ p2, const CgScalars* cg) {
   if (cg->done || cg->iters == 0) return;  // first iteration: k_fpcg_z set p = z
   const double beta = cg->beta;
   using D2 = Pk<double, 2>;
@@ -478,8 +486,16 @@ __global__ void k_fpcg_p(int64_t n, const double* __restrict__ z, double* __rest
 #pragma unroll
     for (int k = 0; k < 2; ++k) pp.e[k] = fma(beta, pp.e[k], zz.e[k]);
     reinterpret_cast<D2*>(p)[c] = pp;
+    if (p2 != nullptr) {
+      const df_pair a0 = split_pair(pp.e[0]), a1 = split_pair(pp.e[1]);
+      reinterpret_cast<float4*>(p2)[c] = make_float4(a0.h, a0.l, a1.h, a1.l);
+    }
   }
-  GRID_TAIL(i, nc * 2, n) p[i] = fma(beta, p[i], z[i]);
+  GRID_TAIL(i, nc * 2, n) {
+    const double pi = fma(beta, p[i], z[i]);
+    p[i] = pi;
+    if (p2 != nullptr) p2[i] = split_pair(pi);
+  }
 }
 
 // x += alpha p, r -= alpha Ap, Ap = 0, b0 = (T) r; r.r; convergence.  VEC: x is
@@ -991,14 +1007,16 @@ int pcg_iter_seq(sem_ctx* ctx, Gmg& g, double alpha, double* x, cudaStream_t s) 
   const int* done = &w.cg->done;
   int rc = vcycle(ctx, g, done, s, true);
   if (rc != SEM_OK) return rc;
-  k_fpcg_z<T><<<gr, kThreads, 0, s>>>(n, (const T*)g.lv[0].x, g.z, w.r, w.p, w.cg, g.partials,
+  // the double-float operator gathers p as the float pairs the p kernels write
+  df_pair* p2 = ctx->op_precision == SEM_PREC_DF64 ? w.p2 : nullptr;
+  k_fpcg_z<T><<<gr, kThreads, 0, s>>>(n, (const T*)g.lv[0].x, g.z, w.r, w.p, p2, w.cg, g.partials,
                                       stride, g.tickets + 1);
-  k_fpcg_p<<<gr, kThreads, 0, s>>>(n, g.z, w.p, w.cg);
+  k_fpcg_p<<<gr, kThreads, 0, s>>>(n, g.z, w.p, p2, w.cg);
   GMG_CK(cudaGetLastError());
   ApplyArgs64 ap{};
   ap.map = L.map; ap.metric = L.metric; ap.u = w.p; ap.y = w.Ap; ap.nelem = L.nelem;
   ap.mass_coef = alpha; ap.out_scale = 1.0; ap.scale_out = 0; ap.done = done;
-  ap.dot_partials = w.apply_partials; ap.cg = w.cg;
+  ap.dot_partials = w.apply_partials; ap.cg = w.cg; ap.u2 = p2;
   // external records become event nodes of the captured graph (timing of the outer apply)
   GMG_CK(cudaEventRecordWithFlags(g.ev0, s, cudaEventRecordExternal));
   GMG_CK(launch_operator(ctx, ap, s));

@@ -167,6 +167,10 @@ struct ApplyArgs {
   double* dot_partials;
   CgScalars* cg;      // when set, the sum goes to pAp, and alpha = rz / pAp
   double* dot_out;    // otherwise the sum goes here
+  // optional (double-float operator with the fused inner product): u split into
+  // float pairs by the kernel that formed u; the gather then reads the pairs and
+  // converts nothing
+  const df_pair* u2;
 };
 using ApplyArgs64 = ApplyArgs<double, double>;
 

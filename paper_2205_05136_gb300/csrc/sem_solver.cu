@@ -91,8 +91,8 @@ __global__ void k_scale_mul32(int64_t n, float a, const double* __restrict__ d,
 __global__ void __launch_bounds__(kVecThreads)
     k_cg_init(int64_t n, const double* __restrict__ b, double* __restrict__ Ap,
               const double* __restrict__ inv, double* __restrict__ r, double* __restrict__ z,
-              double* __restrict__ p, CgScalars* cg, double* partials, unsigned int* ticket,
-              double rtol, double atol) {
+              double* __restrict__ p, df_pair* __restrict__ p2, CgScalars* cg, double* partials,
+              unsigned int* ticket, double rtol, double atol) {
   double v[3] = {0.0, 0.0, 0.0};
 #pragma unroll 1
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -103,6 +103,7 @@ __global__ void __launch_bounds__(kVecThreads)
     r[i] = ri;
     z[i] = zi;
     p[i] = zi;
+    if (p2 != nullptr) p2[i] = split_pair(zi);
     Ap[i] = 0.0;
     v[0] = fma(ri, zi, v[0]);
     v[1] = fma(ri, ri, v[1]);
@@ -188,9 +189,9 @@ __global__ void __launch_bounds__(kVecThreads)
   }
 }
 
-// p = z + beta p, Ap = 0.
+// p = z + beta p, Ap = 0; with p2 set, p also as float pairs (split_pair).
 __global__ void __launch_bounds__(kVecThreads)
-    k_cg_p(int64_t n, const double* __restrict__ z, double* __restrict__ p,
+    k_cg_p(int64_t n, const double* __restrict__ z, double* __restrict__ p, df_pair* __restrict__ p2,
            double* __restrict__ Ap, const CgScalars* cg) {
   if (cg->done) return;
   const double beta = cg->beta;
@@ -205,11 +206,17 @@ __global__ void __launch_bounds__(kVecThreads)
     for (int k = 0; k < 2; ++k) pp.e[k] = fma(beta, pp.e[k], zz.e[k]);
     reinterpret_cast<D2*>(p)[c] = pp;
     reinterpret_cast<D2*>(Ap)[c] = D2{};
+    if (p2 != nullptr) {
+      const df_pair a0 = split_pair(pp.e[0]), a1 = split_pair(pp.e[1]);
+      reinterpret_cast<float4*>(p2)[c] = make_float4(a0.h, a0.l, a1.h, a1.l);
+    }
   }
 #pragma unroll 1
   for (int64_t i = nc * 2 + g0; i < n; i += gs) {
-    p[i] = fma(beta, p[i], z[i]);
+    const double pi = fma(beta, p[i], z[i]);
+    p[i] = pi;
     Ap[i] = 0.0;
+    if (p2 != nullptr) p2[i] = split_pair(pi);
   }
 }
 
@@ -330,6 +337,7 @@ int ensure_workspace(sem_ctx* ctx) {
   const size_t n = (size_t)ctx->L.ndofs;
   double** vecs[] = {&w.r, &w.z, &w.p, &w.Ap, &w.invdiag, &w.b, &w.g};
   for (double** v : vecs) SEM_CK(cudaMalloc(v, sizeof(double) * n));
+  SEM_CK(cudaMalloc(&w.p2, sizeof(df_pair) * n));
   SEM_CK(cudaMalloc(&w.cg, sizeof(CgScalars)));
   SEM_CK(cudaMemset(w.cg, 0, sizeof(CgScalars)));
   SEM_CK(cudaMallocHost(&w.cg_host, sizeof(CgScalars)));
@@ -398,11 +406,14 @@ cudaError_t launch_operator(sem_ctx* ctx, const ApplyArgs64& a, cudaStream_t s) 
   Level& L = ctx->L;
   if (ctx->op_precision != SEM_PREC_DF64) return launch_apply_fp64(L, a, false, s);
   if (!L.metric2_valid) return cudaErrorNotReady;  // prepare_operator was not called
+  // the fused inner product of the double-float operator reads u as float pairs
+  if (a.dot_partials != nullptr && a.u2 == nullptr) return cudaErrorInvalidValue;
   ApplyArgs<df, df_pair> d{};
   d.map = a.map; d.metric = L.metric2; d.u = a.u; d.y = a.y; d.nelem = a.nelem;
   d.mass_coef = df(a.mass_coef); d.out_scale = df(a.out_scale); d.scale_out = a.scale_out;
   d.done = a.done; d.dot_partials = a.dot_partials; d.cg = a.cg;
   d.dot_out = a.dot_out;
+  d.u2 = a.u2;
   return launch_apply_df64(L, d, false, s);
 }
 
@@ -507,7 +518,9 @@ int cg_solve(sem_ctx* ctx, double alpha, const double* b, double* x, double rtol
     SEM_CK(launch_operator(ctx, a, s));
   }
   ctx->launches += 2;
-  k_cg_init<<<vg, kVecThreads, 0, s>>>(n, b, w.Ap, inv, w.r, w.z, w.p, w.cg, w.vec_partials,
+  // the double-float operator gathers p as the float pairs the p kernels write
+  df_pair* p2 = ctx->op_precision == SEM_PREC_DF64 ? w.p2 : nullptr;
+  k_cg_init<<<vg, kVecThreads, 0, s>>>(n, b, w.Ap, inv, w.r, w.z, w.p, p2, w.cg, w.vec_partials,
                                        w.tickets + 0, rtol, atol);
   SEM_CK(cudaGetLastError());
 
@@ -515,6 +528,7 @@ int cg_solve(sem_ctx* ctx, double alpha, const double* b, double* x, double rtol
   ap.done = &w.cg->done;
   ap.dot_partials = w.apply_partials;
   ap.cg = w.cg;
+  ap.u2 = p2;
 
   Timing& tm = ctx->timing;
   constexpr int kChunkMax = 16;
@@ -541,7 +555,7 @@ int cg_solve(sem_ctx* ctx, double alpha, const double* b, double* x, double rtol
         else
           k_cg_xr<false><<<vg, kVecThreads, 0, s>>>(n, x, w.p, w.Ap, w.r, inv, w.z, w.cg, w.vec_partials,
                                                     w.tickets + 0);
-        k_cg_p<<<vg, kVecThreads, 0, s>>>(n, w.z, w.p, w.Ap, w.cg);
+        k_cg_p<<<vg, kVecThreads, 0, s>>>(n, w.z, w.p, p2, w.Ap, w.cg);
       }
       SEM_CK(cudaGetLastError());
       launched += this_chunk;
