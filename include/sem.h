@@ -148,6 +148,21 @@ int sem_apply(sem_ctx* ctx, double alpha, double beta, const void* u, void* y, i
  * products stay FP64). */
 int sem_set_operator_precision(sem_ctx* ctx, int precision);
 
+/* Deterministic mode (enable = 1) or atomic scatter (0, the default).  The
+ * element results of an operator apply (Algorithm 1's "compress" step) are
+ * normally added into the global vector with atomic adds, whose order varies
+ * from run to run, so results differ in the last bits.  In deterministic mode
+ * every apply (sem_apply, sem_cg_solve, sem_step, the multigrid V-cycle and its
+ * restrictions, the adjoint's solves) writes element-local results and a node
+ * kernel adds each node's contributions in a fixed element order: the same
+ * inputs give bitwise the same outputs, at the cost of an extra pass over
+ * nelem (p+1)^3 values per apply.  The tensor-core smoother runs the scalar
+ * bf16-metric kernel in this mode and sem_apply with SEM_PREC_BF16_TC returns
+ * SEM_ERR_UNSUPPORTED; sem_apply_dot_static keeps atomic adds.  The first
+ * enable allocates nelem (p+1)^3 doubles (owned by the context; SEM_ERR_NOMEM
+ * when that fails).  Synchronises the device. */
+int sem_set_deterministic(sem_ctx* ctx, int enable);
+
 /* Diagonal of alpha M + beta K: device double d[ndofs]. */
 int sem_diagonal(sem_ctx* ctx, double alpha, double beta, double* d, void* stream);
 

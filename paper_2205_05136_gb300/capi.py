@@ -49,7 +49,7 @@ EXPORTS = [
     "sem_state_set", "sem_state_get", "sem_state_restore", "sem_step", "sem_step_host", "sem_step_host_out",
     "sem_state_track_activation", "sem_state_get_activation",
     "sem_set_timing", "sem_apply_dot_static", "sem_set_gmg", "sem_vcycle", "sem_gmg_info",
-    "sem_forward_record", "sem_adjoint_grad", "sem_set_operator_precision",
+    "sem_forward_record", "sem_adjoint_grad", "sem_set_operator_precision", "sem_set_deterministic",
 ]
 
 
@@ -116,6 +116,7 @@ def lib():
             "sem_apply_dot_static": (_I, [_P, _D, _D, _P, _P, _P, _P]),
             "sem_set_gmg": (_I, [_P, _I, _I, _I, _I]),
             "sem_set_operator_precision": (_I, [_P, _I]),
+            "sem_set_deterministic": (_I, [_P, _I]),
             "sem_forward_record": (_I, [_P, _P, _D, _I, _I, _P, _I, _P, _D, _D, _I, _I,
                                         ctypes.POINTER(sem_stats), _P]),
             "sem_adjoint_grad": (_I, [_P, _P, _P, _P, _P, _D, _D, _I, _I, ctypes.POINTER(sem_stats), _P]),
@@ -336,6 +337,10 @@ def sem_apply_dot_static(ctx, alpha, beta, u, y, dot, stream=None):
                                              _dev(y, torch.float64, n, "y"),
                                              _dev(dot, torch.float64, 1, "dot"),
                                              _stream(stream)), ctx)
+
+
+def sem_set_deterministic(ctx, enable: bool):
+    return _check(lib().sem_set_deterministic(ctx, 1 if enable else 0), ctx)
 
 
 def sem_set_gmg(ctx, degree=3, coarse_degree=10, min_coarse_dofs=2000, precision=SEM_PREC_FP32):

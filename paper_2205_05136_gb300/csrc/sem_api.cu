@@ -83,6 +83,7 @@ void free_ctx(sem_ctx* ctx) {
   Workspace& w = ctx->ws;
   cudaFree(w.r); cudaFree(w.z); cudaFree(w.p); cudaFree(w.Ap); cudaFree(w.invdiag);
   cudaFree(w.b); cudaFree(w.g); cudaFree(w.p2);
+  cudaFree(ctx->det_scratch);
   cudaFree(w.cg);
   if (w.cg_host) cudaFreeHost(w.cg_host);
   cudaFree(w.vec_partials);
@@ -281,6 +282,24 @@ int sem_set_operator_precision(sem_ctx* ctx, int precision) {
   cudaDeviceSynchronize();
   ctx->op_precision = precision;
   gmg_free(ctx);  // captured graphs embed the operator kernel
+  return SEM_OK;
+}
+
+int sem_set_deterministic(sem_ctx* ctx, int enable) {
+  CK_CTX(ctx);
+  DeviceGuard guard(ctx->device);
+  cudaDeviceSynchronize();
+  if (enable && ctx->det_scratch == nullptr) {
+    const Level& L = ctx->L;
+    const size_t n = (size_t)L.nelem * L.n * L.n * L.n;
+    if (cudaMalloc(&ctx->det_scratch, sizeof(double) * n) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->det_scratch = nullptr;
+      return fail(ctx, SEM_ERR_NOMEM, "cannot allocate the element-local results of the deterministic mode");
+    }
+  }
+  ctx->deterministic = enable != 0;
+  gmg_free(ctx);  // captured graphs embed the apply and transfer kernels
   return SEM_OK;
 }
 

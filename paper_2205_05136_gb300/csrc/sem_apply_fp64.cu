@@ -35,6 +35,53 @@ cudaError_t launch_apply_dot_finish(const double* partials, int n, CgScalars* cg
   return cudaGetLastError();
 }
 
+// y[g] += sum of the element contributions of node g (I, J, K); the elements
+// holding it are ex in [lo(I), hi(I)] (two when I is a multiple of p inside
+// the lattice, else one), likewise ey and ez, summed in ez, ey, ex order.
+template <typename V>
+__global__ void __launch_bounds__(256)
+    k_assemble(int nx, int ny, int nz, int p, const V* __restrict__ yloc, V* __restrict__ y,
+               const int* done) {
+  if (done != nullptr && *done) return;
+  const int n = p + 1, n2 = n * n, n3 = n2 * n;
+  const int64_t NX = (int64_t)p * nx + 1, NY = (int64_t)p * ny + 1, nd = NX * NY * ((int64_t)p * nz + 1);
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nd;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int I = (int)(g % NX), J = (int)((g / NX) % NY), K = (int)(g / (NX * NY));
+    auto range = [p](int idx, int ne, int& lo, int& hi) {
+      hi = min(idx / p, ne - 1);
+      lo = (idx % p == 0 && idx > 0 && idx / p <= ne - 1) ? idx / p - 1 : hi;
+    };
+    int x0, x1, y0, y1, z0, z1;
+    range(I, nx, x0, x1);
+    range(J, ny, y0, y1);
+    range(K, nz, z0, z1);
+    V acc = V(0);
+    for (int ez = z0; ez <= z1; ++ez)
+      for (int ey = y0; ey <= y1; ++ey)
+        for (int ex = x0; ex <= x1; ++ex) {
+          const int64_t e = ex + (int64_t)nx * (ey + (int64_t)ny * ez);
+          acc += yloc[e * n3 + (I - p * ex) + n * (J - p * ey) + n2 * (K - p * ez)];
+        }
+    y[g] += acc;
+  }
+}
+
+template <typename V>
+cudaError_t assemble_t(const Level& L, const V* yloc, V* y, const int* done, cudaStream_t s) {
+  const int64_t want = (L.ndofs + 255) / 256;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, 152 * 16));
+  k_assemble<V><<<grid, 256, 0, s>>>(L.nx, L.ny, L.nz, L.p, yloc, y, done);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assemble(const Level& L, const double* yloc, double* y, const int* done, cudaStream_t s) {
+  return assemble_t(L, yloc, y, done, s);
+}
+cudaError_t launch_assemble(const Level& L, const float* yloc, float* y, const int* done, cudaStream_t s) {
+  return assemble_t(L, yloc, y, done, s);
+}
+
 int apply_grid_blocks(const Level& L) {
   int E = 1;
   switch (L.p) {

@@ -55,6 +55,10 @@ __device__ __forceinline__ df ldmetric(const df_pair* p) {
 __device__ __forceinline__ void scatter_add(double* p, double v) { atomicAdd(p, v); }
 __device__ __forceinline__ void scatter_add(float* p, float v) { atomicAdd(p, v); }
 __device__ __forceinline__ void scatter_add(double* p, df v) { atomicAdd(p, (double)v); }
+// Element-local store of one element result (deterministic mode).
+__device__ __forceinline__ void store_loc(double* p, double v) { *p = v; }
+__device__ __forceinline__ void store_loc(float* p, float v) { *p = v; }
+__device__ __forceinline__ void store_loc(double* p, df v) { *p = (double)v; }
 
 // Base offset and stride of line l of an n^3 tile along direction DIR
 // (0: x-line (j,k), l = j + n k; 1: y-line (i,k), l = i + n k; 2: z-line (i,j), l = i + n j).
@@ -435,7 +439,8 @@ __global__ void __launch_bounds__(kApplyThreads)
           const int g = __ldg(a.map + (size_t)e * N3 + loc);
           T v = sA[idx];
           if (a.scale_out) v *= a.out_scale;
-          scatter_add(a.y + g, v);
+          if (a.yloc != nullptr) store_loc(a.yloc + (size_t)e * N3 + loc, v);
+          else scatter_add(a.y + g, v);
           const float2 uu = __ldg(reinterpret_cast<const float2*>(a.u2) + g);
           dd = fma(df(uu.x, uu.y), v, dd);
         }
@@ -448,7 +453,8 @@ __global__ void __launch_bounds__(kApplyThreads)
           const int g = __ldg(a.map + (size_t)e * N3 + loc);
           T v = sA[idx];
           if (a.scale_out) v *= a.out_scale;
-          scatter_add(a.y + g, v);
+          if (a.yloc != nullptr) store_loc(a.yloc + (size_t)e * N3 + loc, v);
+          else scatter_add(a.y + g, v);
           dot = fma((double)a.u[g], (double)v, dot);
         }
       }
@@ -462,7 +468,8 @@ __global__ void __launch_bounds__(kApplyThreads)
       if ((IT * NTH == E * N3 || idx < E * N3) && idx < nv) {
         T v = sA[idx];
         if (a.scale_out) v *= a.out_scale;
-        scatter_add(a.y + __ldg(gmap + idx), v);
+        if (a.yloc != nullptr) store_loc(a.yloc + (size_t)e0 * N3 + idx, v);
+        else scatter_add(a.y + __ldg(gmap + idx), v);
       }
     }
   }
@@ -694,7 +701,13 @@ __global__ void __launch_bounds__(kApplyThreads, 4)
     }
     // scatter-add y += P_e^T y_e
     const T sc = a.scale_out ? a.out_scale : T(1);
-    if (e0 + G <= a.nelem) {
+    if (a.yloc != nullptr) {  // deterministic mode: element-local results
+#pragma unroll
+      for (int t = 0; t < LPL; ++t) {
+        const int idx = lane + 32 * t;
+        if (idx < C::UT && e0 + idx / N3 < a.nelem) a.yloc[(size_t)e0 * N3 + idx] = sA[idx] * sc;
+      }
+    } else if (e0 + G <= a.nelem) {
 #pragma unroll
       for (int t = 0; t < LPL; ++t) {
         const int idx = lane + 32 * t;
@@ -774,17 +787,12 @@ void make_eo(EoMat<N, T>& E, const double (&M)[kMaxN][kMaxN], bool transpose) {
       for (int l = 0; l < N; ++l) E.m[q][l] = (T)m(q, l);
 }
 
-// Launch helper shared by the precision-specific translation units.
+// The apply kernels of one degree, quadrature and precision (atomic adds into
+// y, or element-local results into a.yloc).
 template <int P, int QUAD, typename T, typename MT>
-cudaError_t launch_apply_t(const Level& L, const ApplyArgs<T, MT>& a, bool mass_only, bool dot,
-                           cudaStream_t s) {
-  constexpr int N = P + 1;
-  KTab<N, T> tab;
-  make_eo(tab.D, QUAD == SEM_QUAD_LG ? L.tab.Dg : L.tab.D, false);
-  make_eo(tab.Dt, QUAD == SEM_QUAD_LG ? L.tab.Dg : L.tab.D, true);
-  make_eo(tab.Bi, L.tab.Bi, false);
-  make_eo(tab.Bit, L.tab.Bi, true);
-  const int E = ApplyCfg<P>::E;
+cudaError_t launch_apply_kernels(const Level& L, const ApplyArgs<T, MT>& a, const KTab<P + 1, T>& tab,
+                                 bool mass_only, bool dot, cudaStream_t s) {
+  constexpr int E = ApplyCfg<P>::E;
   const int grid = (L.nelem + E - 1) / E;
   if (grid == 0) return cudaSuccess;
   constexpr size_t tiles = apply_tile_bytes<P, T, MT>();
@@ -816,6 +824,23 @@ cudaError_t launch_apply_t(const Level& L, const ApplyArgs<T, MT>& a, bool mass_
     sem_apply_kernel<P, QUAD, T, MT, false, false><<<grid, kApplyThreads, full, s>>>(a, tab);
   }
   return cudaGetLastError();
+}
+
+// Launch helper shared by the precision-specific translation units.  With
+// a.yloc set (deterministic mode) the kernels write element results and the
+// node sums follow in a fixed order.
+template <int P, int QUAD, typename T, typename MT>
+cudaError_t launch_apply_t(const Level& L, const ApplyArgs<T, MT>& a, bool mass_only, bool dot,
+                           cudaStream_t s) {
+  constexpr int N = P + 1;
+  KTab<N, T> tab;
+  make_eo(tab.D, QUAD == SEM_QUAD_LG ? L.tab.Dg : L.tab.D, false);
+  make_eo(tab.Dt, QUAD == SEM_QUAD_LG ? L.tab.Dg : L.tab.D, true);
+  make_eo(tab.Bi, L.tab.Bi, false);
+  make_eo(tab.Bit, L.tab.Bi, true);
+  const cudaError_t e = launch_apply_kernels<P, QUAD, T, MT>(L, a, tab, mass_only, dot, s);
+  if (e != cudaSuccess || a.yloc == nullptr) return e;
+  return launch_assemble(L, a.yloc, a.y, a.done, s);
 }
 
 // Dynamic shared-memory limits of the three variants of one instantiation.

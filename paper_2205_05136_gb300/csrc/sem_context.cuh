@@ -58,6 +58,10 @@ struct sem_ctx {
   int gmg_precision = SEM_PREC_FP32;
   int op_precision = SEM_PREC_FP64;  // operator of the CG iterations: FP64 or DF64
   sem_state* host_state = nullptr;  // device copy of the state for sem_step_host
+  // deterministic mode: element-local results of every apply and restriction,
+  // summed per node in a fixed order (scratch of nelem n^3 doubles, fine level)
+  bool deterministic = false;
+  double* det_scratch = nullptr;
   // device address of sem_apply_dot_static's static scratch array in the CUDA
   // context this sem_ctx was created in (looked up on that entry point's first call)
   double* static_scratch = nullptr;

@@ -36,7 +36,7 @@ namespace sem {
 // Sum-factorized p-transfers (sem_transfer.cu).
 template <typename T>
 cudaError_t p_transfer(bool prolong, const Level& F, const Level& C, const double (*P)[kMaxN],
-                       const T* src_b, const T* src_t, T* dst, T* dst_t, const int* done,
+                       const T* src_b, const T* src_t, T* dst, T* dst_t, T* loc, const int* done,
                        cudaStream_t s);
 
 struct GmgLevel {
@@ -281,6 +281,43 @@ __global__ void k_restrict_h(int nfx, int nfy, int nfz, int ncx, int ncy, int nc
           const double w = wx[a] * wy[b] * wz[c];
           if (w != 0.0) atomicAdd(bc + (kx + a) + CX * ((ky + b) + CY * (kz + c)), (T)w * r);
         }
+  }
+}
+
+// The same restriction gathered per coarse node (deterministic mode): the fine
+// nodes within 3 of 2 C in each direction, in a fixed order, weighted by the
+// trilinear prolongation's weight of that coarse node.
+template <typename T>
+__global__ void k_restrict_h_det(int nfx, int nfy, int nfz, int ncx, int ncy, int ncz,
+                                 const T* __restrict__ bf, const T* __restrict__ tf,
+                                 T* __restrict__ bc, const int* done) {
+  if (skip(done)) return;
+  const int64_t NX = nfx + 1, NY = nfy + 1;
+  const int64_t CX = ncx + 1, CY = ncy + 1, nc = CX * CY * (ncz + 1);
+  GRID_LOOP(c, nc) {
+    const int CI = (int)(c % CX), CJ = (int)((c / CX) % CY), CK = (int)(c / (CX * CY));
+    auto wt = [](int I, int nf, int ncoarse, int C) {
+      int k;
+      double w0, w1;
+      hweights(I, nf, ncoarse, k, w0, w1);
+      return k == C ? w0 : (k + 1 == C ? w1 : 0.0);
+    };
+    T acc = T(0);
+    for (int K = max(0, 2 * CK - 3); K <= min(nfz, 2 * CK + 3); ++K) {
+      const double wz = wt(K, nfz, ncz, CK);
+      if (wz == 0.0) continue;
+      for (int J = max(0, 2 * CJ - 3); J <= min(nfy, 2 * CJ + 3); ++J) {
+        const double wy = wt(J, nfy, ncy, CJ);
+        if (wy == 0.0) continue;
+        for (int I = max(0, 2 * CI - 3); I <= min(nfx, 2 * CI + 3); ++I) {
+          const double wx = wt(I, nfx, ncx, CI);
+          if (wx == 0.0) continue;
+          const int64_t g = I + NX * (J + NY * (int64_t)K);
+          acc += (T)(wx * wy * wz) * (bf[g] - tf[g]);
+        }
+      }
+    }
+    bc[c] += acc;
   }
 }
 
@@ -598,21 +635,26 @@ double tridiag_max_eig(const std::vector<double>& a, const std::vector<double>& 
 int level_apply(sem_ctx* ctx, const Level& L, int precision, double alpha, const void* x, void* y,
                 const int* done, cudaStream_t s) {
   cudaError_t e;
+  // deterministic mode: element-local results and fixed-order node sums (scalar kernels)
+  void* loc = ctx->deterministic ? ctx->det_scratch : nullptr;
   if (precision == SEM_PREC_FP64) {
     ApplyArgs64 a{};
     a.map = L.map; a.metric = L.metric; a.u = (const double*)x; a.y = (double*)y;
     a.nelem = L.nelem; a.mass_coef = alpha; a.out_scale = 1.0; a.scale_out = 0; a.done = done;
+    a.yloc = (double*)loc;
     e = launch_apply_fp64(L, a, false, s);
   } else if (precision == SEM_PREC_FP32_BF16 || precision == SEM_PREC_BF16_TC) {
     ApplyArgs<float, __nv_bfloat16> a{};
     a.map = L.map; a.metric = L.metric16; a.u = (const float*)x; a.y = (float*)y;
     a.nelem = L.nelem; a.mass_coef = (float)alpha; a.out_scale = 1.f; a.scale_out = 0; a.done = done;
-    e = (precision == SEM_PREC_BF16_TC && tc_supported(L)) ? launch_apply_tc(L, a, s)
-                                                           : launch_apply_bf16(L, a, false, s);
+    a.yloc = (float*)loc;
+    e = (precision == SEM_PREC_BF16_TC && tc_supported(L) && loc == nullptr) ? launch_apply_tc(L, a, s)
+                                                                             : launch_apply_bf16(L, a, false, s);
   } else {
     ApplyArgs<float, float> a{};
     a.map = L.map; a.metric = L.metric32; a.u = (const float*)x; a.y = (float*)y;
     a.nelem = L.nelem; a.mass_coef = (float)alpha; a.out_scale = 1.f; a.scale_out = 0; a.done = done;
+    a.yloc = (float*)loc;
     e = launch_apply_fp32(L, a, false, s);
   }
   if (e != cudaSuccess) return cuda_fail(ctx, e, "level apply");
@@ -653,10 +695,15 @@ int restrict_to(sem_ctx* ctx, Gmg& g, int l, const int* done, cudaStream_t s) {
   GmgLevel& F = g.lv[l];
   GmgLevel& C = g.lv[l + 1];
   k_zero<T><<<grid_chunks<T>(C.L->ndofs), kThreads, 0, s>>>(C.L->ndofs, (T*)C.b, done);
+  T* loc = ctx->deterministic ? reinterpret_cast<T*>(ctx->det_scratch) : nullptr;
   if (F.to_next == 0) {
     const PTab tab = make_ptab(*F.L, *C.L);
     GMG_CK(p_transfer<T>(false, *F.L, *C.L, tab.P, (const T*)F.b, (const T*)F.t, (T*)C.b, nullptr,
-                         done, s));
+                         loc, done, s));
+  } else if (loc != nullptr) {
+    k_restrict_h_det<T><<<grid1d(C.L->ndofs), kThreads, 0, s>>>(
+        F.L->nx, F.L->ny, F.L->nz, C.L->nx, C.L->ny, C.L->nz, (const T*)F.b, (const T*)F.t,
+        (T*)C.b, done);
   } else {
     k_restrict_h<T><<<grid1d(F.L->ndofs), kThreads, 0, s>>>(
         F.L->nx, F.L->ny, F.L->nz, C.L->nx, C.L->ny, C.L->nz, (const T*)F.b, (const T*)F.t,
@@ -673,8 +720,8 @@ int prolong_from(sem_ctx* ctx, Gmg& g, int l, const int* done, cudaStream_t s) {
   GmgLevel& C = g.lv[l + 1];
   if (F.to_next == 0) {
     const PTab tab = make_ptab(*F.L, *C.L);
-    GMG_CK(p_transfer<T>(true, *F.L, *C.L, tab.P, (const T*)C.x, nullptr, (T*)F.x, (T*)F.t, done,
-                         s));
+    GMG_CK(p_transfer<T>(true, *F.L, *C.L, tab.P, (const T*)C.x, nullptr, (T*)F.x, (T*)F.t, nullptr,
+                         done, s));
   } else {
     k_prolong_h<T><<<grid1d(F.L->ndofs), kThreads, 0, s>>>(
         F.L->nx, F.L->ny, F.L->nz, C.L->nx, C.L->ny, C.L->nz, (const T*)C.x, (T*)F.x, (T*)F.t,
@@ -766,6 +813,7 @@ int estimate_lambda(sem_ctx* ctx, Gmg& g, GmgLevel& V, double alpha, cudaStream_
     ApplyArgs64 a{};
     a.map = L.map; a.metric = L.metric; a.u = g.lp; a.y = g.lAp; a.nelem = L.nelem;
     a.mass_coef = alpha; a.out_scale = 1.0; a.scale_out = 0;
+    a.yloc = ctx->deterministic ? ctx->det_scratch : nullptr;
     GMG_CK(launch_apply_fp64(L, a, false, s));
     k_dot<<<gr, kThreads, 0, s>>>(n, g.lp, g.lAp, g.partials, g.tickets, g.dots + 1);
     GMG_CK(cudaMemcpyAsync(h, g.dots + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -920,7 +968,7 @@ int build(sem_ctx* ctx, cudaStream_t s) {
       if (!L.metric32) GMG_CK(cudaMalloc(&L.metric32, sizeof(float) * metric_count(L)));
       GMG_CK(setup_metric_lowp(L, false, s));
     }
-    const bool tc = g->precision == SEM_PREC_BF16_TC && tc_supported(L);
+    const bool tc = g->precision == SEM_PREC_BF16_TC && tc_supported(L) && !ctx->deterministic;
     if ((g->precision == SEM_PREC_FP32_BF16 || (g->precision == SEM_PREC_BF16_TC && !tc)) &&
         !L.metric16_valid) {
       if (!L.metric16) GMG_CK(cudaMalloc(&L.metric16, sizeof(__nv_bfloat16) * metric16_count(L)));
@@ -985,6 +1033,7 @@ int pcg_init_seq(sem_ctx* ctx, Gmg& g, double alpha, const double* b, const doub
     ApplyArgs64 a{};
     a.map = L.map; a.metric = L.metric; a.u = x; a.y = w.Ap; a.nelem = L.nelem;
     a.mass_coef = alpha; a.out_scale = 1.0; a.scale_out = 0;
+    a.yloc = ctx->deterministic ? ctx->det_scratch : nullptr;
     GMG_CK(launch_operator(ctx, a, s));
   }
   if (aligned16(b))
@@ -1017,6 +1066,7 @@ int pcg_iter_seq(sem_ctx* ctx, Gmg& g, double alpha, double* x, cudaStream_t s) 
   ap.map = L.map; ap.metric = L.metric; ap.u = w.p; ap.y = w.Ap; ap.nelem = L.nelem;
   ap.mass_coef = alpha; ap.out_scale = 1.0; ap.scale_out = 0; ap.done = done;
   ap.dot_partials = w.apply_partials; ap.cg = w.cg; ap.u2 = p2;
+  ap.yloc = ctx->deterministic ? ctx->det_scratch : nullptr;
   // external records become event nodes of the captured graph (timing of the outer apply)
   GMG_CK(cudaEventRecordWithFlags(g.ev0, s, cudaEventRecordExternal));
   GMG_CK(launch_operator(ctx, ap, s));

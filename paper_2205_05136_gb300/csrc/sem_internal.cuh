@@ -171,6 +171,10 @@ struct ApplyArgs {
   // float pairs by the kernel that formed u; the gather then reads the pairs and
   // converts nothing
   const df_pair* u2;
+  // optional (deterministic mode): element results go to yloc[e][n^3] instead of
+  // atomic adds, and a node kernel then adds each node's contributions to y in a
+  // fixed order
+  typename VecOf<T>::type* yloc;
 };
 using ApplyArgs64 = ApplyArgs<double, double>;
 
@@ -183,6 +187,11 @@ cudaError_t launch_apply_bf16(const Level& L, const ApplyArgs<float, __nv_bfloat
 cudaError_t launch_apply_df64(const Level& L, const ApplyArgs<df, df_pair>& a, bool mass_only,
                               cudaStream_t s);
 int apply_grid_blocks(const Level& L);
+// y[g] += the element contributions yloc[e][n^3] of node g, elements in a fixed
+// order (ez, ey, ex ascending): the deterministic assembly of the apply kernels'
+// element results (and of the p-restriction's coarse-element results).
+cudaError_t launch_assemble(const Level& L, const double* yloc, double* y, const int* done, cudaStream_t s);
+cudaError_t launch_assemble(const Level& L, const float* yloc, float* y, const int* done, cudaStream_t s);
 // Sum, in a fixed order, of the n per-CTA partials of a fused inner product:
 // to cg (pAp and alpha = rz / pAp) when set, else to *out; nothing when *done.
 cudaError_t launch_apply_dot_finish(const double* partials, int n, CgScalars* cg, double* out,

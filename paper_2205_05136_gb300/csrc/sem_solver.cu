@@ -364,6 +364,7 @@ ApplyArgs64 base_args(sem_ctx* ctx, double alpha, double beta, const double* u, 
   a.mass_coef = alpha / beta;
   a.out_scale = beta;
   a.scale_out = beta != 1.0;
+  a.yloc = ctx->deterministic ? ctx->det_scratch : nullptr;
   return a;
 }
 
@@ -414,6 +415,7 @@ cudaError_t launch_operator(sem_ctx* ctx, const ApplyArgs64& a, cudaStream_t s) 
   d.done = a.done; d.dot_partials = a.dot_partials; d.cg = a.cg;
   d.dot_out = a.dot_out;
   d.u2 = a.u2;
+  d.yloc = a.yloc;
   return launch_apply_df64(L, d, false, s);
 }
 
@@ -458,11 +460,13 @@ int apply_fp32(sem_ctx* ctx, double alpha, double beta, const float* u, float* y
     ApplyArgs<float, __nv_bfloat16> a{};
     a.map = L.map; a.metric = L.metric16; a.u = u; a.y = y; a.nelem = L.nelem;
     a.mass_coef = (float)(alpha / bb); a.out_scale = (float)bb; a.scale_out = bb != 1.0;
+    a.yloc = ctx->deterministic ? (float*)ctx->det_scratch : nullptr;
     SEM_CK(launch_apply_bf16(L, a, mass_only, s));
   } else {
     ApplyArgs<float, float> a{};
     a.map = L.map; a.metric = L.metric32; a.u = u; a.y = y; a.nelem = L.nelem;
     a.mass_coef = (float)(alpha / bb); a.out_scale = (float)bb; a.scale_out = bb != 1.0;
+    a.yloc = ctx->deterministic ? (float*)ctx->det_scratch : nullptr;
     SEM_CK(launch_apply_fp32(L, a, mass_only, s));
   }
   return SEM_OK;
@@ -472,6 +476,8 @@ int apply_tc(sem_ctx* ctx, double alpha, double beta, const float* u, float* y, 
   Level& L = ctx->L;
   if (!tc_supported(L))
     return fail(ctx, SEM_ERR_UNSUPPORTED, "the tensor-core apply covers SEM-NI at p = 2..4");
+  if (ctx->deterministic)
+    return fail(ctx, SEM_ERR_UNSUPPORTED, "the tensor-core apply has no deterministic mode");
   if (beta == 0.0) {  // SEM-NI mass: diagonal
     k_scale_mul32<<<vec_grid(L.ndofs), kVecThreads, 0, s>>>(L.ndofs, (float)alpha, L.mdiag, u, y);
     SEM_CK(cudaGetLastError());

@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(kTThreads)
     k_restrict_sf(int nelem, int nx, int ny, int nz, const int* __restrict__ map_c,
                   const int* __restrict__ map_f, const __grid_constant__ PMat<NF, NC, T> pm,
                   const T* __restrict__ bf, const T* __restrict__ tf, T* __restrict__ bc,
-                  const int* done) {
+                  T* __restrict__ bloc, const int* done) {
   if (done != nullptr && *done) return;
   constexpr int E = TransferCfg<NF>::E;
   constexpr int NF3 = NF * NF * NF, NC3 = NC * NC * NC;
@@ -208,6 +208,11 @@ __global__ void __launch_bounds__(kTThreads)
 #pragma unroll
     for (int k = 0; k < NF; ++k) in[k] = s2[s * NF * NC * NC + (k * NC + b) * NC + a];
     down_line<NF, NC>(pm.P, in, out);
+    if (bloc != nullptr) {  // deterministic mode: coarse-element results, assembled afterwards
+#pragma unroll
+      for (int c = 0; c < NC; ++c) bloc[(size_t)(e0 + s) * NC3 + c * NC * NC + b * NC + a] = out[c];
+      continue;
+    }
     const int* gm = map_c + (size_t)(e0 + s) * NC3 + b * NC + a;
 #pragma unroll
     for (int c = 0; c < NC; ++c) atomicAdd(bc + __ldg(gm + c * NC * NC), out[c]);
@@ -216,7 +221,7 @@ __global__ void __launch_bounds__(kTThreads)
 
 template <int NF, int NC, typename T>
 cudaError_t launch_pair(bool prolong, const Level& F, const Level& C, const double (*P)[kMaxN],
-                        const T* src_b, const T* src_t, T* dst, T* dst_t, const int* done,
+                        const T* src_b, const T* src_t, T* dst, T* dst_t, T* loc, const int* done,
                         cudaStream_t s) {
   PMat<NF, NC, T> pm;
   for (int i = 0; i < NF; ++i)
@@ -228,21 +233,25 @@ cudaError_t launch_pair(bool prolong, const Level& F, const Level& C, const doub
                                                        src_b, dst, dst_t, done);
   else
     k_restrict_sf<NF, NC, T><<<grid, kTThreads, 0, s>>>(F.nelem, F.nx, F.ny, F.nz, C.map, F.map, pm,
-                                                        src_b, src_t, dst, done);
-  return cudaGetLastError();
+                                                        src_b, src_t, dst, loc, done);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || prolong || loc == nullptr) return e;
+  return launch_assemble(C, loc, dst, done, s);
 }
 
 }  // namespace
 
 // prolong: dst (fine x) += P src_b (coarse x), dst_t (fine t) cleared.
-// restrict: dst (coarse b) += P^T (src_b - src_t) (fine b, fine t).
+// restrict: dst (coarse b) += P^T (src_b - src_t) (fine b, fine t); with loc set
+// (deterministic mode) through coarse-element results in loc and the
+// fixed-order node sums instead of atomic adds.
 template <typename T>
 cudaError_t p_transfer(bool prolong, const Level& F, const Level& C, const double (*P)[kMaxN],
-                       const T* src_b, const T* src_t, T* dst, T* dst_t, const int* done,
+                       const T* src_b, const T* src_t, T* dst, T* dst_t, T* loc, const int* done,
                        cudaStream_t s) {
   const int nf = F.n, nc = C.n;
 #define SEM_PAIR(A, B) \
-  if (nf == A && nc == B) return launch_pair<A, B, T>(prolong, F, C, P, src_b, src_t, dst, dst_t, done, s);
+  if (nf == A && nc == B) return launch_pair<A, B, T>(prolong, F, C, P, src_b, src_t, dst, dst_t, loc, done, s);
   SEM_PAIR(7, 4)
   SEM_PAIR(6, 3)
   SEM_PAIR(5, 3)
@@ -256,10 +265,10 @@ cudaError_t p_transfer(bool prolong, const Level& F, const Level& C, const doubl
 }
 
 template cudaError_t p_transfer<float>(bool, const Level&, const Level&, const double (*)[kMaxN],
-                                       const float*, const float*, float*, float*, const int*,
+                                       const float*, const float*, float*, float*, float*, const int*,
                                        cudaStream_t);
 template cudaError_t p_transfer<double>(bool, const Level&, const Level&, const double (*)[kMaxN],
-                                        const double*, const double*, double*, double*, const int*,
-                                        cudaStream_t);
+                                        const double*, const double*, double*, double*, double*,
+                                        const int*, cudaStream_t);
 
 }  // namespace sem
