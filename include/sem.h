@@ -325,6 +325,19 @@ int sem_adjoint_grad(sem_ctx* ctx, const double* trace_bar, double* g_sigma_l, d
 int sem_apply_dot_static(sem_ctx* ctx, double alpha, double beta, const double* u, double* y,
                          double* dot, void* stream);
 
+/* Fault injection for the SEM_DEBUG build (paper_2205_05136_gb300.build with
+ * debug=True: -DSEM_DEBUG).  That build checks every node index the apply
+ * and transfer kernels read from the element-to-DOF map (or compute from the
+ * node lattice) against [0, ndofs); an index outside is not used (node 0 is
+ * read or written instead), the first one is recorded in a device word, and
+ * sem_apply, sem_cg_solve, sem_step and sem_vcycle then synchronise their
+ * stream and return SEM_ERR_ARG naming it.  This entry point overwrites entry
+ * `entry` (element e, local node a at e (p+1)^3 + a) of the context's fine
+ * level map with `value` and returns the old value in *previous (may be
+ * NULL), so a test can plant a bad index.  The normal build returns
+ * SEM_ERR_UNSUPPORTED.  Synchronous. */
+int sem_debug_set_map_entry(sem_ctx* ctx, int64_t entry, int value, int* previous);
+
 /* Enable (1) or disable (0) CUDA-event timing of the operator-apply kernels
  * inside sem_step / sem_cg_solve (reported in sem_stats). */
 int sem_set_timing(sem_ctx* ctx, int enable);

@@ -11,7 +11,8 @@ import os
 import torch
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libsem.so")
+# SEM_LIBRARY selects another build of the library (the SEM_DEBUG one, for instance)
+LIB_PATH = os.environ.get("SEM_LIBRARY") or os.path.join(HERE, "libsem.so")
 
 SEM_OK = 0
 SEM_ERR_ARG = -1
@@ -50,6 +51,7 @@ EXPORTS = [
     "sem_state_track_activation", "sem_state_get_activation",
     "sem_set_timing", "sem_apply_dot_static", "sem_set_gmg", "sem_vcycle", "sem_gmg_info",
     "sem_forward_record", "sem_adjoint_grad", "sem_set_operator_precision", "sem_set_deterministic",
+    "sem_debug_set_map_entry",
 ]
 
 
@@ -117,6 +119,7 @@ def lib():
             "sem_set_gmg": (_I, [_P, _I, _I, _I, _I]),
             "sem_set_operator_precision": (_I, [_P, _I]),
             "sem_set_deterministic": (_I, [_P, _I]),
+            "sem_debug_set_map_entry": (_I, [_P, _I64, _I, ctypes.POINTER(_I)]),
             "sem_forward_record": (_I, [_P, _P, _D, _I, _I, _P, _I, _P, _D, _D, _I, _I,
                                         ctypes.POINTER(sem_stats), _P]),
             "sem_adjoint_grad": (_I, [_P, _P, _P, _P, _P, _D, _D, _I, _I, ctypes.POINTER(sem_stats), _P]),
@@ -337,6 +340,13 @@ def sem_apply_dot_static(ctx, alpha, beta, u, y, dot, stream=None):
                                              _dev(y, torch.float64, n, "y"),
                                              _dev(dot, torch.float64, 1, "dot"),
                                              _stream(stream)), ctx)
+
+
+def sem_debug_set_map_entry(ctx, entry: int, value: int) -> int:
+    """Plants `value` at map entry `entry` (SEM_DEBUG build only); returns the old value."""
+    old = _I()
+    _check(lib().sem_debug_set_map_entry(ctx, int(entry), int(value), ctypes.byref(old)), ctx)
+    return old.value
 
 
 def sem_set_deterministic(ctx, enable: bool):

@@ -74,6 +74,7 @@ bool is_host_ptr(const void* p) {
 void free_ctx(sem_ctx* ctx) {
   gmg_free(ctx);
   tape_free(ctx);
+  cudaFree(ctx->L.dbg);  // shared with the multigrid levels, freed once here
   level_free(ctx->L);
   cudaFree(ctx->sigma_l);
   cudaFree(ctx->sigma_t);
@@ -126,6 +127,10 @@ int build_level(sem_ctx* ctx, int nx, int ny, int nz, const double* vertices, in
   SEM_CK(cudaGetLastError());
   SEM_CK(cudaMalloc(&ctx->d_flag, sizeof(int)));
   SEM_CK(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), s));
+#ifdef SEM_DEBUG
+  SEM_CK(cudaMalloc(&L.dbg, sizeof(unsigned long long)));
+  SEM_CK(cudaMemsetAsync(L.dbg, 0, sizeof(unsigned long long), s));
+#endif
   SEM_CK(setup_geometry(L, ctx->sigma_l, ctx->sigma_t, ctx->theta, ctx->d_flag, s));
   int bad = 0;
   SEM_CK(cudaMemcpyAsync(&bad, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -141,7 +146,36 @@ int build_level(sem_ctx* ctx, int nx, int ny, int nz, const double* vertices, in
 
 extern "C" {
 
-const char* sem_version(void) { return "libsem 0.1 (sm_103a)"; }
+// SEM_DEBUG build: after a call, the first out-of-range node index the kernels
+// met (recorded instead of accessed) becomes SEM_ERR_ARG; the word is cleared.
+// The normal build returns rc unchanged and does not synchronise.
+int debug_check(sem_ctx* ctx, int rc, cudaStream_t s) {
+#ifdef SEM_DEBUG
+  if (ctx->L.dbg == nullptr) return rc;
+  unsigned long long w = 0;
+  if (cudaStreamSynchronize(s) != cudaSuccess ||
+      cudaMemcpy(&w, ctx->L.dbg, sizeof(w), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return cuda_fail(ctx, cudaGetLastError(), "SEM_DEBUG index-error word");
+  if (w == 0) return rc;
+  cudaMemset(ctx->L.dbg, 0, sizeof(w));
+  static const char* kinds[] = {"?", "gather", "scatter", "node line", "transfer"};
+  const unsigned kind = (unsigned)(w >> 56);
+  const int idx = (int)(uint32_t)(w & 0xffffffffull);
+  return fail(ctx, SEM_ERR_ARG, std::string("SEM_DEBUG: ") + kinds[kind < 5 ? kind : 0] +
+                                    " node index " + std::to_string(idx) + " outside [0, " +
+                                    std::to_string(ctx->L.ndofs) + ") (access skipped)");
+#else
+  (void)ctx;
+  (void)s;
+  return rc;
+#endif
+}
+
+#ifdef SEM_DEBUG
+const char* sem_version(void) { return "libsem 0.2 (sm_103a, SEM_DEBUG index checks)"; }
+#else
+const char* sem_version(void) { return "libsem 0.2 (sm_103a)"; }
+#endif
 
 const char* sem_last_error(const sem_ctx* ctx) {
   if (ctx == nullptr) return g_create_err.c_str();
@@ -258,20 +292,27 @@ int sem_apply(sem_ctx* ctx, double alpha, double beta, const void* u, void* y, i
   if (u == y) return fail(ctx, SEM_ERR_ARG, "u and y must not overlap");
   if (!std::isfinite(alpha) || !std::isfinite(beta)) return fail(ctx, SEM_ERR_ARG, "alpha and beta must be finite");
   cudaStream_t s = as_stream(stream);
+  int rc;
   switch (precision) {
     case SEM_PREC_FP64:
-      return apply_fp64(ctx, alpha, beta, static_cast<const double*>(u), static_cast<double*>(y), s);
+      rc = apply_fp64(ctx, alpha, beta, static_cast<const double*>(u), static_cast<double*>(y), s);
+      break;
     case SEM_PREC_DF64:
-      return apply_df64(ctx, alpha, beta, static_cast<const double*>(u), static_cast<double*>(y), s);
+      rc = apply_df64(ctx, alpha, beta, static_cast<const double*>(u), static_cast<double*>(y), s);
+      break;
     case SEM_PREC_FP32:
-      return apply_fp32(ctx, alpha, beta, static_cast<const float*>(u), static_cast<float*>(y), false, s);
+      rc = apply_fp32(ctx, alpha, beta, static_cast<const float*>(u), static_cast<float*>(y), false, s);
+      break;
     case SEM_PREC_FP32_BF16:
-      return apply_fp32(ctx, alpha, beta, static_cast<const float*>(u), static_cast<float*>(y), true, s);
+      rc = apply_fp32(ctx, alpha, beta, static_cast<const float*>(u), static_cast<float*>(y), true, s);
+      break;
     case SEM_PREC_BF16_TC:
-      return apply_tc(ctx, alpha, beta, static_cast<const float*>(u), static_cast<float*>(y), s);
+      rc = apply_tc(ctx, alpha, beta, static_cast<const float*>(u), static_cast<float*>(y), s);
+      break;
     default:
       return fail(ctx, SEM_ERR_ARG, "unknown precision");
   }
+  return debug_check(ctx, rc, s);
 }
 
 int sem_set_operator_precision(sem_ctx* ctx, int precision) {
@@ -323,8 +364,9 @@ int sem_cg_solve(sem_ctx* ctx, double alpha, const double* b, double* x, double 
   if (b == x) return fail(ctx, SEM_ERR_ARG, "b and x must not overlap");
   if (maxit < 0 || !(rtol >= 0.0) || !(atol >= 0.0) || !std::isfinite(alpha))
     return fail(ctx, SEM_ERR_ARG, "bad solver parameters");
-  return cg_solve(ctx, alpha, b, x, rtol, atol, maxit, precond, iters, final_res, nullptr,
-                  as_stream(stream));
+  const int rc = cg_solve(ctx, alpha, b, x, rtol, atol, maxit, precond, iters, final_res, nullptr,
+                          as_stream(stream));
+  return debug_check(ctx, rc, as_stream(stream));
 }
 
 int sem_set_ionic(sem_ctx* ctx, const sem_ionic_params* prm) {
@@ -503,7 +545,7 @@ int sem_step(sem_ctx* ctx, sem_state* st, double dt, int nsteps, double rtol, do
   sp->smoother_apply_ms = ctx->timing.smoother_ms - sm0;
   sp->n_smoother_apply = ctx->timing.smoother_count - sc0;
   sp->kernel_launches = ctx->launches - l0;
-  return rc;
+  return debug_check(ctx, rc, as_stream(stream));
 }
 
 int sem_step_host(sem_ctx* ctx, double* u, double* u_prev, double* h, double* h_prev, int64_t n,
@@ -627,7 +669,28 @@ int sem_vcycle(sem_ctx* ctx, double alpha, const double* r, double* z, void* str
   CK_DEV(r, "r");
   CK_DEV(z, "z");
   if (!(alpha >= 0.0) || !std::isfinite(alpha)) return fail(ctx, SEM_ERR_ARG, "alpha must be finite and >= 0");
-  return gmg_vcycle(ctx, alpha, r, z, as_stream(stream));
+  return debug_check(ctx, gmg_vcycle(ctx, alpha, r, z, as_stream(stream)), as_stream(stream));
+}
+
+int sem_debug_set_map_entry(sem_ctx* ctx, int64_t entry, int value, int* previous) {
+  CK_CTX(ctx);
+#ifdef SEM_DEBUG
+  const Level& L = ctx->L;
+  if (entry < 0 || entry >= (int64_t)L.nelem * L.n * L.n * L.n)
+    return fail(ctx, SEM_ERR_ARG, "entry outside the element-to-DOF map");
+  DeviceGuard guard(ctx->device);
+  int old = 0;
+  if (cudaMemcpy(&old, L.map + entry, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(L.map + entry, &value, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+    return cuda_fail(ctx, cudaGetLastError(), "map entry");
+  if (previous != nullptr) *previous = old;
+  return SEM_OK;
+#else
+  (void)entry;
+  (void)value;
+  (void)previous;
+  return fail(ctx, SEM_ERR_UNSUPPORTED, "sem_debug_set_map_entry needs the SEM_DEBUG build");
+#endif
 }
 
 int sem_gmg_info(sem_ctx* ctx, double alpha, int max_levels, int* nlevels, int* p, int* dims,

@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(kApplyThreads)
     for (int idx = tid; idx < E * N3; idx += nth) {
       const int s = idx / N3, loc = idx - s * N3, e = e0 + s;
       if (e < a.nelem) {
-        const int gi = __ldg(a.map + (size_t)e * N3 + loc);
+        const int gi = (int)SEM_IDX(__ldg(a.map + (size_t)e * N3 + loc), a.ndofs, a.dbg, kDbgGather);
         if constexpr (std::is_same<T, df>::value) {
           const float2 v = __ldg(reinterpret_cast<const float2*>(a.u2) + gi);
           sA[idx] = df(v.x, v.y);
@@ -353,7 +353,8 @@ __global__ void __launch_bounds__(kApplyThreads)
 #pragma unroll
     for (int it = 0; it < IT; ++it) {
       const int idx = tid + it * NTH;
-      if (IT * NTH == E * N3 || idx < E * N3) sA[idx] = idx < nv ? T(a.u[__ldg(gmap + idx)]) : T(0);
+      if (IT * NTH == E * N3 || idx < E * N3)
+        sA[idx] = idx < nv ? T(a.u[SEM_IDX(__ldg(gmap + idx), a.ndofs, a.dbg, kDbgGather)]) : T(0);
     }
   }
   group_sync();
@@ -436,7 +437,7 @@ __global__ void __launch_bounds__(kApplyThreads)
       for (int idx = tid; idx < E * N3; idx += nth) {
         const int s = idx / N3, loc = idx - s * N3, e = e0 + s;
         if (e < a.nelem) {
-          const int g = __ldg(a.map + (size_t)e * N3 + loc);
+          const int g = (int)SEM_IDX(__ldg(a.map + (size_t)e * N3 + loc), a.ndofs, a.dbg, kDbgScatter);
           T v = sA[idx];
           if (a.scale_out) v *= a.out_scale;
           if (a.yloc != nullptr) store_loc(a.yloc + (size_t)e * N3 + loc, v);
@@ -450,7 +451,7 @@ __global__ void __launch_bounds__(kApplyThreads)
       for (int idx = tid; idx < E * N3; idx += nth) {
         const int s = idx / N3, loc = idx - s * N3, e = e0 + s;
         if (e < a.nelem) {
-          const int g = __ldg(a.map + (size_t)e * N3 + loc);
+          const int g = (int)SEM_IDX(__ldg(a.map + (size_t)e * N3 + loc), a.ndofs, a.dbg, kDbgScatter);
           T v = sA[idx];
           if (a.scale_out) v *= a.out_scale;
           if (a.yloc != nullptr) store_loc(a.yloc + (size_t)e * N3 + loc, v);
@@ -469,7 +470,7 @@ __global__ void __launch_bounds__(kApplyThreads)
         T v = sA[idx];
         if (a.scale_out) v *= a.out_scale;
         if (a.yloc != nullptr) store_loc(a.yloc + (size_t)e0 * N3 + idx, v);
-        else scatter_add(a.y + __ldg(gmap + idx), v);
+        else scatter_add(a.y + SEM_IDX(__ldg(gmap + idx), a.ndofs, a.dbg, kDbgScatter), v);
       }
     }
   }
@@ -543,7 +544,7 @@ __device__ __forceinline__ void pipe_load_map(const ApplyArgs<float, MT>& a, int
 #pragma unroll
   for (int t = 0; t < C::LPL; ++t) {
     const int idx = lane + 32 * t;
-    m[t] = idx < nv ? __ldg(src + idx) : 0;
+    m[t] = idx < nv ? (int)SEM_IDX(__ldg(src + idx), a.ndofs, a.dbg, kDbgGather) : 0;
   }
 }
 
@@ -838,7 +839,10 @@ cudaError_t launch_apply_t(const Level& L, const ApplyArgs<T, MT>& a, bool mass_
   make_eo(tab.Dt, QUAD == SEM_QUAD_LG ? L.tab.Dg : L.tab.D, true);
   make_eo(tab.Bi, L.tab.Bi, false);
   make_eo(tab.Bit, L.tab.Bi, true);
-  const cudaError_t e = launch_apply_kernels<P, QUAD, T, MT>(L, a, tab, mass_only, dot, s);
+  ApplyArgs<T, MT> b = a;
+  b.ndofs = L.ndofs;
+  b.dbg = L.dbg;
+  const cudaError_t e = launch_apply_kernels<P, QUAD, T, MT>(L, b, tab, mass_only, dot, s);
   if (e != cudaSuccess || a.yloc == nullptr) return e;
   return launch_assemble(L, a.yloc, a.y, a.done, s);
 }

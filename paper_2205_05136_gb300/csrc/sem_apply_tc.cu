@@ -118,6 +118,8 @@ struct TcArgs {
   float mass_coef, out_scale;
   int scale_out;
   const int* done;
+  int64_t ndofs;             // SEM_DEBUG index checks
+  unsigned long long* dbg;
 };
 
 namespace {
@@ -269,7 +271,7 @@ __global__ void __launch_bounds__(TcCfg<P>::WARPS * 32, 3) sem_apply_tc_kernel(c
 #pragma unroll
       for (int rr = 0; rr < NP; ++rr) {
         const int k = rr / N, j = rr - k * N;
-        const float* src = a.u + line_base(a, q, P, k, j) + x;
+        const float* src = a.u + SEM_IDX(line_base(a, q, P, k, j) + x, a.ndofs, a.dbg, kDbgLine);
         cp4(dst + o1 + k * NP + j * N, src);
         if (dup) cp4(dst + o2 + k * NP + j * N, src);
       }
@@ -444,7 +446,7 @@ __global__ void __launch_bounds__(TcCfg<P>::WARPS * 32, 3) sem_apply_tc_kernel(c
           const int k = rr / N, j = rr - k * N;
           float v = own ? st[o1 + k * NP + j * N] : 0.f;
           if (face) v += st[o2 + k * NP + j * N];
-          atomicAdd(a.y + line_base(a, q, P, k, j) + x, v * sc);
+          atomicAdd(a.y + SEM_IDX(line_base(a, q, P, k, j) + x, a.ndofs, a.dbg, kDbgLine), v * sc);
         }
       }
     }
@@ -666,6 +668,8 @@ cudaError_t launch_tc_p(const Level& L, const ApplyArgs<float, __nv_bfloat16>& a
   t.out_scale = a.out_scale;
   t.scale_out = a.scale_out;
   t.done = a.done;
+  t.ndofs = L.ndofs;
+  t.dbg = L.dbg;
   const int grid = std::min(resident, (t.nunits + C::WARPS - 1) / C::WARPS);
   if (grid == 0) return cudaSuccess;
   sem_apply_tc_kernel<P><<<grid, C::WARPS * 32, C::cta_bytes, s>>>(t);

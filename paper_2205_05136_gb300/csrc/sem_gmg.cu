@@ -920,6 +920,7 @@ int build(sem_ctx* ctx, cudaStream_t s) {
     g->lv.back().to_next = 0;
     g->lv.push_back(V);
     GMG_CK(level_create(*g->lv.back().L, nx, ny, nz, verts.data(), pc, quad, false, s));
+    g->lv.back().L->dbg = ctx->L.dbg;
     GMG_CK(setup_geometry(*g->lv.back().L, V.sl, V.st, V.th, ctx->d_flag, s));
     GMG_CK(setup_diagonals(*g->lv.back().L, s));
     p = pc;
@@ -950,6 +951,7 @@ int build(sem_ctx* ctx, cudaStream_t s) {
     F.to_next = 1;
     g->lv.push_back(V);
     GMG_CK(level_create(*g->lv.back().L, cx, cy, cz, cv.data(), 1, quad, false, s));
+    g->lv.back().L->dbg = ctx->L.dbg;
     GMG_CK(setup_geometry(*g->lv.back().L, V.sl, V.st, V.th, ctx->d_flag, s));
     GMG_CK(setup_diagonals(*g->lv.back().L, s));
     verts.swap(cv);

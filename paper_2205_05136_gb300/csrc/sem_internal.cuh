@@ -24,6 +24,25 @@
 
 namespace sem {
 
+// Index checks of the SEM_DEBUG build.  dbg_index returns a node index read
+// from an element-to-DOF map (or computed from the lattice) when it lies in
+// [0, n); otherwise it records the first offender in *word as
+// (kind << 56) | (32-bit index) and returns 0, so no access leaves the vector.
+// The host reads and clears the word after the call (debug_check) and returns
+// SEM_ERR_ARG with the index.  In the normal build SEM_IDX is the index itself.
+constexpr unsigned kDbgGather = 1, kDbgScatter = 2, kDbgLine = 3, kDbgTransfer = 4;
+#if defined(SEM_DEBUG) && defined(__CUDACC__)
+__device__ __forceinline__ int64_t dbg_index(int64_t g, int64_t n, unsigned long long* word, unsigned kind) {
+  if (g >= 0 && g < n) return g;
+  if (word != nullptr)
+    atomicCAS(word, 0ull, ((unsigned long long)kind << 56) | (unsigned long long)(uint32_t)g);
+  return 0;
+}
+#define SEM_IDX(g, n, word, kind) dbg_index((g), (n), (word), (kind))
+#else
+#define SEM_IDX(g, n, word, kind) (g)
+#endif
+
 // Storage type of the vectors an operator kernel reads and writes: the df64
 // operator works on FP64 vectors.
 template <typename T> struct VecOf { using type = T; };
@@ -116,6 +135,7 @@ struct Level {
   uint32_t* metric_tc = nullptr;  // bf16 metric in the tensor-core kernel's order (sem_apply_tc.cu)
   uint32_t* tc_frag = nullptr;    // constant MMA fragments of the tensor-core kernel
   bool metric32_valid = false, metric16_valid = false, metric2_valid = false, metric_tc_valid = false;
+  unsigned long long* dbg = nullptr;  // SEM_DEBUG build: the context's index-error word
   double* mdiag = nullptr;
   double* kdiag = nullptr;
   double* xyz = nullptr;
@@ -175,6 +195,9 @@ struct ApplyArgs {
   // atomic adds, and a node kernel then adds each node's contributions to y in a
   // fixed order
   typename VecOf<T>::type* yloc;
+  // set by the launcher: the vectors' length and the SEM_DEBUG index-error word
+  int64_t ndofs;
+  unsigned long long* dbg;
 };
 using ApplyArgs64 = ApplyArgs<double, double>;
 

@@ -77,7 +77,8 @@ template <int NF, int NC, typename T>
 __global__ void __launch_bounds__(kTThreads)
     k_prolong_sf(int nelem, int nx, int ny, int nz, const int* __restrict__ map_c,
                  const int* __restrict__ map_f, const __grid_constant__ PMat<NF, NC, T> pm,
-                 const T* __restrict__ xc, T* __restrict__ xf, T* __restrict__ tf, const int* done) {
+                 const T* __restrict__ xc, T* __restrict__ xf, T* __restrict__ tf, int64_t ndf,
+                 int64_t ndc, unsigned long long* dbg, const int* done) {
   if (done != nullptr && *done) return;
   constexpr int E = TransferCfg<NF>::E;
   constexpr int NF3 = NF * NF * NF, NC3 = NC * NC * NC;
@@ -94,7 +95,8 @@ __global__ void __launch_bounds__(kTThreads)
 #pragma unroll
     for (int it = 0; it < IT; ++it) {
       const int idx = threadIdx.x + it * kTThreads;
-      if (IT * kTThreads == E * NC3 || idx < E * NC3) c0[idx] = idx < nv ? xc[__ldg(gm + idx)] : T(0);
+      if (IT * kTThreads == E * NC3 || idx < E * NC3)
+        c0[idx] = idx < nv ? xc[SEM_IDX(__ldg(gm + idx), ndc, dbg, kDbgTransfer)] : T(0);
     }
   }
   __syncthreads();
@@ -134,7 +136,7 @@ __global__ void __launch_bounds__(kTThreads)
 #pragma unroll
     for (int k = 0; k < NF; ++k) {
       if (k == NF - 1 && (f & 32u)) continue;
-      const int g = __ldg(gm + k * NF * NF);
+      const int64_t g = SEM_IDX(__ldg(gm + k * NF * NF), ndf, dbg, kDbgTransfer);
       xf[g] += out[k];
       tf[g] = T(0);
     }
@@ -146,7 +148,8 @@ __global__ void __launch_bounds__(kTThreads)
     k_restrict_sf(int nelem, int nx, int ny, int nz, const int* __restrict__ map_c,
                   const int* __restrict__ map_f, const __grid_constant__ PMat<NF, NC, T> pm,
                   const T* __restrict__ bf, const T* __restrict__ tf, T* __restrict__ bc,
-                  T* __restrict__ bloc, const int* done) {
+                  T* __restrict__ bloc, int64_t ndf, int64_t ndc, unsigned long long* dbg,
+                  const int* done) {
   if (done != nullptr && *done) return;
   constexpr int E = TransferCfg<NF>::E;
   constexpr int NF3 = NF * NF * NF, NC3 = NC * NC * NC;
@@ -173,7 +176,7 @@ __global__ void __launch_bounds__(kTThreads)
           const T w = (((i == 0 && (f & 1u)) || (i == NF - 1 && (f & 2u))) ? T(0.5) : T(1)) *
                       (((j == 0 && (f & 4u)) || (j == NF - 1 && (f & 8u))) ? T(0.5) : T(1)) *
                       (((k == 0 && (f & 16u)) || (k == NF - 1 && (f & 32u))) ? T(0.5) : T(1));
-          const int g = __ldg(gm + idx);
+          const int64_t g = SEM_IDX(__ldg(gm + idx), ndf, dbg, kDbgTransfer);
           v = (bf[g] - tf[g]) * w;
         }
         f0[idx] = v;
@@ -215,7 +218,7 @@ __global__ void __launch_bounds__(kTThreads)
     }
     const int* gm = map_c + (size_t)(e0 + s) * NC3 + b * NC + a;
 #pragma unroll
-    for (int c = 0; c < NC; ++c) atomicAdd(bc + __ldg(gm + c * NC * NC), out[c]);
+    for (int c = 0; c < NC; ++c) atomicAdd(bc + SEM_IDX(__ldg(gm + c * NC * NC), ndc, dbg, kDbgTransfer), out[c]);
   }
 }
 
@@ -230,10 +233,11 @@ cudaError_t launch_pair(bool prolong, const Level& F, const Level& C, const doub
   const int grid = (F.nelem + E - 1) / E;
   if (prolong)
     k_prolong_sf<NF, NC, T><<<grid, kTThreads, 0, s>>>(F.nelem, F.nx, F.ny, F.nz, C.map, F.map, pm,
-                                                       src_b, dst, dst_t, done);
+                                                       src_b, dst, dst_t, F.ndofs, C.ndofs, F.dbg, done);
   else
     k_restrict_sf<NF, NC, T><<<grid, kTThreads, 0, s>>>(F.nelem, F.nx, F.ny, F.nz, C.map, F.map, pm,
-                                                        src_b, src_t, dst, loc, done);
+                                                        src_b, src_t, dst, loc, F.ndofs, C.ndofs, F.dbg,
+                                                        done);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || prolong || loc == nullptr) return e;
   return launch_assemble(C, loc, dst, done, s);
