@@ -11,17 +11,29 @@ layers of elements along z:
 * after a local operator apply, the two interface planes are summed with the
   neighbours (one exchange per apply, with torch.distributed send / recv);
 * inner products count each node once: a node plane at a cut is owned by the
-  upper rank.
+  upper rank;
+* a neighbour that fails (its process exits, or it stops answering) makes the
+  next exchange or inner product raise PeerLost on the other ranks within the
+  given timeout instead of waiting forever.
 
-On this GB300 pool every process gets one GPU, so the benchmark runs
-independent replicas; the partition is exercised by CPU ranks (gloo).
+Each rank's elements form a slab of their own (sub_slab_vertices), so a rank
+can apply libsem's operator to its layers on its device and exchange the
+interface planes through host memory.  On this GB300 pool every process gets
+one GPU, so the benchmark runs independent replicas; the partition is
+exercised by CPU ranks (gloo), with the oracle's or libsem's local apply.
 """
 from __future__ import annotations
 
 from dataclasses import dataclass
+from datetime import timedelta
 
+import numpy as np
 import torch
 import torch.distributed as dist
+
+
+class PeerLost(RuntimeError):
+    """A neighbouring rank did not take part in an exchange or reduction in time."""
 
 
 def split_layers(nz: int, world: int):
@@ -72,8 +84,10 @@ class SlabPartition:
             m[-self.plane:] = 0.0
         return m
 
-    def exchange(self, y_local: torch.Tensor, group=None) -> torch.Tensor:
-        """Sum the interface planes with the neighbouring ranks (in place)."""
+    def exchange(self, y_local: torch.Tensor, group=None, timeout_s: float | None = None) -> torch.Tensor:
+        """Sum the interface planes with the neighbouring ranks (in place).  With
+        timeout_s, a neighbour that has exited or does not answer within that
+        many seconds raises PeerLost."""
         reqs = []
         bufs = {}
         if self.rank > 0:
@@ -87,15 +101,35 @@ class SlabPartition:
             reqs.append(dist.isend(hi, self.rank + 1, group=group))
             reqs.append(dist.irecv(bufs["hi"], self.rank + 1, group=group))
         for r in reqs:
-            r.wait()
+            try:
+                if timeout_s is None:
+                    r.wait()
+                else:
+                    r.wait(timeout=timedelta(seconds=timeout_s))
+            except RuntimeError as exc:
+                raise PeerLost(f"rank {self.rank}: interface exchange with a neighbour failed: {exc}") from exc
         if "lo" in bufs:
             y_local[:self.plane] += bufs["lo"]
         if "hi" in bufs:
             y_local[-self.plane:] += bufs["hi"]
         return y_local
 
-    def dot(self, a: torch.Tensor, b: torch.Tensor, group=None) -> float:
-        """Global inner product of two local vectors (each node counted once)."""
+    def dot(self, a: torch.Tensor, b: torch.Tensor, group=None, timeout_s: float | None = None) -> float:
+        """Global inner product of two local vectors (each node counted once);
+        PeerLost when a rank does not join the reduction within timeout_s."""
         v = torch.sum(a * b * self.owned_mask().to(a.device)).reshape(1).to(torch.float64)
-        dist.all_reduce(v, group=group)
+        try:
+            work = dist.all_reduce(v, group=group, async_op=True)
+            if timeout_s is None:
+                work.wait()
+            else:
+                work.wait(timeout=timedelta(seconds=timeout_s))
+        except RuntimeError as exc:
+            raise PeerLost(f"rank {self.rank}: inner product reduction failed: {exc}") from exc
         return float(v.item())
+
+    def sub_slab_vertices(self, vertices) -> np.ndarray:
+        """The vertex lattice of this rank's element layers, (nx+1)(ny+1)(ez1-ez0+1)
+        points, x fastest, taken from the global lattice (same point order)."""
+        v = np.asarray(vertices, dtype=np.float64).reshape(self.nz + 1, self.ny + 1, self.nx + 1, 3)
+        return np.ascontiguousarray(v[self.ez0:self.ez1 + 1].reshape(-1, 3))
