@@ -80,24 +80,30 @@ __device__ __forceinline__ df operator-(df a, df b) { return a + df(-b.h, -b.l);
 using dfx::df;
 using dfx::df_pair;
 
-// x as a float pair (h, l), h + l = x to about 2^-48 relative, with integer and
-// FP32 instructions only (FP64 instructions, conversions included, issue at a
-// small fraction of the FP32 rate on GB300): h is x with its mantissa cut to
-// 23 bits, l the remaining 29 bits, m_low 2^(E - 1075), as a float (the one
-// rounding).  Zeros, tiny (|x| < 2^-63), huge and non-finite values take FP64
-// conversions instead.
+// x as a float pair (h, l), h + l = x to about 2^-46 relative, with 32-bit
+// integer and FP32 instructions only (FP64 instructions, conversions included,
+// issue at a small fraction of the FP32 rate on GB300): h is x with its
+// mantissa cut to 23 bits, l the next 23 bits, made exact as a float by the
+// 2^23 exponent trick (the bits under the mantissa of 2^23, minus 2^23) and
+// scaled by 2^(E - 1069) in two exact halves.  |x| below 2^-126 (no normal
+// float) gives a signed zero, |x| from 2^128 on an infinity and a NaN a NaN;
+// for |x| below 2^-80 l loses bits to FP32 underflow (absolute error below
+// 2^-149).
 #ifdef __CUDACC__
 __device__ __forceinline__ df_pair split_pair(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const int E = (int)((b >> 52) & 0x7ffull);
-  if (E < 960 || E > 1150) {
-    const float h = (float)x;
-    return df_pair{h, (float)(x - (double)h)};
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const int E = (int)((hi >> 20) & 0x7ffu);
+  const unsigned sign = hi & 0x80000000u;
+  if (E < 897) return df_pair{__uint_as_float(sign), 0.f};
+  if (E > 1150) {
+    const bool nan = E == 2047 && ((hi & 0xfffffu) | lo) != 0u;
+    return df_pair{__uint_as_float(sign | 0x7f800000u | (nan ? 0x400000u : 0u)), 0.f};
   }
-  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
-  const unsigned hb = sign | ((unsigned)(E - 896) << 23) | (unsigned)((b >> 29) & 0x7fffffull);
-  const float l = (float)(unsigned)(b & ((1ull << 29) - 1)) * __int_as_float((E - 948) << 23);
-  return df_pair{__int_as_float((int)hb), sign ? -l : l};
+  const unsigned hb = sign | ((unsigned)(E - 896) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const float m = __uint_as_float(0x4b000000u | ((lo >> 6) & 0x7fffffu)) - 8388608.f;
+  const int s = E - 1069, s1 = s >> 1, s2 = s - s1;  // both in [-86, 41]
+  const float l = (m * __int_as_float((s1 + 127) << 23)) * __int_as_float((s2 + 127) << 23);
+  return df_pair{__uint_as_float(hb), __uint_as_float(__float_as_uint(l) ^ sign)};
 }
 #endif
 }  // namespace sem

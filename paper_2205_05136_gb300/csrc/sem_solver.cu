@@ -19,6 +19,7 @@
 
 #include "sem_apply_kernel.cuh"
 #include "sem_context.cuh"
+#include "sem_dfmath.cuh"
 
 namespace sem {
 namespace {
@@ -272,6 +273,50 @@ __global__ void __launch_bounds__(kVecThreads)
     hnext[i] = h;
     x0[i] = u0;
     out[i] = mdiag ? mdiag[i] * g : g;
+  }
+}
+
+// The same per-node update in double-float arithmetic on the FP32 pipe (the
+// operator precision SEM_PREC_DF64): inputs split into float pairs and results
+// joined by integer operations, exp and the division from sem_dfmath.cuh.
+// Agrees with the FP64 kernel to about 1e-14 relative.
+struct IonicDfArgs {
+  df inv_amp, v_off, neg_inv_kappa, x_off, i_in, i_out;
+  df c_open, c_close, c_den, inv_dt, inv_2dt, iapp;
+  DfExpConst ex;
+};
+
+__global__ void __launch_bounds__(kVecThreads)
+    k_ionic_rhs_df(int64_t n, const double* __restrict__ un, const double* __restrict__ unm1,
+                   const double* __restrict__ hn, const double* __restrict__ hnm1,
+                   double* __restrict__ hnext, double* __restrict__ x0, double* __restrict__ out,
+                   const double* __restrict__ mdiag, const double* __restrict__ mask,
+                   const IonicDfArgs P, int first) {
+#pragma unroll 1
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double u0d = un[i];
+    const df u0 = dfd(u0d);
+    const df u1 = first ? u0 : dfd(unm1[i]);
+    const df us = first ? u0 : (u0 + u0) - u1;
+    const df v = dfnorm(fma(us, P.inv_amp, P.v_off));
+    df xe = fma(v, P.neg_inv_kappa, P.x_off);
+    if (xe.h > 80.f) xe = df(80.f, 0.f);
+    const df E = dfexp(xe, P.ex);
+    const df ope = df(1.f, 0.f) + E;
+    const df H = first ? dfd(hn[i]) : fma(df(4.f, 0.f), dfd(hn[i]), dfneg(dfd(hnm1[i])));
+    const df num = fma(H, ope, P.c_open * E);
+    const df den = fma(P.c_den, ope, fma(P.c_open, E, P.c_close));
+    const df h = dfdiv(num, den);
+    const df v2 = v * v;
+    const df iion = fma(P.i_in * h, v2 - v * v2, P.i_out * v);
+    df g = first ? fma(u0, P.inv_dt, dfneg(iion))
+                 : fma((u0 + u0 + u0 + u0) - u1, P.inv_2dt, dfneg(iion));
+    // the stimulus mask holds 0 or 1
+    if (mask != nullptr && __double2hiint(mask[i]) != 0) g = g + P.iapp;
+    hnext[i] = df_to_double(h);
+    x0[i] = u0d;
+    out[i] = df_to_double(mdiag ? dfnorm(dfd(mdiag[i]) * g) : dfnorm(g));
   }
 }
 
@@ -601,6 +646,29 @@ int cg_solve(sem_ctx* ctx, double alpha, const double* b, double* x, double rtol
   return rc_out;
 }
 
+// Constants of dfexp: ln2 split for Cody and Waite's reduction (c1, c2 with 16
+// significant bits, so k c1 and k c2 are exact floats for |k| < 128; c3 the
+// rest), and the Taylor coefficients 1 / j! as float pairs.
+DfExpConst dfexp_constants() {
+  DfExpConst K{};
+  const long double ln2 = 0.6931471805599453094172321214581765680755L;
+  const long double c1 = std::ldexp(std::floor(std::ldexp(ln2, 16)), -16);
+  const long double rem = ln2 - c1;
+  const int e = std::ilogb(rem);
+  const long double c2 = std::ldexp(std::floor(std::ldexp(rem, 15 - e)), e - 15);
+  K.inv_ln2 = (float)(1.0L / ln2);
+  K.c1 = (float)c1;
+  K.c2 = (float)c2;
+  K.c3 = (float)(rem - c2);
+  long double f = 1.0L;
+  for (int j = 0; j < 14; ++j) {
+    if (j > 0) f /= (long double)j;
+    K.th[j] = (float)f;
+    K.tl[j] = (float)(f - (long double)K.th[j]);
+  }
+  return K;
+}
+
 int time_steps(sem_ctx* ctx, sem_state* st, double dt, int nsteps, double rtol, double atol,
                int maxit, int precond, sem_stats* stats, cudaStream_t s) {
   int rc = ensure_workspace(ctx);
@@ -619,15 +687,40 @@ int time_steps(sem_ctx* ctx, sem_state* st, double dt, int nsteps, double rtol, 
   ia.inv_tau_close = 1.0 / ip.tau_close;
   ia.i_in = -ip.u_amp / ip.tau_in;
   ia.i_out = ip.u_amp / ip.tau_out;
+  // double-float update with the double-float operator
+  const bool ionic_df = ctx->op_precision == SEM_PREC_DF64;
+  IonicDfArgs idf{};
+  if (ionic_df) {
+    idf.inv_amp = df(ia.inv_amp);
+    idf.v_off = df(ia.v_off);
+    idf.neg_inv_kappa = df(-ia.inv_kappa);
+    idf.x_off = df(ia.x_off);
+    idf.i_in = df(ia.i_in);
+    idf.i_out = df(ia.i_out);
+    idf.ex = dfexp_constants();
+  }
   for (int k = 0; k < nsteps; ++k) {
     const int first = st->n == 0 ? 1 : 0;
     const double t1 = (double)(st->n + 1) * dt;
     const bool on = ctx->stim_mask != nullptr && t1 > ctx->stim_on && t1 <= ctx->stim_off;
     double* out = L.quad == SEM_QUAD_LGL ? w.b : w.g;
-    k_ionic_rhs<<<vg, kVecThreads, 0, s>>>(
-        n, st->U[st->cur], st->U[st->prev], st->H[st->cur], st->H[st->prev], st->H[st->next],
-        st->U[st->next], out, L.quad == SEM_QUAD_LGL ? L.mdiag : nullptr,
-        on ? ctx->stim_mask : nullptr, on ? ctx->stim_amp : 0.0, ia, dt, first);
+    if (ionic_df) {
+      idf.c_open = df((first ? dt : 2.0 * dt) * ia.inv_tau_open);
+      idf.c_close = df((first ? dt : 2.0 * dt) * ia.inv_tau_close);
+      idf.c_den = df(first ? 1.0 : 3.0);
+      idf.inv_dt = df(1.0 / dt);
+      idf.inv_2dt = df(0.5 / dt);
+      idf.iapp = df(on ? ctx->stim_amp : 0.0);
+      k_ionic_rhs_df<<<vg, kVecThreads, 0, s>>>(
+          n, st->U[st->cur], st->U[st->prev], st->H[st->cur], st->H[st->prev], st->H[st->next],
+          st->U[st->next], out, L.quad == SEM_QUAD_LGL ? L.mdiag : nullptr,
+          on ? ctx->stim_mask : nullptr, idf, first);
+    } else {
+      k_ionic_rhs<<<vg, kVecThreads, 0, s>>>(
+          n, st->U[st->cur], st->U[st->prev], st->H[st->cur], st->H[st->prev], st->H[st->next],
+          st->U[st->next], out, L.quad == SEM_QUAD_LGL ? L.mdiag : nullptr,
+          on ? ctx->stim_mask : nullptr, on ? ctx->stim_amp : 0.0, ia, dt, first);
+    }
     SEM_CK(cudaGetLastError());
     ctx->launches += 1;
     if (L.quad == SEM_QUAD_LG) {

@@ -407,3 +407,42 @@ def test_mixed_precision_30m_matches_fp64_multigrid():
     g.close()
     del out
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("first", [True, False])
+def test_double_float_ionic_update_matches_fp64(first):
+    """The ionic update and right-hand side in double-float arithmetic (used with
+    the double-float operator) against the FP64 kernel, from a state whose u
+    spans -90..40 mV (the gate's exponent from -112, where it underflows, to 18)
+    and h spans 0..1: one step (BDF1 from n = 0, else BDF2), Jacobi-CG at rtol
+    1e-13; the new gate agrees to 1e-13 absolute and u to 1e-11 relative, and the
+    gate matches the oracle's closed-form BDF update at every node."""
+    s, tissue, g, o = _small(3, "LGL", perturb=0.1, dims=(6, 4, 3))
+    g.set_ionic()
+    g.set_stimulus("box", (0.0, 0.0, 0.0, 5.0, 3.0, 1.5), 50.0, 0.0, 1.0)
+    n = g.ndofs
+    u = torch.tensor(W.uniform_vector(n, -90.0, 40.0, seed=31), device="cuda")
+    um = torch.tensor(W.uniform_vector(n, -90.0, 40.0, seed=32), device="cuda")
+    h = torch.tensor(W.uniform_vector(n, 0.0, 1.0, seed=33), device="cuda")
+    hm = torch.tensor(W.uniform_vector(n, 0.0, 1.0, seed=34), device="cuda")
+    state = {"u": u, "u_prev": um, "h": h, "h_prev": hm, "n": 0 if first else 5}
+    res = {}
+    for prec in (gb.SEM_PREC_FP64, gb.SEM_PREC_DF64):
+        capi.sem_set_operator_precision(g.ctx, prec)
+        st = g.new_state(-85.0, 1.0)
+        st.restore(state)
+        st.step(0.05, 1, rtol=1e-13, maxit=5000, precond=capi.SEM_PC_JACOBI)
+        u1, h1, _ = st.get()
+        res[prec] = (u1.cpu().numpy(), h1.cpu().numpy())
+        st.close()
+    (u64, h64), (udf, hdf) = res[gb.SEM_PREC_FP64], res[gb.SEM_PREC_DF64]
+    assert np.abs(hdf - h64).max() < 1e-13
+    assert rel(udf, u64) < 1e-11
+    prm = ionic.DEFAULT_PARAMS
+    un, unm1, hn, hnm1 = (state[k].cpu().numpy() for k in ("u", "u_prev", "h", "h_prev"))
+    if first:
+        h_ref = ionic.gate_bdf1(hn, un, 0.05, prm)
+    else:
+        h_ref = ionic.gate_bdf2(hn, hnm1, 2.0 * un - unm1, 0.05, prm)
+    assert np.abs(hdf - h_ref).max() < 1e-13
+    g.close()
