@@ -223,34 +223,47 @@ __device__ __forceinline__ float ldsmetric(const __nv_bfloat16* p) { return __bf
 __device__ __forceinline__ double ldsmetric(const double* p) { return *p; }
 __device__ __forceinline__ df ldsmetric(const df_pair* p) { return df(p->h, p->l); }
 
-// The 7 metric values G00 G01 G02 G11 G12 G22 W of one quadrature point, from
-// global memory (ld_point_g) or shared memory (ld_point_s); cs is the component
-// stride of the layout.  The point-major bf16 layout holds them in 16 bytes,
-// read by one 128-bit load.
+// The 7 metric values G00 G01 G02 G11 G12 G22 W of the quadrature points of
+// one column (i, j) of an element, level by level: MetricColumn(block, c) then
+// point(k, g).  SHARED: the block is in shared memory.  The bf16 column is read
+// once, with 64-bit loads, into registers; the other layouts are read point by
+// point.
 __device__ __forceinline__ float bf16_lo(unsigned w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf16_hi(unsigned w) { return __uint_as_float(w & 0xffff0000u); }
-__device__ __forceinline__ void unpack_point(const uint4 v, float (&g)[kMetricComps]) {
-  g[0] = bf16_lo(v.x); g[1] = bf16_hi(v.x);
-  g[2] = bf16_lo(v.y); g[3] = bf16_hi(v.y);
-  g[4] = bf16_lo(v.z); g[5] = bf16_hi(v.z);
-  g[6] = bf16_lo(v.w);
-}
-template <typename T, typename MT>
-__device__ __forceinline__ void ld_point_g(const MT* p, int cs, T (&g)[kMetricComps]) {
+template <int N, typename MT, bool SHARED>
+struct MetricColumn {
+  using ML = MetricLayout<MT>;
+  const MT* p;
+  __device__ __forceinline__ MetricColumn(const MT* block, int c) : p(block + ML::at(N, c, 0, 0)) {}
+  template <typename T>
+  __device__ __forceinline__ void point(int k, T (&g)[kMetricComps]) const {
 #pragma unroll
-  for (int c = 0; c < kMetricComps; ++c) g[c] = ldmetric(p + c * cs);
-}
-__device__ __forceinline__ void ld_point_g(const __nv_bfloat16* p, int, float (&g)[kMetricComps]) {
-  unpack_point(__ldg(reinterpret_cast<const uint4*>(p)), g);
-}
-template <typename T, typename MT>
-__device__ __forceinline__ void ld_point_s(const MT* p, int cs, T (&g)[kMetricComps]) {
+    for (int comp = 0; comp < kMetricComps; ++comp) {
+      const MT* q = p + ML::at(N, 0, k, comp);
+      g[comp] = SHARED ? ldsmetric(q) : ldmetric(q);
+    }
+  }
+};
+template <int N, bool SHARED>
+struct MetricColumn<N, __nv_bfloat16, SHARED> {
+  using ML = MetricLayout<__nv_bfloat16>;
+  static constexpr int NW = ML::col_width(N) / 4;  // 64-bit words of a column
+  uint2 w[NW];
+  __device__ __forceinline__ MetricColumn(const __nv_bfloat16* block, int c) {
+    const uint2* q = reinterpret_cast<const uint2*>(block + ML::at(N, c, 0, 0));
 #pragma unroll
-  for (int c = 0; c < kMetricComps; ++c) g[c] = ldsmetric(p + c * cs);
-}
-__device__ __forceinline__ void ld_point_s(const __nv_bfloat16* p, int, float (&g)[kMetricComps]) {
-  unpack_point(*reinterpret_cast<const uint4*>(p), g);
-}
+    for (int t = 0; t < NW; ++t) w[t] = SHARED ? q[t] : __ldg(q + t);
+  }
+  // k is a compile-time constant after unrolling: the selects below resolve to registers
+  __device__ __forceinline__ void point(int k, float (&g)[kMetricComps]) const {
+#pragma unroll
+    for (int comp = 0; comp < kMetricComps; ++comp) {
+      const int v = kMetricComps * k + comp, h = v >> 1;
+      const unsigned u = (h & 1) ? w[h >> 1].y : w[h >> 1].x;
+      g[comp] = (v & 1) ? bf16_hi(u) : bf16_lo(u);
+    }
+  }
+};
 
 // Warp-per-element mode (WARP): each warp of the CTA owns one element and
 // synchronises with __syncwarp only, so the warps of an SM run their gather,
@@ -275,7 +288,7 @@ __global__ void __launch_bounds__(kApplyThreads)
   static_assert(!(WARP && DOT), "the fused inner product needs the CTA-wide mode");
   constexpr int N = P + 1, N2 = N * N, N3 = N2 * N;
   using ML = MetricLayout<MT>;
-  constexpr int BLK = ML::block(N), CS = ML::comp_stride(N), PS = ML::kPointStride;
+  constexpr int BLK = ML::block(N);
   constexpr int E = WARP ? WarpCfg<P>::G : ApplyCfg<P>::E;
   constexpr bool STAGE = StageMetric<T>::value && !MASS_ONLY && !WARP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -372,7 +385,7 @@ __global__ void __launch_bounds__(kApplyThreads)
     for (int idx = tid; idx < E * N3; idx += nth) {
       const int s = idx / N3, loc = idx - s * N3, e = e0 + s;
       if (e < a.nelem) {
-        const T W = ldmetric(a.metric + (size_t)e * BLK + 6 * CS + loc * PS);
+        const T W = ldmetric(a.metric + (size_t)e * BLK + ML::at(N, loc % N2, loc / N2, 6));
         sA[idx] = (a.mass_coef * W) * sA[idx];
       }
     }
@@ -394,13 +407,12 @@ __global__ void __launch_bounds__(kApplyThreads)
 #pragma unroll
       for (int k = 0; k < N; ++k) uz[k] = pa[k * N2];
       eo_line<N, true, false>(tab.D, uz, g3);
-      const MT* mp = STAGE ? sM + (size_t)s * BLK + c * PS : a.metric + (size_t)e * BLK + c * PS;
+      const MetricColumn<N, MT, STAGE> mcol(STAGE ? sM + (size_t)s * BLK : a.metric + (size_t)e * BLK, c);
 #pragma unroll
       for (int k = 0; k < N; ++k) {
         const T g1 = pb[k * N2], g2 = pc[k * N2];
         T gm[kMetricComps];
-        if (STAGE) ld_point_s(mp + k * N2 * PS, CS, gm);
-        else ld_point_g(mp + k * N2 * PS, CS, gm);
+        mcol.point(k, gm);
         const T G00 = gm[0], G01 = gm[1], G02 = gm[2], G11 = gm[3], G12 = gm[4], G22 = gm[5], W = gm[6];
         pb[k * N2] = fma(G02, g3[k], fma(G01, g2, G00 * g1));
         pc[k * N2] = fma(G12, g3[k], fma(G11, g2, G01 * g1));
@@ -490,16 +502,19 @@ __global__ void __launch_bounds__(kApplyThreads)
 // copies of unit j+1 in flight while it computes unit j:
 //   - the unit's metric block, contiguous in the element-blocked layout
 //     (16-byte aligned), by 16-byte cp.async;
-//   - the unit's nodal values, gathered by 4-byte cp.async from the map
-//     entries, which were loaded into registers one unit earlier still.
+//   - the unit's nodal values, gathered by plain loads into registers from the
+//     map entries (loaded one unit earlier still) and stored to the stage after
+//     this unit's sweeps.  (4-byte cp.async gathers measured the same time, with
+//     10 % more shared-memory wavefronts: the shared-side write of each gather is split
+//     by the global lines it touches.)
 // Two stage buffers per warp; a stage is complete after cp.async.wait_group
 // and visible to the whole warp after __syncwarp.  The grid is persistent
 // (the CTAs that are resident at once), so the pipeline runs over several units.
 //
 // Every lane owns one line of each sweep (G n^2 <= 32 for p <= 4).  Lanes
 // beyond the unit's G n^2 lines run the same instructions on the line of lane
-// (lane - G n^2): their loads are broadcasts of that lane's, their stores are
-// predicated off, so no sweep needs a divergent branch.
+// (lane - (32 - G n^2)): their loads are broadcasts of that lane's, their
+// stores are predicated off, so no sweep needs a divergent branch.
 template <int P, typename MT>
 struct PipeCfg {
   static constexpr int N = P + 1, N2 = N * N, N3 = N2 * N;
@@ -524,11 +539,6 @@ __device__ __forceinline__ void cp_async_16(void* dst, const void* src) {
                "l"(src)
                : "memory");
 }
-__device__ __forceinline__ void cp_async_4(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
-               "l"(src)
-               : "memory");
-}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int K>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory"); }
@@ -548,37 +558,45 @@ __device__ __forceinline__ void pipe_load_map(const ApplyArgs<float, MT>& a, int
   }
 }
 
-// Issues the copies of one unit into a stage (metric block and gathered u).
+// Issues the cp.async copies of one unit's metric block into a stage.
 template <int P, typename MT>
-__device__ __forceinline__ void pipe_issue(const ApplyArgs<float, MT>& a, int unit, int lane,
-                                           const int (&m)[PipeCfg<P, MT>::LPL], MT* sM, float* sU) {
+__device__ __forceinline__ void pipe_issue_metric(const ApplyArgs<float, MT>& a, int unit, int lane, MT* sM) {
   using C = PipeCfg<P, MT>;
   const int e0 = unit * C::G;
   const char* src = reinterpret_cast<const char*>(a.metric + (size_t)e0 * C::BLK);
   char* dst = reinterpret_cast<char*>(sM);
-  if (e0 + C::G <= a.nelem) {  // full unit: compile-time trip counts
+  if (e0 + C::G <= a.nelem) {
 #pragma unroll
     for (int t = 0; t < (C::CH + 31) / 32; ++t) {
       const int c = lane + 32 * t;
       if (C::CH % 32 == 0 || c < C::CH) cp_async_16(dst + 16 * c, src + 16 * c);
     }
-#pragma unroll
-    for (int t = 0; t < C::LPL; ++t) {
-      const int idx = lane + 32 * t;
-      if (C::UT % 32 == 0 || idx < C::UT) cp_async_4(sU + idx, a.u + m[t]);
-    }
-  } else {  // the mesh's last, partial unit: zeros in the missing elements' tiles
-    const int ne = a.nelem - e0;
-    const int chunks = (int)((size_t)ne * C::BLK * sizeof(MT) / 16);
+  } else {
+    const int chunks = (int)((size_t)(a.nelem - e0) * C::BLK * sizeof(MT) / 16);
     for (int c = lane; c < chunks; c += 32) cp_async_16(dst + 16 * c, src + 16 * c);
+  }
+}
+
+// Gathered nodal values of a unit into registers (node lane + 32 t), zero for
+// the nodes of elements past the mesh; pipe_put_gather stores them to a stage.
+template <int P, typename MT>
+__device__ __forceinline__ void pipe_gather(const ApplyArgs<float, MT>& a, int unit, int lane,
+                                            const int (&m)[PipeCfg<P, MT>::LPL], float (&v)[PipeCfg<P, MT>::LPL]) {
+  using C = PipeCfg<P, MT>;
+  const int nv = min(C::UT, (a.nelem - unit * C::G) * C::N3);
 #pragma unroll
-    for (int t = 0; t < C::LPL; ++t) {
-      const int idx = lane + 32 * t;
-      if (idx < C::UT) {
-        if (idx < ne * C::N3) cp_async_4(sU + idx, a.u + m[t]);
-        else sU[idx] = 0.f;
-      }
-    }
+  for (int t = 0; t < C::LPL; ++t) {
+    const int idx = lane + 32 * t;
+    v[t] = (idx < nv) ? __ldg(a.u + m[t]) : 0.f;
+  }
+}
+template <int P, typename MT>
+__device__ __forceinline__ void pipe_put_gather(int lane, const float (&v)[PipeCfg<P, MT>::LPL], float* sU) {
+  using C = PipeCfg<P, MT>;
+#pragma unroll
+  for (int t = 0; t < C::LPL; ++t) {
+    const int idx = lane + 32 * t;
+    if (C::UT % 32 == 0 || idx < C::UT) sU[idx] = v[t];
   }
 }
 
@@ -606,7 +624,6 @@ __global__ void __launch_bounds__(kApplyThreads, 4)
   using C = PipeCfg<P, MT>;
   using T = float;
   constexpr int N = C::N, N2 = C::N2, N3 = C::N3, G = C::G, LPL = C::LPL, NL = C::NL;
-  constexpr int CS = MetricLayout<MT>::comp_stride(N), PS = MetricLayout<MT>::kPointStride;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (a.done != nullptr && *a.done) return;
@@ -619,24 +636,32 @@ __global__ void __launch_bounds__(kApplyThreads, 4)
   T* sB = sU0 + 2 * C::UTP;
   T* sC = sB + C::UTP;  // followed by the scratch lines of the lanes >= NL
 
-  // line offsets of this lane (of lane - NL for the lanes >= NL): element slot ls, line ll
+  // line offsets of this lane (of lane - (32 - NL) for the lanes >= NL, a lane of
+  // the same half-warp, so that the 64-bit metric loads of the idle lanes are
+  // broadcasts within their phase): element slot ls, line ll
+  static_assert(NL >= 24, "idle lanes must replay a lane of their half-warp");
   const bool act = lane < NL;
-  const int lw = act ? lane : lane - NL;
+  const int lw = act ? lane : lane - (32 - NL);
   const int ls = lw / N2, ll = lw - ls * N2;
   const int ox = ls * N3 + ll * N;                      // x-line (j, k) = ll
   const int oy = ls * N3 + (ll / N) * N2 + (ll % N);    // y-line (i, k): i = ll % N, k = ll / N
   const int oz = ls * N3 + ll;                          // z-line (i, j) = ll
-  const int mo = ls * C::BLK + ll * PS;  // the lane's first metric value in a unit stage
 
   int mc[LPL], mn[LPL], mnn[LPL];  // map entries of units j, j+1, j+2
   pipe_load_map<P>(a, unit, nunits, lane, mc);
-  pipe_issue<P>(a, unit, lane, mc, sM0, sU0);
+  float gv[LPL];  // the next unit's gathered values, in flight during this unit's sweeps
+  pipe_issue_metric<P>(a, unit, lane, sM0);
+  pipe_gather<P>(a, unit, lane, mc, gv);
+  pipe_put_gather<P, MT>(lane, gv, sU0);
   cp_async_commit();
   pipe_load_map<P>(a, unit + tw, nunits, lane, mn);
   int b = 0;
   for (; unit < nunits; unit += tw) {
     const int nxt = unit + tw;
-    if (nxt < nunits) pipe_issue<P>(a, nxt, lane, mn, sM0 + (b ^ 1) * C::MV, sU0 + (b ^ 1) * C::UTP);
+    if (nxt < nunits) {
+      pipe_issue_metric<P>(a, nxt, lane, sM0 + (b ^ 1) * C::MV);
+      pipe_gather<P>(a, nxt, lane, mn, gv);
+    }
     cp_async_commit();  // possibly empty group: keeps "all but the newest group" = stage b
     pipe_load_map<P>(a, nxt + tw, nunits, lane, mnn);
     cp_async_wait<1>();
@@ -666,12 +691,12 @@ __global__ void __launch_bounds__(kApplyThreads, 4)
 #pragma unroll
       for (int k = 0; k < N; ++k) uz[k] = pa[k * N2];
       eo_line<N, true, false>(tab.D, uz, g3);
-      const MT* mp = sM + mo;
+      const MetricColumn<N, MT, true> mcol(sM + ls * C::BLK, ll);
 #pragma unroll
       for (int k = 0; k < N; ++k) {
         const T g1 = pb[k * N2], g2 = pc[k * N2];
         T gm[kMetricComps];
-        ld_point_s(mp + k * N2 * PS, CS, gm);
+        mcol.point(k, gm);
         const T G00 = gm[0], G01 = gm[1], G02 = gm[2], G11 = gm[3], G12 = gm[4], G22 = gm[5], W = gm[6];
         const T q1 = fma(G02, g3[k], fma(G01, g2, G00 * g1));
         const T q2 = fma(G12, g3[k], fma(G11, g2, G01 * g1));
@@ -721,6 +746,7 @@ __global__ void __launch_bounds__(kApplyThreads, 4)
         if (idx < C::UT && e0 + idx / N3 < a.nelem) atomicAdd(a.y + mc[t], sA[idx] * sc);
       }
     }
+    if (nxt < nunits) pipe_put_gather<P, MT>(lane, gv, sU0 + (b ^ 1) * C::UTP);
     __syncwarp();  // stage b is refilled by the next iteration's issue
 #pragma unroll
     for (int t = 0; t < LPL; ++t) {

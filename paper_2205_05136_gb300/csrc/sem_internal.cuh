@@ -6,8 +6,9 @@
 //            n3p = n^3 rounded up to a multiple of 8 (16-byte aligned blocks),
 //            G = w |det J| J^{-1} D J^{-T}, W = w |det J|  (element-blocked SoA)
 //   metric32 float [nelem][7][n3p] copy of the same array (mixed-precision applies)
-//   metric16 bf16  [nelem][n^3][8] point-major copy: the 7 values of a quadrature
-//            point (and one zero) in 16 bytes, read by one 128-bit load
+//   metric16 bf16  [nelem][n^2][CW] column-major copy: the 7 n values of the
+//            quadrature points of column (i, j) in CW = 7 n rounded up to 4
+//            (p = 4: 36 values, 72 bytes), read by 64-bit loads
 //   mdiag    double [ndofs]  diagonal of the assembled mass matrix
 //   kdiag    double [ndofs]  diagonal of the assembled stiffness matrix
 //   xyz      double [3][ndofs] node coordinates
@@ -146,22 +147,29 @@ inline size_t metric_count(const Level& L) {
   return (size_t)L.nelem * kMetricComps * padded_n3(L.n);
 }
 
-// Index of component c of quadrature point q inside one element's metric block:
-// component-major [7][n3p] for double, float and float pairs; point-major
-// [n^3][8] for bf16 (the storage precision whose 7 values fit one 16-byte load).
+// Offset of component `comp` of the quadrature point on column c = i + n j at
+// level k inside one element's metric block.
+//   double, float, float pairs: component-major [7][padded n^3], point c + n^2 k;
+//   bf16: column-major, the 7 values of level k at 7 k .. 7 k + 6 of the
+//   column's CW = 7 n (rounded up to a multiple of 4) values, so that a lane
+//   reads its whole column with CW / 4 aligned 64-bit loads and no point is
+//   padded; the block is rounded up to 16 bytes (cp.async / TMA granularity).
 template <typename MT>
 struct MetricLayout {
-  static constexpr bool kPointMajor = false;
+  static constexpr bool kColumnMajor = false;
   __host__ __device__ static constexpr int block(int n) { return kMetricComps * padded_n3(n); }
-  __host__ __device__ static constexpr int comp_stride(int n) { return padded_n3(n); }
-  static constexpr int kPointStride = 1;
+  __host__ __device__ static constexpr int at(int n, int c, int k, int comp) {
+    return comp * padded_n3(n) + c + k * n * n;
+  }
 };
 template <>
 struct MetricLayout<__nv_bfloat16> {
-  static constexpr bool kPointMajor = true;
-  __host__ __device__ static constexpr int block(int n) { return 8 * n * n * n; }
-  __host__ __device__ static constexpr int comp_stride(int) { return 1; }
-  static constexpr int kPointStride = 8;
+  static constexpr bool kColumnMajor = true;
+  __host__ __device__ static constexpr int col_width(int n) { return (kMetricComps * n + 3) / 4 * 4; }
+  __host__ __device__ static constexpr int block(int n) { return (n * n * col_width(n) + 7) / 8 * 8; }
+  __host__ __device__ static constexpr int at(int n, int c, int k, int comp) {
+    return c * col_width(n) + kMetricComps * k + comp;
+  }
 };
 
 // Number of values of the bf16 metric of a level.

@@ -243,13 +243,17 @@ __global__ void k_convert<float>(int64_t n, const double* __restrict__ in, float
 }
 
 // bf16 copy in the point-major layout: out[e][q][c] = in[e][c][q] (c < 7), out[e][q][7] = 0.
-__global__ void k_convert_points_bf16(int64_t n, int n3, int n3p, const double* __restrict__ in,
-                                      __nv_bfloat16* __restrict__ out) {
+// FP64 component-major metric -> the column-major bf16 layout (MetricLayout).
+__global__ void k_convert_columns_bf16(int64_t n, int np, const double* __restrict__ in,
+                                       __nv_bfloat16* __restrict__ out) {
+  using ML = MetricLayout<__nv_bfloat16>;
+  const int n2 = np * np, cw = ML::col_width(np), blk = ML::block(np), n3p = padded_n3(np);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t e = i / (8 * n3);
-    const int r = (int)(i - e * 8 * n3), q = r >> 3, c = r & 7;
-    const double v = c < kMetricComps ? in[(e * kMetricComps + c) * n3p + q] : 0.0;
+    const int64_t e = i / blk;
+    const int r = (int)(i - e * blk), c = r / cw, s = r - c * cw, k = s / kMetricComps,
+              comp = s - k * kMetricComps;
+    const double v = (c < n2 && k < np) ? in[(e * kMetricComps + comp) * n3p + c + (int64_t)n2 * k] : 0.0;
     out[i] = __float2bfloat16_rn(__double2float_rn(v));
   }
 }
@@ -366,8 +370,7 @@ cudaError_t setup_metric_lowp(Level& L, bool bf16, cudaStream_t s) {
   if (bf16) {
     const int64_t count16 = (int64_t)metric16_count(L);
     const int blocks16 = (int)std::min<int64_t>((count16 + threads - 1) / threads, 152 * 16);
-    k_convert_points_bf16<<<blocks16, threads, 0, s>>>(count16, L.n * L.n * L.n, padded_n3(L.n),
-                                                       L.metric, L.metric16);
+    k_convert_columns_bf16<<<blocks16, threads, 0, s>>>(count16, L.n, L.metric, L.metric16);
     L.metric16_valid = true;
   } else {
     k_convert<float><<<blocks, threads, 0, s>>>(count, L.metric, L.metric32);
