@@ -271,10 +271,10 @@ int sem_step_host(sem_ctx* ctx, double* u, double* u_prev, double* h, double* h_
  * The step is the one sem_step takes (Section 3, Algorithm 1).  A caller that
  * rotates three host arrays per field (u_prev <- u <- u_next) moves 4 vectors
  * to and 2 from the device per step, against 4 and 4 with sem_step_host.
- * With page-locked arrays the ionic update reads the inputs and writes h^{n+1}
- * over the host link while it computes, and only u^{n+1} is copied back;
- * pageable arrays are staged by copies.  The host must not change the arrays
- * during the call.  SEM_ERR_ARG when an array is device memory or when u_next
+ * With page-locked inputs the ionic update reads them over the host link
+ * while it computes; pageable inputs are staged by copies.  h^{n+1} is copied
+ * back on a second stream of the context while the linear solve runs, u^{n+1}
+ * after the solve.  The host must not change the arrays during the call.  SEM_ERR_ARG when an array is device memory or when u_next
  * or h_next overlaps another array.  Synchronises stream. */
 int sem_step_host_out(sem_ctx* ctx, const double* u, const double* u_prev, const double* h,
                       const double* h_prev, double* u_next, double* h_next, int64_t n, double dt,

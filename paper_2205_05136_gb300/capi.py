@@ -301,7 +301,7 @@ def sem_step_host(ctx, u, u_prev, h, h_prev, n, dt, rtol, atol, maxit, precond=S
 def sem_step_host_out(ctx, u, u_prev, h, h_prev, u_next, h_next, n, dt, rtol, atol, maxit,
                       precond=SEM_PC_JACOBI, stream=None):
     """Inputs u, u_prev, h, h_prev and outputs u_next, h_next: contiguous float64
-    CPU tensors (page-locked ones are read and written by the device in place)."""
+    CPU tensors (page-locked inputs are read by the device in place)."""
     nd = sem_num_dofs(ctx)
     for t, name in ((u, "u"), (u_prev, "u_prev"), (h, "h"), (h_prev, "h_prev"),
                     (u_next, "u_next"), (h_next, "h_next")):

@@ -1,6 +1,7 @@
 // C ABI of libsem (declared in include/sem.h): argument checking, context and
 // state management, and dispatch to the setup, apply and solver layers.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -13,7 +14,12 @@ using namespace sem;
 namespace sem {
 int apply_fp32(sem_ctx* ctx, double alpha, double beta, const float* u, float* y, bool bf16,
                cudaStream_t s);
+
+bool pdl_enabled() {
+  static const bool on = std::getenv("SEM_NO_PDL") == nullptr;
+  return on;
 }
+}  // namespace sem
 
 namespace {
 
@@ -236,6 +242,10 @@ int sem_destroy(sem_ctx* ctx) {
   cudaDeviceSynchronize();
   if (ctx->host_state) sem_state_destroy(ctx->host_state);
   ctx->host_state = nullptr;
+  auto& hc = ctx->host_copies;
+  for (cudaEvent_t e : {hc.ev_ionic, hc.ev_h})
+    if (e) cudaEventDestroy(e);
+  if (hc.side) cudaStreamDestroy(hc.side);
   if (ctx->timing.start) cudaEventDestroy(ctx->timing.start);
   if (ctx->timing.stop) cudaEventDestroy(ctx->timing.stop);
   free_ctx(ctx);
@@ -617,9 +627,17 @@ int sem_step_host_out(sem_ctx* ctx, const double* u, const double* u_prev, const
   }
   sem_state* st = ctx->host_state;
   cudaStream_t s = as_stream(stream);
-  // Page-locked inputs are read in place by the ionic update (over the host
-  // link, while it computes) and h^{n+1} is written straight to h_next; pageable
-  // arrays are staged through the state's device buffers.
+  // Page-locked inputs are read in place by the ionic update, over the host
+  // link while it computes (measured faster than copy-engine transfers of the
+  // four inputs on two streams); pageable arrays are staged through the
+  // state's device buffers.  h^{n+1} goes to the host on a second stream as
+  // soon as the ionic update has written it (time_steps issues that copy), so
+  // that it overlaps the linear solve; u^{n+1} follows the solve.
+  auto& hc = ctx->host_copies;
+  if (hc.side == nullptr) {
+    SEM_CK(cudaStreamCreateWithFlags(&hc.side, cudaStreamNonBlocking));
+    for (cudaEvent_t* e : {&hc.ev_ionic, &hc.ev_h}) SEM_CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  }
   sem_state view = *st;
   view.cur = 0; view.prev = 1; view.next = 2; view.n = n;
   const double* in[4] = {u, u_prev, h, h_prev};
@@ -633,13 +651,17 @@ int sem_step_host_out(sem_ctx* ctx, const double* u, const double* u_prev, const
     }
   }
   view.U[0] = use[0]; view.U[1] = use[1]; view.H[0] = use[2]; view.H[1] = use[3];
-  double* h_out = mapped_ptr(h_next);
-  view.H[2] = h_out ? h_out : st->H[2];
   view.U[2] = st->U[2];
-  int rc = sem_step(ctx, &view, dt, 1, rtol, atol, maxit, precond, stats, stream);
-  if (rc != SEM_OK) return rc;
+  view.H[2] = st->H[2];
+  hc.h_dst = h_next;
+  const int rc = sem_step(ctx, &view, dt, 1, rtol, atol, maxit, precond, stats, stream);
+  hc.h_dst = nullptr;
+  if (rc != SEM_OK) {
+    cudaStreamSynchronize(hc.side);
+    return rc;
+  }
   SEM_CK(cudaMemcpyAsync(u_next, st->U[2], bytes, cudaMemcpyDeviceToHost, s));
-  if (h_out == nullptr) SEM_CK(cudaMemcpyAsync(h_next, st->H[2], bytes, cudaMemcpyDeviceToHost, s));
+  SEM_CK(cudaStreamWaitEvent(s, hc.ev_h, 0));
   SEM_CK(cudaStreamSynchronize(s));
   return SEM_OK;
 }

@@ -14,6 +14,7 @@ cudaError_t launch_apply_fp64(const Level& L, const ApplyArgs64& a, bool mass_on
 __global__ void __launch_bounds__(kApplyThreads)
     k_apply_dot_finish(const double* __restrict__ partials, int n, CgScalars* cg, double* out,
                        const int* done) {
+  pdl_entry();
   __shared__ double red[32];
   if (done != nullptr && *done) return;
   double v = 0.0;
@@ -31,7 +32,7 @@ __global__ void __launch_bounds__(kApplyThreads)
 
 cudaError_t launch_apply_dot_finish(const double* partials, int n, CgScalars* cg, double* out,
                                     const int* done, cudaStream_t s) {
-  k_apply_dot_finish<<<1, kApplyThreads, 0, s>>>(partials, n, cg, out, done);
+  launch_k(k_apply_dot_finish, 1, kApplyThreads, 0, s, partials, n, cg, out, done);
   return cudaGetLastError();
 }
 
@@ -42,6 +43,7 @@ template <typename V>
 __global__ void __launch_bounds__(256)
     k_assemble(int nx, int ny, int nz, int p, const V* __restrict__ yloc, V* __restrict__ y,
                const int* done) {
+  pdl_entry();
   if (done != nullptr && *done) return;
   const int n = p + 1, n2 = n * n, n3 = n2 * n;
   const int64_t NX = (int64_t)p * nx + 1, NY = (int64_t)p * ny + 1, nd = NX * NY * ((int64_t)p * nz + 1);
@@ -71,7 +73,7 @@ template <typename V>
 cudaError_t assemble_t(const Level& L, const V* yloc, V* y, const int* done, cudaStream_t s) {
   const int64_t want = (L.ndofs + 255) / 256;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, 152 * 16));
-  k_assemble<V><<<grid, 256, 0, s>>>(L.nx, L.ny, L.nz, L.p, yloc, y, done);
+  launch_k(k_assemble<V>, grid, 256, 0, s, L.nx, L.ny, L.nz, L.p, yloc, y, done);
   return cudaGetLastError();
 }
 

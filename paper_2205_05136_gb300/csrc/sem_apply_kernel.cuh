@@ -285,6 +285,7 @@ __host__ __device__ constexpr size_t apply_warp_tile_bytes() {
 template <int P, int QUAD, typename T, typename MT, bool DOT, bool MASS_ONLY, bool WARP = false>
 __global__ void __launch_bounds__(kApplyThreads)
     sem_apply_kernel(const ApplyArgs<T, MT> a, const __grid_constant__ KTab<P + 1, T> tab) {
+  pdl_entry();
   static_assert(!(WARP && DOT), "the fused inner product needs the CTA-wide mode");
   constexpr int N = P + 1, N2 = N * N, N3 = N2 * N;
   using ML = MetricLayout<MT>;
@@ -621,6 +622,7 @@ template <int P, int QUAD, typename MT>
 __global__ void __launch_bounds__(kApplyThreads, 4)
     sem_apply_pipe_kernel(const ApplyArgs<float, MT> a, const __grid_constant__ KTab<P + 1, float> tab,
                           int nunits) {
+  pdl_entry();
   using C = PipeCfg<P, MT>;
   using T = float;
   constexpr int N = C::N, N2 = C::N2, N3 = C::N3, G = C::G, LPL = C::LPL, NL = C::NL;
@@ -791,7 +793,7 @@ cudaError_t launch_apply_pipe(const Level& L, const ApplyArgs<float, MT>& a, con
   const int nunits = (L.nelem + C::G - 1) / C::G;
   const int grid = std::min(resident, (nunits + kWarpsPerCta - 1) / kWarpsPerCta);
   if (grid == 0) return cudaSuccess;
-  sem_apply_pipe_kernel<P, QUAD, MT><<<grid, kApplyThreads, C::cta_bytes, s>>>(a, tab, nunits);
+  launch_k(sem_apply_pipe_kernel<P, QUAD, MT>, grid, kApplyThreads, C::cta_bytes, s, a, tab, nunits);
   return cudaGetLastError();
 }
 
@@ -835,20 +837,20 @@ cudaError_t launch_apply_kernels(const Level& L, const ApplyArgs<T, MT>& a, cons
     const int wgrid = (L.nelem + per_cta - 1) / per_cta;
     constexpr size_t wbytes = apply_warp_tile_bytes<P, T>();
     if (mass_only)
-      sem_apply_kernel<P, QUAD, T, MT, false, true, true><<<wgrid, kApplyThreads, wbytes, s>>>(a, tab);
+      launch_k(sem_apply_kernel<P, QUAD, T, MT, false, true, true>, wgrid, kApplyThreads, wbytes, s, a, tab);
     else
-      sem_apply_kernel<P, QUAD, T, MT, false, false, true><<<wgrid, kApplyThreads, wbytes, s>>>(a, tab);
+      launch_k(sem_apply_kernel<P, QUAD, T, MT, false, false, true>, wgrid, kApplyThreads, wbytes, s, a, tab);
     return cudaGetLastError();
   }
   if (mass_only) {
-    sem_apply_kernel<P, QUAD, T, MT, false, true><<<grid, kApplyThreads, tiles, s>>>(a, tab);
+    launch_k(sem_apply_kernel<P, QUAD, T, MT, false, true>, grid, kApplyThreads, tiles, s, a, tab);
   } else if (dot) {
-    sem_apply_kernel<P, QUAD, T, MT, true, false><<<grid, kApplyThreads, full, s>>>(a, tab);
+    launch_k(sem_apply_kernel<P, QUAD, T, MT, true, false>, grid, kApplyThreads, full, s, a, tab);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_apply_dot_finish(a.dot_partials, grid, a.cg, a.dot_out, a.done, s);
   } else {
-    sem_apply_kernel<P, QUAD, T, MT, false, false><<<grid, kApplyThreads, full, s>>>(a, tab);
+    launch_k(sem_apply_kernel<P, QUAD, T, MT, false, false>, grid, kApplyThreads, full, s, a, tab);
   }
   return cudaGetLastError();
 }

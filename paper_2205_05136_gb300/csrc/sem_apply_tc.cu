@@ -211,6 +211,7 @@ __device__ __forceinline__ int64_t line_base(const TcArgs& a, const UnitPos& q, 
 
 template <int P>
 __global__ void __launch_bounds__(TcCfg<P>::WARPS * 32, 3) sem_apply_tc_kernel(const TcArgs a) {
+  pdl_entry();
   using C = TcCfg<P>;
   constexpr int N = C::N, NP = C::NP, N3 = C::N3, EPT = C::EPT, ROWS = C::ROWS, NG = C::NG;
   constexpr int KS1 = C::KS1, NT1 = C::NT1, NT2 = C::NT2, MTU = C::MTU;
@@ -551,6 +552,7 @@ bool tc_fragments(const Tables1D& tab, std::vector<uint32_t>& f) {
 template <int P>
 __global__ void k_metric_tc(int64_t nwords, int nx, int ny, int upr, const double* __restrict__ metric,
                             uint32_t* __restrict__ out) {
+  pdl_entry();
   using C = TcCfg<P>;
   constexpr int N = C::N, NP = C::NP, N3P = padded_n3(N);
   for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < nwords;
@@ -643,7 +645,7 @@ cudaError_t setup_tc_p(Level& L, cudaStream_t s) {
   const int64_t nw = (int64_t)tc_metric_words_p<P>(L);
   const int threads = 256;
   const int blocks = (int)std::min<int64_t>((nw + threads - 1) / threads, 152 * 16);
-  k_metric_tc<P><<<blocks, threads, 0, s>>>(nw, L.nx, L.ny, units_per_row<P>(L), L.metric, L.metric_tc);
+  launch_k(k_metric_tc<P>, blocks, threads, 0, s, nw, L.nx, L.ny, units_per_row<P>(L), L.metric, L.metric_tc);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // the fragments' host vector must outlive the copy
   return cudaStreamSynchronize(s);
@@ -672,7 +674,7 @@ cudaError_t launch_tc_p(const Level& L, const ApplyArgs<float, __nv_bfloat16>& a
   t.dbg = L.dbg;
   const int grid = std::min(resident, (t.nunits + C::WARPS - 1) / C::WARPS);
   if (grid == 0) return cudaSuccess;
-  sem_apply_tc_kernel<P><<<grid, C::WARPS * 32, C::cta_bytes, s>>>(t);
+  launch_k(sem_apply_tc_kernel<P>, grid, C::WARPS * 32, C::cta_bytes, s, t);
   return cudaGetLastError();
 }
 

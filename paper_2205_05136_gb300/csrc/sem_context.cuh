@@ -65,6 +65,14 @@ struct sem_ctx {
   // device address of sem_apply_dot_static's static scratch array in the CUDA
   // context this sem_ctx was created in (looked up on that entry point's first call)
   double* static_scratch = nullptr;
+  // sem_step_host_out: a second stream for the copy of h^{n+1} to the host,
+  // which the ionic update writes first thing in the step and which then
+  // overlaps the linear solve (time_steps issues it when h_dst is set)
+  struct HostCopies {
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_ionic = nullptr, ev_h = nullptr;
+    double* h_dst = nullptr;
+  } host_copies;
   std::string err;
 };
 

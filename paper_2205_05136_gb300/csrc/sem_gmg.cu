@@ -135,6 +135,7 @@ __host__ __device__ constexpr int k16() { return 16 / (int)sizeof(T); }
 
 template <typename T>
 __global__ void k_zero(int64_t n, T* x, const int* done) {
+  pdl_entry();
   if (skip(done)) return;
   constexpr int K = k16<T>();
   const int64_t nc = n / K;
@@ -145,6 +146,7 @@ __global__ void k_zero(int64_t n, T* x, const int* done) {
 template <typename T>
 __global__ void k_level_inv_diag(int64_t n, double alpha, const double* m, const double* k,
                                  T* inv, double* inv64) {
+  pdl_entry();
   GRID_LOOP(i, n) {
     const double v = 1.0 / fma(alpha, m[i], k[i]);
     inv[i] = (T)v;
@@ -157,6 +159,7 @@ template <typename T>
 __global__ void k_cheb_zero_start(int64_t n, const T* __restrict__ b, const T* __restrict__ invd,
                                   T* __restrict__ x, T* __restrict__ d, T* __restrict__ t,
                                   T inv_theta, const int* done) {
+  pdl_entry();
   if (skip(done)) return;
   constexpr int K = k16<T>();
   using V = Pk<T, K>;
@@ -190,6 +193,7 @@ template <typename T>
 __global__ void k_cheb_step(int64_t n, const T* __restrict__ b, const T* __restrict__ invd,
                             T* __restrict__ x, T* __restrict__ d, T* __restrict__ t, T c1, T c2,
                             int first, const int* done) {
+  pdl_entry();
   if (skip(done)) return;
   constexpr int K = k16<T>();
   using V = Pk<T, K>;
@@ -238,6 +242,7 @@ template <typename T>
 __global__ void k_prolong_h(int nfx, int nfy, int nfz, int ncx, int ncy, int ncz,
                             const T* __restrict__ xc, T* __restrict__ xf, T* __restrict__ tf,
                             const int* done) {
+  pdl_entry();
   if (skip(done)) return;
   const int64_t NX = nfx + 1, NY = nfy + 1, n = NX * NY * (nfz + 1);
   const int64_t CX = ncx + 1, CY = ncy + 1;
@@ -264,6 +269,7 @@ template <typename T>
 __global__ void k_restrict_h(int nfx, int nfy, int nfz, int ncx, int ncy, int ncz,
                              const T* __restrict__ bf, const T* __restrict__ tf,
                              T* __restrict__ bc, const int* done) {
+  pdl_entry();
   if (skip(done)) return;
   const int64_t NX = nfx + 1, NY = nfy + 1, n = NX * NY * (nfz + 1);
   const int64_t CX = ncx + 1, CY = ncy + 1;
@@ -291,6 +297,7 @@ template <typename T>
 __global__ void k_restrict_h_det(int nfx, int nfy, int nfz, int ncx, int ncy, int ncz,
                                  const T* __restrict__ bf, const T* __restrict__ tf,
                                  T* __restrict__ bc, const int* done) {
+  pdl_entry();
   if (skip(done)) return;
   const int64_t NX = nfx + 1, NY = nfy + 1;
   const int64_t CX = ncx + 1, CY = ncy + 1, nc = CX * CY * (ncz + 1);
@@ -324,6 +331,7 @@ __global__ void k_restrict_h_det(int nfx, int nfy, int nfz, int ncx, int ncy, in
 __global__ void k_coarse_tissue(int ncx, int ncy, int ncz, int nfx, int nfy, const double* sl,
                                 const double* st, const double* th, double* csl, double* cst,
                                 double* cth) {
+  pdl_entry();
   const int64_t n = (int64_t)ncx * ncy * ncz;
   GRID_LOOP(e, n) {
     const int kx = (int)(e % ncx), ky = (int)((e / ncx) % ncy), kz = (int)(e / ((int64_t)ncx * ncy));
@@ -338,6 +346,7 @@ __global__ void k_coarse_tissue(int ncx, int ncy, int ncz, int nfx, int nfy, con
 // Deterministic dot product; the last CTA writes the total to *out.
 __global__ void k_dot(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
                       double* partials, unsigned int* ticket, double* out) {
+  pdl_entry();
   __shared__ double red[32];
   double v = 0.0;
   GRID_LOOP(i, n) v = fma(a[i], b[i], v);
@@ -347,6 +356,7 @@ __global__ void k_dot(int64_t n, const double* __restrict__ a, const double* __r
 }
 
 __global__ void k_fill_start(int64_t n, double* v) {
+  pdl_entry();
   GRID_LOOP(i, n) {
     const unsigned long long h = ((unsigned long long)i * 2654435761ull) & 0xffffffffull;
     v[i] = (double)h / 4294967296.0 - 0.5;
@@ -354,11 +364,13 @@ __global__ void k_fill_start(int64_t n, double* v) {
 }
 
 __global__ void k_lanczos_z(int64_t n, const double* dinv, const double* r, double* z) {
+  pdl_entry();
   GRID_LOOP(i, n) z[i] = dinv[i] * r[i];
 }
 
 __global__ void k_lanczos_update(int64_t n, double alpha, const double* Ap, double* r,
                                  const double* dinv, double* z) {
+  pdl_entry();
   GRID_LOOP(i, n) {
     const double ri = fma(-alpha, Ap[i], r[i]);
     r[i] = ri;
@@ -367,6 +379,7 @@ __global__ void k_lanczos_update(int64_t n, double alpha, const double* Ap, doub
 }
 
 __global__ void k_lanczos_p(int64_t n, double beta, const double* z, double* p, double* Ap) {
+  pdl_entry();
   GRID_LOOP(i, n) {
     p[i] = fma(beta, p[i], z[i]);
     Ap[i] = 0.0;
@@ -411,6 +424,7 @@ __global__ void k_fpcg_init(int64_t n, const double* __restrict__ b, double* __r
                             double* __restrict__ r, T* __restrict__ b0, CgScalars* cg,
                             double* partials, int stride, unsigned int* ticket, double rtol,
                             double atol) {
+  pdl_entry();
   double v[2] = {0.0, 0.0};
   const int64_t nc = VEC ? n / 2 : 0;
   GRID_CHUNKS(c, nc) {
@@ -459,6 +473,7 @@ template <typename T>
 __global__ void k_fpcg_z(int64_t n, const T* __restrict__ x0, double* __restrict__ z,
                          const double* __restrict__ r, double* __restrict__ p, df_pair* __restrict__ p2,
                          CgScalars* cg, double* partials, int stride, unsigned int* ticket) {
+  pdl_entry();
   if (cg->done) return;
   const bool first = cg->iters == 0;
   double v[2] = {0.0, 0.0};
@@ -513,6 +528,7 @@ __global__ void k_fpcg_z(int64_t n, const T* __restrict__ x0, double* __restrict
 
 __global__ void k_fpcg_p(int64_t n, const double* __restrict__ z, double* __restrict__ p,
                          df_pair* __restrict__ p2, const CgScalars* cg) {
+  pdl_entry();
   if (cg->done || cg->iters == 0) return;  // first iteration: k_fpcg_z set p = z
   const double beta = cg->beta;
   using D2 = Pk<double, 2>;
@@ -541,6 +557,7 @@ template <typename T, bool VEC>
 __global__ void k_fpcg_xr(int64_t n, double* __restrict__ x, const double* __restrict__ p,
                           double* __restrict__ Ap, double* __restrict__ r, T* __restrict__ b0,
                           CgScalars* cg, double* partials, int stride, unsigned int* ticket) {
+  pdl_entry();
   if (cg->done) return;
   const double alpha = cg->alpha;
   double v[1] = {0.0};
@@ -587,11 +604,13 @@ __global__ void k_fpcg_xr(int64_t n, double* __restrict__ x, const double* __res
 
 template <typename T>
 __global__ void k_to_level0(int64_t n, const double* __restrict__ r, T* __restrict__ b0) {
+  pdl_entry();
   GRID_LOOP(i, n) b0[i] = (T)r[i];
 }
 
 template <typename T>
 __global__ void k_from_level0(int64_t n, const T* __restrict__ x0, double* __restrict__ z) {
+  pdl_entry();
   GRID_LOOP(i, n) z[i] = (double)x0[i];
 }
 
@@ -694,18 +713,18 @@ template <typename T>
 int restrict_to(sem_ctx* ctx, Gmg& g, int l, const int* done, cudaStream_t s) {
   GmgLevel& F = g.lv[l];
   GmgLevel& C = g.lv[l + 1];
-  k_zero<T><<<grid_chunks<T>(C.L->ndofs), kThreads, 0, s>>>(C.L->ndofs, (T*)C.b, done);
+  launch_k(k_zero<T>, grid_chunks<T>(C.L->ndofs), kThreads, 0, s, C.L->ndofs, (T*)C.b, done);
   T* loc = ctx->deterministic ? reinterpret_cast<T*>(ctx->det_scratch) : nullptr;
   if (F.to_next == 0) {
     const PTab tab = make_ptab(*F.L, *C.L);
     GMG_CK(p_transfer<T>(false, *F.L, *C.L, tab.P, (const T*)F.b, (const T*)F.t, (T*)C.b, nullptr,
                          loc, done, s));
   } else if (loc != nullptr) {
-    k_restrict_h_det<T><<<grid1d(C.L->ndofs), kThreads, 0, s>>>(
+    launch_k(k_restrict_h_det<T>, grid1d(C.L->ndofs), kThreads, 0, s,
         F.L->nx, F.L->ny, F.L->nz, C.L->nx, C.L->ny, C.L->nz, (const T*)F.b, (const T*)F.t,
         (T*)C.b, done);
   } else {
-    k_restrict_h<T><<<grid1d(F.L->ndofs), kThreads, 0, s>>>(
+    launch_k(k_restrict_h<T>, grid1d(F.L->ndofs), kThreads, 0, s,
         F.L->nx, F.L->ny, F.L->nz, C.L->nx, C.L->ny, C.L->nz, (const T*)F.b, (const T*)F.t,
         (T*)C.b, done);
   }
@@ -723,7 +742,7 @@ int prolong_from(sem_ctx* ctx, Gmg& g, int l, const int* done, cudaStream_t s) {
     GMG_CK(p_transfer<T>(true, *F.L, *C.L, tab.P, (const T*)C.x, nullptr, (T*)F.x, (T*)F.t, nullptr,
                          done, s));
   } else {
-    k_prolong_h<T><<<grid1d(F.L->ndofs), kThreads, 0, s>>>(
+    launch_k(k_prolong_h<T>, grid1d(F.L->ndofs), kThreads, 0, s,
         F.L->nx, F.L->ny, F.L->nz, C.L->nx, C.L->ny, C.L->nz, (const T*)C.x, (T*)F.x, (T*)F.t,
         done);
   }
@@ -746,7 +765,7 @@ int chebyshev(sem_ctx* ctx, Gmg& g, int l, int degree, bool zero_start, const in
   T* b = (T*)V.b; T* x = (T*)V.x; T* t = (T*)V.t; T* d = (T*)V.d; const T* invd = (const T*)V.invd;
   int k0 = 0;
   if (zero_start) {
-    k_cheb_zero_start<T><<<grid_chunks<T>(n), kThreads, 0, s>>>(n, b, invd, x, d, t, (T)(1.0 / theta), done);
+    launch_k(k_cheb_zero_start<T>, grid_chunks<T>(n), kThreads, 0, s, n, b, invd, x, d, t, (T)(1.0 / theta), done);
     GMG_CK(cudaGetLastError());
     ctx->launches += 1;
     k0 = 1;
@@ -755,11 +774,11 @@ int chebyshev(sem_ctx* ctx, Gmg& g, int l, int degree, bool zero_start, const in
     int rc = level_apply(ctx, L, g.precision, g.alpha, x, t, done, s);
     if (rc != SEM_OK) return rc;
     if (k == 0) {
-      k_cheb_step<T><<<grid_chunks<T>(n), kThreads, 0, s>>>(n, b, invd, x, d, t, (T)0, (T)(1.0 / theta), 1,
+      launch_k(k_cheb_step<T>, grid_chunks<T>(n), kThreads, 0, s, n, b, invd, x, d, t, (T)0, (T)(1.0 / theta), 1,
                                                            done);
     } else {
       const double rho = 1.0 / (2.0 * sigma - rho_old);
-      k_cheb_step<T><<<grid_chunks<T>(n), kThreads, 0, s>>>(n, b, invd, x, d, t, (T)(rho * rho_old),
+      launch_k(k_cheb_step<T>, grid_chunks<T>(n), kThreads, 0, s, n, b, invd, x, d, t, (T)(rho * rho_old),
                                                            (T)(2.0 * rho / delta), 0, done);
       rho_old = rho;
     }
@@ -797,11 +816,11 @@ int estimate_lambda(sem_ctx* ctx, Gmg& g, GmgLevel& V, double alpha, cudaStream_
   const Level& L = *V.L;
   const int64_t n = L.ndofs;
   const int gr = grid1d(n);
-  k_fill_start<<<gr, kThreads, 0, s>>>(n, g.lr);
-  k_lanczos_z<<<gr, kThreads, 0, s>>>(n, V.dinv64, g.lr, g.lz);
+  launch_k(k_fill_start, gr, kThreads, 0, s, n, g.lr);
+  launch_k(k_lanczos_z, gr, kThreads, 0, s, n, V.dinv64, g.lr, g.lz);
   GMG_CK(cudaMemcpyAsync(g.lp, g.lz, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   GMG_CK(cudaMemsetAsync(g.lAp, 0, sizeof(double) * n, s));
-  k_dot<<<gr, kThreads, 0, s>>>(n, g.lr, g.lz, g.partials, g.tickets, g.dots + 0);
+  launch_k(k_dot, gr, kThreads, 0, s, n, g.lr, g.lz, g.partials, g.tickets, g.dots + 0);
   GMG_CK(cudaGetLastError());
   double h[2];
   GMG_CK(cudaMemcpyAsync(h, g.dots, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -815,14 +834,14 @@ int estimate_lambda(sem_ctx* ctx, Gmg& g, GmgLevel& V, double alpha, cudaStream_
     a.mass_coef = alpha; a.out_scale = 1.0; a.scale_out = 0;
     a.yloc = ctx->deterministic ? ctx->det_scratch : nullptr;
     GMG_CK(launch_apply_fp64(L, a, false, s));
-    k_dot<<<gr, kThreads, 0, s>>>(n, g.lp, g.lAp, g.partials, g.tickets, g.dots + 1);
+    launch_k(k_dot, gr, kThreads, 0, s, n, g.lp, g.lAp, g.partials, g.tickets, g.dots + 1);
     GMG_CK(cudaMemcpyAsync(h, g.dots + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
     GMG_CK(cudaStreamSynchronize(s));
     const double pAp = h[0];
     if (!(pAp > 0.0) || !(rz > 0.0)) break;
     const double al = rz / pAp;
-    k_lanczos_update<<<gr, kThreads, 0, s>>>(n, al, g.lAp, g.lr, V.dinv64, g.lz);
-    k_dot<<<gr, kThreads, 0, s>>>(n, g.lr, g.lz, g.partials, g.tickets, g.dots + 2);
+    launch_k(k_lanczos_update, gr, kThreads, 0, s, n, al, g.lAp, g.lr, V.dinv64, g.lz);
+    launch_k(k_dot, gr, kThreads, 0, s, n, g.lr, g.lz, g.partials, g.tickets, g.dots + 2);
     GMG_CK(cudaMemcpyAsync(h, g.dots + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
     GMG_CK(cudaStreamSynchronize(s));
     const double rz_new = h[0];
@@ -830,7 +849,7 @@ int estimate_lambda(sem_ctx* ctx, Gmg& g, GmgLevel& V, double alpha, cudaStream_
     alphas.push_back(al);
     betas.push_back(be);
     rz = rz_new;
-    k_lanczos_p<<<gr, kThreads, 0, s>>>(n, be, g.lz, g.lp, g.lAp);
+    launch_k(k_lanczos_p, gr, kThreads, 0, s, n, be, g.lz, g.lp, g.lAp);
     GMG_CK(cudaGetLastError());
     if (!(rz > 0.0)) break;
   }
@@ -850,10 +869,10 @@ int set_alpha(sem_ctx* ctx, Gmg& g, double alpha, cudaStream_t s) {
   for (GmgLevel& V : g.lv) {
     const Level& L = *V.L;
     if (g.precision == SEM_PREC_FP64)
-      k_level_inv_diag<double><<<grid1d(L.ndofs), kThreads, 0, s>>>(L.ndofs, alpha, L.mdiag, L.kdiag,
+      launch_k(k_level_inv_diag<double>, grid1d(L.ndofs), kThreads, 0, s, L.ndofs, alpha, L.mdiag, L.kdiag,
                                                                    (double*)V.invd, V.dinv64);
     else
-      k_level_inv_diag<float><<<grid1d(L.ndofs), kThreads, 0, s>>>(L.ndofs, alpha, L.mdiag, L.kdiag,
+      launch_k(k_level_inv_diag<float>, grid1d(L.ndofs), kThreads, 0, s, L.ndofs, alpha, L.mdiag, L.kdiag,
                                                                   (float*)V.invd, V.dinv64);
     GMG_CK(cudaGetLastError());
     int rc = estimate_lambda(ctx, g, V, alpha, s);
@@ -945,7 +964,7 @@ int build(sem_ctx* ctx, cudaStream_t s) {
     GMG_CK(cudaMalloc(&V.sl, sizeof(double) * ne));
     GMG_CK(cudaMalloc(&V.st, sizeof(double) * ne));
     GMG_CK(cudaMalloc(&V.th, sizeof(double) * ne));
-    k_coarse_tissue<<<grid1d((int64_t)ne), kThreads, 0, s>>>(cx, cy, cz, nx, ny, F.sl, F.st, F.th,
+    launch_k(k_coarse_tissue, grid1d((int64_t)ne), kThreads, 0, s, cx, cy, cz, nx, ny, F.sl, F.st, F.th,
                                                               V.sl, V.st, V.th);
     GMG_CK(cudaGetLastError());
     F.to_next = 1;
@@ -1030,7 +1049,7 @@ int pcg_init_seq(sem_ctx* ctx, Gmg& g, double alpha, const double* b, const doub
   const int gr = grid1d(n);
   T* b0 = (T*)g.lv[0].b;
   const int stride = g.partial_len;
-  k_zero<double><<<gr, kThreads, 0, s>>>(n, w.Ap, nullptr);
+  launch_k(k_zero<double>, gr, kThreads, 0, s, n, w.Ap, nullptr);
   {
     ApplyArgs64 a{};
     a.map = L.map; a.metric = L.metric; a.u = x; a.y = w.Ap; a.nelem = L.nelem;
@@ -1039,10 +1058,10 @@ int pcg_init_seq(sem_ctx* ctx, Gmg& g, double alpha, const double* b, const doub
     GMG_CK(launch_operator(ctx, a, s));
   }
   if (aligned16(b))
-    k_fpcg_init<T, true><<<gr, kThreads, 0, s>>>(n, b, w.Ap, w.r, b0, w.cg, g.partials, stride, g.tickets,
+    launch_k(k_fpcg_init<T, true>, gr, kThreads, 0, s, n, b, w.Ap, w.r, b0, w.cg, g.partials, stride, g.tickets,
                                                rtol, atol);
   else
-    k_fpcg_init<T, false><<<gr, kThreads, 0, s>>>(n, b, w.Ap, w.r, b0, w.cg, g.partials, stride, g.tickets,
+    launch_k(k_fpcg_init<T, false>, gr, kThreads, 0, s, n, b, w.Ap, w.r, b0, w.cg, g.partials, stride, g.tickets,
                                                 rtol, atol);
   GMG_CK(cudaGetLastError());
   return SEM_OK;
@@ -1060,9 +1079,9 @@ int pcg_iter_seq(sem_ctx* ctx, Gmg& g, double alpha, double* x, cudaStream_t s) 
   if (rc != SEM_OK) return rc;
   // the double-float operator gathers p as the float pairs the p kernels write
   df_pair* p2 = ctx->op_precision == SEM_PREC_DF64 ? w.p2 : nullptr;
-  k_fpcg_z<T><<<gr, kThreads, 0, s>>>(n, (const T*)g.lv[0].x, g.z, w.r, w.p, p2, w.cg, g.partials,
+  launch_k(k_fpcg_z<T>, gr, kThreads, 0, s, n, (const T*)g.lv[0].x, g.z, w.r, w.p, p2, w.cg, g.partials,
                                       stride, g.tickets + 1);
-  k_fpcg_p<<<gr, kThreads, 0, s>>>(n, g.z, w.p, p2, w.cg);
+  launch_k(k_fpcg_p, gr, kThreads, 0, s, n, g.z, w.p, p2, w.cg);
   GMG_CK(cudaGetLastError());
   ApplyArgs64 ap{};
   ap.map = L.map; ap.metric = L.metric; ap.u = w.p; ap.y = w.Ap; ap.nelem = L.nelem;
@@ -1074,10 +1093,10 @@ int pcg_iter_seq(sem_ctx* ctx, Gmg& g, double alpha, double* x, cudaStream_t s) 
   GMG_CK(launch_operator(ctx, ap, s));
   GMG_CK(cudaEventRecordWithFlags(g.ev1, s, cudaEventRecordExternal));
   if (aligned16(x))
-    k_fpcg_xr<T, true><<<gr, kThreads, 0, s>>>(n, x, w.p, w.Ap, w.r, (T*)g.lv[0].b, w.cg, g.partials,
+    launch_k(k_fpcg_xr<T, true>, gr, kThreads, 0, s, n, x, w.p, w.Ap, w.r, (T*)g.lv[0].b, w.cg, g.partials,
                                              stride, g.tickets + 2);
   else
-    k_fpcg_xr<T, false><<<gr, kThreads, 0, s>>>(n, x, w.p, w.Ap, w.r, (T*)g.lv[0].b, w.cg, g.partials,
+    launch_k(k_fpcg_xr<T, false>, gr, kThreads, 0, s, n, x, w.p, w.Ap, w.r, (T*)g.lv[0].b, w.cg, g.partials,
                                               stride, g.tickets + 2);
   GMG_CK(cudaGetLastError());
   return SEM_OK;
@@ -1218,15 +1237,15 @@ int gmg_vcycle(sem_ctx* ctx, double alpha, const double* r, double* z, cudaStrea
   if ((rc = set_alpha(ctx, g, alpha, s)) != SEM_OK) return rc;
   const int64_t n = ctx->L.ndofs;
   if (g.precision == SEM_PREC_FP64)
-    k_to_level0<double><<<grid1d(n), kThreads, 0, s>>>(n, r, (double*)g.lv[0].b);
+    launch_k(k_to_level0<double>, grid1d(n), kThreads, 0, s, n, r, (double*)g.lv[0].b);
   else
-    k_to_level0<float><<<grid1d(n), kThreads, 0, s>>>(n, r, (float*)g.lv[0].b);
+    launch_k(k_to_level0<float>, grid1d(n), kThreads, 0, s, n, r, (float*)g.lv[0].b);
   GMG_CK(cudaGetLastError());
   if ((rc = vcycle(ctx, g, nullptr, s)) != SEM_OK) return rc;
   if (g.precision == SEM_PREC_FP64)
-    k_from_level0<double><<<grid1d(n), kThreads, 0, s>>>(n, (const double*)g.lv[0].x, z);
+    launch_k(k_from_level0<double>, grid1d(n), kThreads, 0, s, n, (const double*)g.lv[0].x, z);
   else
-    k_from_level0<float><<<grid1d(n), kThreads, 0, s>>>(n, (const float*)g.lv[0].x, z);
+    launch_k(k_from_level0<float>, grid1d(n), kThreads, 0, s, n, (const float*)g.lv[0].x, z);
   GMG_CK(cudaGetLastError());
   return SEM_OK;
 }

@@ -19,6 +19,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 
 #include "sem.h"
 #include "sem_df64.cuh"
@@ -43,6 +44,40 @@ __device__ __forceinline__ int64_t dbg_index(int64_t g, int64_t n, unsigned long
 #else
 #define SEM_IDX(g, n, word, kind) (g)
 #endif
+
+// Programmatic dependent launch (PDL).  A kernel launched by launch_k may be
+// scheduled while the kernel before it in the stream is still draining, and
+// then runs its blocks up to pdl_entry().  pdl_entry() first lets the next
+// kernel of the stream launch in turn (griddepcontrol.launch_dependents), then
+// waits until the previous grid has completed and its writes are visible
+// (griddepcontrol.wait).  Every kernel launched by launch_k calls pdl_entry()
+// in every block before it reads or writes memory that another kernel writes
+// or reads, so that grids still complete in stream order and each kernel sees
+// all earlier results.  In a kernel launched without the attribute both
+// instructions return at once.  Inside a CUDA graph the attribute becomes a
+// programmatic edge between the two kernel nodes.
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_entry() {
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+}
+#endif
+bool pdl_enabled();  // false when the environment sets SEM_NO_PDL (read once)
+template <typename... P, typename... A>
+cudaError_t launch_k(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                     A&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
 
 // Storage type of the vectors an operator kernel reads and writes: the df64
 // operator works on FP64 vectors.

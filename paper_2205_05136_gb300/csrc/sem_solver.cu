@@ -66,6 +66,7 @@ __device__ __forceinline__ bool grid_sums(double (&v)[K], double* partials, unsi
 
 __global__ void k_inv_diag(int64_t n, double alpha, const double* __restrict__ m,
                            const double* __restrict__ k, double* __restrict__ inv) {
+  pdl_entry();
 #pragma unroll 1
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -74,6 +75,7 @@ __global__ void k_inv_diag(int64_t n, double alpha, const double* __restrict__ m
 
 __global__ void k_scale_mul(int64_t n, double a, const double* __restrict__ d,
                             const double* __restrict__ x, double* __restrict__ y) {
+  pdl_entry();
 #pragma unroll 1
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -82,6 +84,7 @@ __global__ void k_scale_mul(int64_t n, double a, const double* __restrict__ d,
 
 __global__ void k_scale_mul32(int64_t n, float a, const double* __restrict__ d,
                               const float* __restrict__ x, float* __restrict__ y) {
+  pdl_entry();
 #pragma unroll 1
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -94,6 +97,7 @@ __global__ void __launch_bounds__(kVecThreads)
               const double* __restrict__ inv, double* __restrict__ r, double* __restrict__ z,
               double* __restrict__ p, df_pair* __restrict__ p2, CgScalars* cg, double* partials,
               unsigned int* ticket, double rtol, double atol) {
+  pdl_entry();
   double v[3] = {0.0, 0.0, 0.0};
 #pragma unroll 1
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -137,6 +141,7 @@ __global__ void __launch_bounds__(kVecThreads)
     k_cg_xr(int64_t n, double* __restrict__ x, const double* __restrict__ p,
             const double* __restrict__ Ap, double* __restrict__ r, const double* __restrict__ inv,
             double* __restrict__ z, CgScalars* cg, double* partials, unsigned int* ticket) {
+  pdl_entry();
   if (cg->done) return;
   const double alpha = cg->alpha;
   double v[2] = {0.0, 0.0};
@@ -194,6 +199,7 @@ __global__ void __launch_bounds__(kVecThreads)
 __global__ void __launch_bounds__(kVecThreads)
     k_cg_p(int64_t n, const double* __restrict__ z, double* __restrict__ p, df_pair* __restrict__ p2,
            double* __restrict__ Ap, const CgScalars* cg) {
+  pdl_entry();
   if (cg->done) return;
   const double beta = cg->beta;
   const int64_t g0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -251,6 +257,7 @@ __global__ void __launch_bounds__(kVecThreads)
                 double* __restrict__ hnext, double* __restrict__ x0, double* __restrict__ out,
                 const double* __restrict__ mdiag, const double* __restrict__ mask, double iapp,
                 const IonicArgs prm, double dt, int first) {
+  pdl_entry();
   const double inv_dt = 1.0 / dt, inv_2dt = 0.5 / dt;
   const double c_open = (first ? dt : 2.0 * dt) * prm.inv_tau_open;
   const double c_close = (first ? dt : 2.0 * dt) * prm.inv_tau_close;
@@ -286,41 +293,93 @@ struct IonicDfArgs {
   DfExpConst ex;
 };
 
+// One node: h^{n+1} and the right-hand side from u^n, u^{n-1}, h^n, h^{n-1}
+// (the mass diagonal md and the stimulus mask value mk, 0 or 1, when present).
+__device__ __forceinline__ void ionic_df_node(double u0d, double u1d, double h0d, double h1d, double md,
+                                              bool use_md, bool stim, const IonicDfArgs& P, int first,
+                                              double& h_out, double& rhs_out) {
+  const df u0 = dfd(u0d);
+  const df u1 = first ? u0 : dfd(u1d);
+  const df us = first ? u0 : (u0 + u0) - u1;
+  const df v = dfnorm(fma(us, P.inv_amp, P.v_off));
+  df xe = fma(v, P.neg_inv_kappa, P.x_off);
+  if (xe.h > 80.f) xe = df(80.f, 0.f);
+  const df E = dfexp(xe, P.ex);
+  const df ope = df(1.f, 0.f) + E;
+  const df H = first ? dfd(h0d) : fma(df(4.f, 0.f), dfd(h0d), dfneg(dfd(h1d)));
+  const df num = fma(H, ope, P.c_open * E);
+  const df den = fma(P.c_den, ope, fma(P.c_open, E, P.c_close));
+  const df h = dfdiv(num, den);
+  const df v2 = v * v;
+  const df iion = fma(P.i_in * h, v2 - v * v2, P.i_out * v);
+  df g = first ? fma(u0, P.inv_dt, dfneg(iion)) : fma((u0 + u0 + u0 + u0) - u1, P.inv_2dt, dfneg(iion));
+  if (stim) g = g + P.iapp;
+  h_out = df_to_double(h);
+  rhs_out = df_to_double(use_md ? dfnorm(dfd(md) * g) : dfnorm(g));
+}
+
 __global__ void __launch_bounds__(kVecThreads)
     k_ionic_rhs_df(int64_t n, const double* __restrict__ un, const double* __restrict__ unm1,
                    const double* __restrict__ hn, const double* __restrict__ hnm1,
                    double* __restrict__ hnext, double* __restrict__ x0, double* __restrict__ out,
                    const double* __restrict__ mdiag, const double* __restrict__ mask,
                    const IonicDfArgs P, int first) {
+  pdl_entry();
 #pragma unroll 1
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double u0d = un[i];
-    const df u0 = dfd(u0d);
-    const df u1 = first ? u0 : dfd(unm1[i]);
-    const df us = first ? u0 : (u0 + u0) - u1;
-    const df v = dfnorm(fma(us, P.inv_amp, P.v_off));
-    df xe = fma(v, P.neg_inv_kappa, P.x_off);
-    if (xe.h > 80.f) xe = df(80.f, 0.f);
-    const df E = dfexp(xe, P.ex);
-    const df ope = df(1.f, 0.f) + E;
-    const df H = first ? dfd(hn[i]) : fma(df(4.f, 0.f), dfd(hn[i]), dfneg(dfd(hnm1[i])));
-    const df num = fma(H, ope, P.c_open * E);
-    const df den = fma(P.c_den, ope, fma(P.c_open, E, P.c_close));
-    const df h = dfdiv(num, den);
-    const df v2 = v * v;
-    const df iion = fma(P.i_in * h, v2 - v * v2, P.i_out * v);
-    df g = first ? fma(u0, P.inv_dt, dfneg(iion))
-                 : fma((u0 + u0 + u0 + u0) - u1, P.inv_2dt, dfneg(iion));
     // the stimulus mask holds 0 or 1
-    if (mask != nullptr && __double2hiint(mask[i]) != 0) g = g + P.iapp;
-    hnext[i] = df_to_double(h);
+    const bool stim = mask != nullptr && __double2hiint(mask[i]) != 0;
+    ionic_df_node(u0d, first ? 0.0 : unm1[i], hn[i], first ? 0.0 : hnm1[i], mdiag ? mdiag[i] : 0.0,
+                  mdiag != nullptr, stim, P, first, hnext[i], out[i]);
     x0[i] = u0d;
-    out[i] = df_to_double(mdiag ? dfnorm(dfd(mdiag[i]) * g) : dfnorm(g));
+  }
+}
+
+// The same on two consecutive nodes per thread with 16-byte loads and stores
+// (all arrays 16-byte aligned): twice the bytes in flight per load, which
+// matters when the inputs are page-locked host memory read over the host link.
+// The last node of an odd n is done by thread 0 of block 0.
+__global__ void __launch_bounds__(kVecThreads)
+    k_ionic_rhs_df2(int64_t n, const double2* __restrict__ un, const double2* __restrict__ unm1,
+                    const double2* __restrict__ hn, const double2* __restrict__ hnm1,
+                    double2* __restrict__ hnext, double2* __restrict__ x0, double2* __restrict__ out,
+                    const double2* __restrict__ mdiag, const double2* __restrict__ mask,
+                    const IonicDfArgs P, int first) {
+  pdl_entry();
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+    const int64_t t = n - 1;
+    auto r = [](const double2* q, int64_t i) { return reinterpret_cast<const double*>(q)[i]; };
+    const double u0 = r(un, t);
+    ionic_df_node(u0, first ? 0.0 : r(unm1, t), r(hn, t), first ? 0.0 : r(hnm1, t),
+                  mdiag ? r(mdiag, t) : 0.0, mdiag != nullptr, mask != nullptr && __double2hiint(r(mask, t)) != 0,
+                  P, first, reinterpret_cast<double*>(hnext)[t], reinterpret_cast<double*>(out)[t]);
+    reinterpret_cast<double*>(x0)[t] = u0;
+  }
+  const int64_t n2 = n / 2;
+#pragma unroll 1
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 u0 = un[i];
+    const double2 u1 = first ? make_double2(0.0, 0.0) : unm1[i];
+    const double2 h0 = hn[i];
+    const double2 h1 = first ? make_double2(0.0, 0.0) : hnm1[i];
+    const double2 md = mdiag ? mdiag[i] : make_double2(0.0, 0.0);
+    const double2 mk = mask ? mask[i] : make_double2(0.0, 0.0);
+    double2 hh, rr;
+    ionic_df_node(u0.x, u1.x, h0.x, h1.x, md.x, mdiag != nullptr, __double2hiint(mk.x) != 0, P, first, hh.x,
+                  rr.x);
+    ionic_df_node(u0.y, u1.y, h0.y, h1.y, md.y, mdiag != nullptr, __double2hiint(mk.y) != 0, P, first, hh.y,
+                  rr.y);
+    hnext[i] = hh;
+    out[i] = rr;
+    x0[i] = u0;
   }
 }
 
 __global__ void k_fill_pair(int64_t n, double* a, double va, double* b, double vb) {
+  pdl_entry();
 #pragma unroll 1
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -336,6 +395,7 @@ __global__ void __launch_bounds__(kVecThreads)
     k_activation(int64_t n, const double* __restrict__ u1, const double* __restrict__ u0,
                  const double* __restrict__ um1, int first, double dt, double t1,
                  double* __restrict__ dmax, double* __restrict__ tau) {
+  pdl_entry();
   const double inv_dt = 1.0 / dt, inv_2dt = 0.5 / dt;
 #pragma unroll 1
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -353,7 +413,7 @@ __global__ void __launch_bounds__(kVecThreads)
 
 cudaError_t activation_reset(sem_state* st, cudaStream_t s) {
   const int64_t n = st->ctx->L.ndofs;
-  k_fill_pair<<<vec_grid(n), kVecThreads, 0, s>>>(n, st->act_dmax, -1.0, st->act_tau,
+  launch_k(k_fill_pair, vec_grid(n), kVecThreads, 0, s, n, st->act_dmax, -1.0, st->act_tau,
                                                   std::numeric_limits<double>::quiet_NaN());
   return cudaGetLastError();
 }
@@ -420,7 +480,7 @@ int apply_fp64(sem_ctx* ctx, double alpha, double beta, const double* u, double*
   const Level& L = ctx->L;
   if (beta == 0.0) {
     if (L.quad == SEM_QUAD_LGL) {
-      k_scale_mul<<<vec_grid(L.ndofs), kVecThreads, 0, s>>>(L.ndofs, alpha, L.mdiag, u, y);
+      launch_k(k_scale_mul, vec_grid(L.ndofs), kVecThreads, 0, s, L.ndofs, alpha, L.mdiag, u, y);
       ctx->launches += 1;
       SEM_CK(cudaGetLastError());
       return SEM_OK;
@@ -494,7 +554,7 @@ int apply_fp32(sem_ctx* ctx, double alpha, double beta, const float* u, float* y
     SEM_CK(setup_metric_lowp(L, false, s));
   }
   if (beta == 0.0 && L.quad == SEM_QUAD_LGL) {
-    k_scale_mul32<<<vec_grid(L.ndofs), kVecThreads, 0, s>>>(L.ndofs, (float)alpha, L.mdiag, u, y);
+    launch_k(k_scale_mul32, vec_grid(L.ndofs), kVecThreads, 0, s, L.ndofs, (float)alpha, L.mdiag, u, y);
     SEM_CK(cudaGetLastError());
     return SEM_OK;
   }
@@ -524,7 +584,7 @@ int apply_tc(sem_ctx* ctx, double alpha, double beta, const float* u, float* y, 
   if (ctx->deterministic)
     return fail(ctx, SEM_ERR_UNSUPPORTED, "the tensor-core apply has no deterministic mode");
   if (beta == 0.0) {  // SEM-NI mass: diagonal
-    k_scale_mul32<<<vec_grid(L.ndofs), kVecThreads, 0, s>>>(L.ndofs, (float)alpha, L.mdiag, u, y);
+    launch_k(k_scale_mul32, vec_grid(L.ndofs), kVecThreads, 0, s, L.ndofs, (float)alpha, L.mdiag, u, y);
     SEM_CK(cudaGetLastError());
     return SEM_OK;
   }
@@ -551,7 +611,7 @@ int cg_solve(sem_ctx* ctx, double alpha, const double* b, double* x, double rtol
   const double* inv = nullptr;
   if (precond == SEM_PC_JACOBI) {
     if (w.inv_alpha != alpha) {
-      k_inv_diag<<<vg, kVecThreads, 0, s>>>(n, alpha, L.mdiag, L.kdiag, w.invdiag);
+      launch_k(k_inv_diag, vg, kVecThreads, 0, s, n, alpha, L.mdiag, L.kdiag, w.invdiag);
       ctx->launches += 1;
       SEM_CK(cudaGetLastError());
       w.inv_alpha = alpha;
@@ -571,7 +631,7 @@ int cg_solve(sem_ctx* ctx, double alpha, const double* b, double* x, double rtol
   ctx->launches += 2;
   // the double-float operator gathers p as the float pairs the p kernels write
   df_pair* p2 = ctx->op_precision == SEM_PREC_DF64 ? w.p2 : nullptr;
-  k_cg_init<<<vg, kVecThreads, 0, s>>>(n, b, w.Ap, inv, w.r, w.z, w.p, p2, w.cg, w.vec_partials,
+  launch_k(k_cg_init, vg, kVecThreads, 0, s, n, b, w.Ap, inv, w.r, w.z, w.p, p2, w.cg, w.vec_partials,
                                        w.tickets + 0, rtol, atol);
   SEM_CK(cudaGetLastError());
 
@@ -601,12 +661,12 @@ int cg_solve(sem_ctx* ctx, double alpha, const double* b, double* x, double rtol
         SEM_CK(launch_operator(ctx, ap, s));
         if (tm.enabled) SEM_CK(cudaEventRecord(evs[2 * c + 1], s));
         if ((reinterpret_cast<uintptr_t>(x) & 15u) == 0)
-          k_cg_xr<true><<<vg, kVecThreads, 0, s>>>(n, x, w.p, w.Ap, w.r, inv, w.z, w.cg, w.vec_partials,
+          launch_k(k_cg_xr<true>, vg, kVecThreads, 0, s, n, x, w.p, w.Ap, w.r, inv, w.z, w.cg, w.vec_partials,
                                                    w.tickets + 0);
         else
-          k_cg_xr<false><<<vg, kVecThreads, 0, s>>>(n, x, w.p, w.Ap, w.r, inv, w.z, w.cg, w.vec_partials,
+          launch_k(k_cg_xr<false>, vg, kVecThreads, 0, s, n, x, w.p, w.Ap, w.r, inv, w.z, w.cg, w.vec_partials,
                                                     w.tickets + 0);
-        k_cg_p<<<vg, kVecThreads, 0, s>>>(n, w.z, w.p, p2, w.Ap, w.cg);
+        launch_k(k_cg_p, vg, kVecThreads, 0, s, n, w.z, w.p, p2, w.Ap, w.cg);
       }
       SEM_CK(cudaGetLastError());
       launched += this_chunk;
@@ -711,18 +771,38 @@ int time_steps(sem_ctx* ctx, sem_state* st, double dt, int nsteps, double rtol, 
       idf.inv_dt = df(1.0 / dt);
       idf.inv_2dt = df(0.5 / dt);
       idf.iapp = df(on ? ctx->stim_amp : 0.0);
-      k_ionic_rhs_df<<<vg, kVecThreads, 0, s>>>(
-          n, st->U[st->cur], st->U[st->prev], st->H[st->cur], st->H[st->prev], st->H[st->next],
-          st->U[st->next], out, L.quad == SEM_QUAD_LGL ? L.mdiag : nullptr,
-          on ? ctx->stim_mask : nullptr, idf, first);
+      const double* ptrs[9] = {st->U[st->cur], st->U[st->prev], st->H[st->cur], st->H[st->prev],
+                               st->H[st->next], st->U[st->next], out, L.mdiag, ctx->stim_mask};
+      bool a16 = true;
+      for (const double* q : ptrs) a16 = a16 && (q == nullptr || (reinterpret_cast<uintptr_t>(q) & 15u) == 0);
+      const double* md = L.quad == SEM_QUAD_LGL ? L.mdiag : nullptr;
+      const double* mk = on ? ctx->stim_mask : nullptr;
+      if (a16) {
+        auto d2 = [](const double* q) { return reinterpret_cast<const double2*>(q); };
+        auto w2 = [](double* q) { return reinterpret_cast<double2*>(q); };
+        launch_k(k_ionic_rhs_df2, vec_grid(n / 2 + 1), kVecThreads, 0, s, n, d2(st->U[st->cur]),
+                 d2(st->U[st->prev]), d2(st->H[st->cur]), d2(st->H[st->prev]), w2(st->H[st->next]),
+                 w2(st->U[st->next]), w2(out), d2(md), d2(mk), idf, first);
+      } else {
+        launch_k(k_ionic_rhs_df, vg, kVecThreads, 0, s, n, st->U[st->cur], st->U[st->prev], st->H[st->cur],
+                 st->H[st->prev], st->H[st->next], st->U[st->next], out, md, mk, idf, first);
+      }
     } else {
-      k_ionic_rhs<<<vg, kVecThreads, 0, s>>>(
+      launch_k(k_ionic_rhs, vg, kVecThreads, 0, s,
           n, st->U[st->cur], st->U[st->prev], st->H[st->cur], st->H[st->prev], st->H[st->next],
           st->U[st->next], out, L.quad == SEM_QUAD_LGL ? L.mdiag : nullptr,
           on ? ctx->stim_mask : nullptr, on ? ctx->stim_amp : 0.0, ia, dt, first);
     }
     SEM_CK(cudaGetLastError());
     ctx->launches += 1;
+    auto& hc = ctx->host_copies;
+    if (hc.h_dst != nullptr && k == 0) {  // h^{n+1} to the host while the solve runs
+      SEM_CK(cudaEventRecord(hc.ev_ionic, s));
+      SEM_CK(cudaStreamWaitEvent(hc.side, hc.ev_ionic, 0));
+      SEM_CK(cudaMemcpyAsync(hc.h_dst, st->H[st->next], sizeof(double) * n, cudaMemcpyDeviceToHost,
+                             hc.side));
+      SEM_CK(cudaEventRecord(hc.ev_h, hc.side));
+    }
     if (L.quad == SEM_QUAD_LG) {
       rc = apply_fp64(ctx, 1.0, 0.0, w.g, w.b, s);
       if (rc != SEM_OK) return rc;
@@ -737,7 +817,7 @@ int time_steps(sem_ctx* ctx, sem_state* st, double dt, int nsteps, double rtol, 
     st->next = old_prev;
     st->n += 1;
     if (st->act_track) {  // u^{n+1}, u^n, u^{n-1} sit in U[cur], U[prev], U[next] now
-      k_activation<<<vg, kVecThreads, 0, s>>>(n, st->U[st->cur], st->U[st->prev], st->U[st->next],
+      launch_k(k_activation, vg, kVecThreads, 0, s, n, st->U[st->cur], st->U[st->prev], st->U[st->next],
                                               first, dt, (double)st->n * dt, st->act_dmax, st->act_tau);
       SEM_CK(cudaGetLastError());
       ctx->launches += 1;

@@ -79,6 +79,7 @@ __global__ void __launch_bounds__(kTThreads)
                  const int* __restrict__ map_f, const __grid_constant__ PMat<NF, NC, T> pm,
                  const T* __restrict__ xc, T* __restrict__ xf, T* __restrict__ tf, int64_t ndf,
                  int64_t ndc, unsigned long long* dbg, const int* done) {
+  pdl_entry();
   if (done != nullptr && *done) return;
   constexpr int E = TransferCfg<NF>::E;
   constexpr int NF3 = NF * NF * NF, NC3 = NC * NC * NC;
@@ -150,6 +151,7 @@ __global__ void __launch_bounds__(kTThreads)
                   const T* __restrict__ bf, const T* __restrict__ tf, T* __restrict__ bc,
                   T* __restrict__ bloc, int64_t ndf, int64_t ndc, unsigned long long* dbg,
                   const int* done) {
+  pdl_entry();
   if (done != nullptr && *done) return;
   constexpr int E = TransferCfg<NF>::E;
   constexpr int NF3 = NF * NF * NF, NC3 = NC * NC * NC;
@@ -232,10 +234,10 @@ cudaError_t launch_pair(bool prolong, const Level& F, const Level& C, const doub
   const int E = TransferCfg<NF>::E;
   const int grid = (F.nelem + E - 1) / E;
   if (prolong)
-    k_prolong_sf<NF, NC, T><<<grid, kTThreads, 0, s>>>(F.nelem, F.nx, F.ny, F.nz, C.map, F.map, pm,
+    launch_k(k_prolong_sf<NF, NC, T>, grid, kTThreads, 0, s, F.nelem, F.nx, F.ny, F.nz, C.map, F.map, pm,
                                                        src_b, dst, dst_t, F.ndofs, C.ndofs, F.dbg, done);
   else
-    k_restrict_sf<NF, NC, T><<<grid, kTThreads, 0, s>>>(F.nelem, F.nx, F.ny, F.nz, C.map, F.map, pm,
+    launch_k(k_restrict_sf<NF, NC, T>, grid, kTThreads, 0, s, F.nelem, F.nx, F.ny, F.nz, C.map, F.map, pm,
                                                         src_b, src_t, dst, loc, F.ndofs, C.ndofs, F.dbg,
                                                         done);
   const cudaError_t e = cudaGetLastError();

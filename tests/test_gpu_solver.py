@@ -160,20 +160,29 @@ def test_step_host_matches_device_step():
     assert rel(u.numpy(), ud.cpu().numpy()) < 1e-13 and rel(h.numpy(), hd.cpu().numpy()) < 1e-13
 
 
-@pytest.mark.parametrize("pinned", [True, False])
-def test_step_host_out_matches_device_step(pinned):
-    """Separate output arrays, rotated by the caller; page-locked arrays are read and
-    written by the device in place, pageable ones are staged by copies."""
+@pytest.mark.parametrize("layout", ["pinned", "pageable", "pinned_offset"])
+@pytest.mark.parametrize("precision", [capi.SEM_PREC_FP64, capi.SEM_PREC_DF64])
+def test_step_host_out_matches_device_step(layout, precision):
+    """Separate output arrays, rotated by the caller; page-locked inputs are read by
+    the device in place, pageable ones are staged by copies.  The slab has an odd
+    number of nodes (765): the double-float ionic update's two-node kernel does
+    the last node alone; arrays that start 8 bytes past a 16-byte boundary
+    (pinned_offset) take its one-node kernel."""
     s, tissue, g, o = _small(2, "LGL")
     g.set_ionic()
     g.set_stimulus("box", (0, 0, 0, 1.5, 1.5, 1.5), 50.0, 0.0, 1.0)
+    capi.sem_set_operator_precision(g.ctx, precision)
     st = g.new_state(-85.0, 1.0)
     st.step(0.05, 4, rtol=1e-12)
     ud, hd, _ = st.get()
 
     def arr(v):
+        if layout == "pinned_offset":
+            t = torch.full((o.ndofs + 1,), v, dtype=torch.float64).pin_memory()[1:]
+            assert t.data_ptr() % 16 == 8
+            return t
         t = torch.full((o.ndofs,), v, dtype=torch.float64)
-        return t.pin_memory() if pinned else t
+        return t.pin_memory() if layout == "pinned" else t
 
     us = [arr(-85.0), arr(-85.0), arr(0.0)]  # u^{n-1}, u^n, free
     hs = [arr(1.0), arr(1.0), arr(0.0)]
