@@ -285,7 +285,7 @@ __host__ __device__ constexpr size_t apply_warp_tile_bytes() {
 template <int P, int QUAD, typename T, typename MT, bool DOT, bool MASS_ONLY, bool WARP = false>
 __global__ void __launch_bounds__(kApplyThreads)
     sem_apply_kernel(const ApplyArgs<T, MT> a, const __grid_constant__ KTab<P + 1, T> tab) {
-  pdl_entry();
+  pdl_trigger();
   static_assert(!(WARP && DOT), "the fused inner product needs the CTA-wide mode");
   constexpr int N = P + 1, N2 = N * N, N3 = N2 * N;
   using ML = MetricLayout<MT>;
@@ -305,9 +305,12 @@ __global__ void __launch_bounds__(kApplyThreads)
     if (WARP) __syncwarp(); else __syncthreads();
   };
 
-  if (a.done != nullptr && *a.done) return;
   const int e0 = WARP ? (blockIdx.x * kWarpsPerCta + warp) * E : blockIdx.x * E;
   if (WARP && e0 >= a.nelem) return;  // no CTA-wide barrier follows in this mode
+  // while the previous kernel drains: the group's map entries into L2
+  prefetch_l2_lines(a.map + (size_t)e0 * N3, (size_t)min(E, a.nelem - e0) * N3 * sizeof(int), tid, nth);
+  pdl_wait();
+  if (a.done != nullptr && *a.done) return;
 
   if (STAGE) {  // the CTA's metric block: contiguous, 16-byte aligned, a multiple of 16 bytes
     const int ne = min(E, a.nelem - e0);
@@ -622,15 +625,21 @@ template <int P, int QUAD, typename MT>
 __global__ void __launch_bounds__(kApplyThreads, 4)
     sem_apply_pipe_kernel(const ApplyArgs<float, MT> a, const __grid_constant__ KTab<P + 1, float> tab,
                           int nunits) {
-  pdl_entry();
+  pdl_trigger();
   using C = PipeCfg<P, MT>;
   using T = float;
   constexpr int N = C::N, N2 = C::N2, N3 = C::N3, G = C::G, LPL = C::LPL, NL = C::NL;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (a.done != nullptr && *a.done) return;
   int unit = blockIdx.x * kWarpsPerCta + warp;
   if (unit >= nunits) return;  // no CTA-wide barrier in this kernel
+  {  // while the previous kernel drains: the first unit's map entries and metric into L2
+    const int ne = min(G, a.nelem - unit * G);
+    prefetch_l2_lines(a.map + (size_t)unit * C::UT, (size_t)ne * N3 * sizeof(int), lane, 32);
+    prefetch_l2_lines(a.metric + (size_t)unit * G * C::BLK, (size_t)ne * C::BLK * sizeof(MT), lane, 32);
+  }
+  pdl_wait();
+  if (a.done != nullptr && *a.done) return;
   const int tw = gridDim.x * kWarpsPerCta;
   unsigned char* wb = smem_raw + (size_t)warp * C::warp_bytes;
   MT* sM0 = reinterpret_cast<MT*>(wb);

@@ -56,10 +56,24 @@ __device__ __forceinline__ int64_t dbg_index(int64_t g, int64_t n, unsigned long
 // all earlier results.  In a kernel launched without the attribute both
 // instructions return at once.  Inside a CUDA graph the attribute becomes a
 // programmatic edge between the two kernel nodes.
+// Kernels that can start useful independent work (L2 prefetches of the map and
+// metric, which no kernel of a solve writes) call pdl_trigger(), issue it, then
+// pdl_wait(); a prefetch only warms L2, the point of coherence, so nothing read
+// before the wait is used.
 #ifdef __CUDACC__
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
 __device__ __forceinline__ void pdl_entry() {
-  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
-  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  pdl_trigger();
+  pdl_wait();
+}
+// L2 prefetch of the 128-byte lines of [p, p + bytes), line `first` and every
+// `step`-th after it by this thread.
+__device__ __forceinline__ void prefetch_l2_lines(const void* p, size_t bytes, int first, int step) {
+  const uintptr_t a0 = reinterpret_cast<uintptr_t>(p) & ~(uintptr_t)127;
+  const uintptr_t end = reinterpret_cast<uintptr_t>(p) + bytes;
+  for (uintptr_t a = a0 + (uintptr_t)first * 128u; a < end; a += (uintptr_t)step * 128u)
+    asm volatile("prefetch.global.L2 [%0];\n" ::"l"(a));
 }
 #endif
 bool pdl_enabled();  // false when the environment sets SEM_NO_PDL (read once)
