@@ -33,11 +33,13 @@
 
 namespace sem {
 
-// Sum-factorized p-transfers (sem_transfer.cu).
+// Separable p-transfers on the slab lattice (sem_transfer.cu); w1, w2 scratch of
+// p_transfer_scratch(F, C, 1) and (F, C, 2) entries.
 template <typename T>
 cudaError_t p_transfer(bool prolong, const Level& F, const Level& C, const double (*P)[kMaxN],
-                       const T* src_b, const T* src_t, T* dst, T* dst_t, T* loc, const int* done,
+                       const T* src_b, const T* src_t, T* dst, T* dst_t, T* w1, T* w2, const int* done,
                        cudaStream_t s);
+size_t p_transfer_scratch(const Level& F, const Level& C, int which);
 
 struct GmgLevel {
   Level* L = nullptr;
@@ -46,6 +48,7 @@ struct GmgLevel {
   double *sl = nullptr, *st = nullptr, *th = nullptr;
   bool owns_tissue = false;
   void *b = nullptr, *x = nullptr, *t = nullptr, *d = nullptr, *invd = nullptr;
+  void *pw1 = nullptr, *pw2 = nullptr;  // p-transfer scratch towards the next level
   double* dinv64 = nullptr;
   double lam = 0.0;
 };
@@ -708,18 +711,21 @@ PTab make_ptab(const Level& fine, const Level& coarse) {
   return t;
 }
 
-// Restrict (b_l - t_l) into b_{l+1} (zeroed first).
+// Restrict (b_l - t_l) into b_{l+1}.
 template <typename T>
 int restrict_to(sem_ctx* ctx, Gmg& g, int l, const int* done, cudaStream_t s) {
   GmgLevel& F = g.lv[l];
   GmgLevel& C = g.lv[l + 1];
-  launch_k(k_zero<T>, grid_chunks<T>(C.L->ndofs), kThreads, 0, s, C.L->ndofs, (T*)C.b, done);
-  T* loc = ctx->deterministic ? reinterpret_cast<T*>(ctx->det_scratch) : nullptr;
-  if (F.to_next == 0) {
+  if (F.to_next == 0) {  // three passes that write b_{l+1}
     const PTab tab = make_ptab(*F.L, *C.L);
     GMG_CK(p_transfer<T>(false, *F.L, *C.L, tab.P, (const T*)F.b, (const T*)F.t, (T*)C.b, nullptr,
-                         loc, done, s));
-  } else if (loc != nullptr) {
+                         (T*)F.pw1, (T*)F.pw2, done, s));
+    ctx->launches += 3;
+    return SEM_OK;
+  }
+  launch_k(k_zero<T>, grid_chunks<T>(C.L->ndofs), kThreads, 0, s, C.L->ndofs, (T*)C.b, done);
+  T* loc = ctx->deterministic ? reinterpret_cast<T*>(ctx->det_scratch) : nullptr;
+  if (loc != nullptr) {
     launch_k(k_restrict_h_det<T>, grid1d(C.L->ndofs), kThreads, 0, s,
         F.L->nx, F.L->ny, F.L->nz, C.L->nx, C.L->ny, C.L->nz, (const T*)F.b, (const T*)F.t,
         (T*)C.b, done);
@@ -739,8 +745,10 @@ int prolong_from(sem_ctx* ctx, Gmg& g, int l, const int* done, cudaStream_t s) {
   GmgLevel& C = g.lv[l + 1];
   if (F.to_next == 0) {
     const PTab tab = make_ptab(*F.L, *C.L);
-    GMG_CK(p_transfer<T>(true, *F.L, *C.L, tab.P, (const T*)C.x, nullptr, (T*)F.x, (T*)F.t, nullptr,
-                         done, s));
+    GMG_CK(p_transfer<T>(true, *F.L, *C.L, tab.P, (const T*)C.x, nullptr, (T*)F.x, (T*)F.t, (T*)F.pw1,
+                         (T*)F.pw2, done, s));
+    ctx->launches += 3;
+    return SEM_OK;
   } else {
     launch_k(k_prolong_h<T>, grid1d(F.L->ndofs), kThreads, 0, s,
         F.L->nx, F.L->ny, F.L->nz, C.L->nx, C.L->ny, C.L->nz, (const T*)C.x, (T*)F.x, (T*)F.t,
@@ -893,6 +901,7 @@ void free_gmg_struct(Gmg* g) {
       cudaFree(V.sl); cudaFree(V.st); cudaFree(V.th);
     }
     cudaFree(V.b); cudaFree(V.x); cudaFree(V.t); cudaFree(V.d); cudaFree(V.invd);
+    cudaFree(V.pw1); cudaFree(V.pw2);
     cudaFree(V.dinv64);
   }
   cudaFree(g->z);
@@ -1000,6 +1009,12 @@ int build(sem_ctx* ctx, cudaStream_t s) {
     for (void** v : vecs) GMG_CK(cudaMalloc(v, es * L.ndofs));
     GMG_CK(cudaMemsetAsync(V.t, 0, es * L.ndofs, s));
     GMG_CK(cudaMalloc(&V.dinv64, sizeof(double) * L.ndofs));
+  }
+  for (size_t l = 0; l + 1 < g->lv.size(); ++l) {
+    GmgLevel& V = g->lv[l];
+    if (V.to_next != 0) continue;
+    GMG_CK(cudaMalloc(&V.pw1, es * p_transfer_scratch(*V.L, *g->lv[l + 1].L, 1)));
+    GMG_CK(cudaMalloc(&V.pw2, es * p_transfer_scratch(*V.L, *g->lv[l + 1].L, 2)));
   }
   const int64_t nf = ctx->L.ndofs;
   GMG_CK(cudaMalloc(&g->z, sizeof(double) * nf));
