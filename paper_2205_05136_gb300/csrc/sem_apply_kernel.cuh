@@ -231,7 +231,7 @@ __device__ __forceinline__ df ldsmetric(const df_pair* p) { return df(p->h, p->l
 __device__ __forceinline__ float bf16_lo(unsigned w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf16_hi(unsigned w) { return __uint_as_float(w & 0xffff0000u); }
 template <int N, typename MT, bool SHARED>
-struct MetricColumn {
+struct MetricColumn {  // component-major layouts: point by point
   using ML = MetricLayout<MT>;
   const MT* p;
   __device__ __forceinline__ MetricColumn(const MT* block, int c) : p(block + ML::at(N, c, 0, 0)) {}
@@ -411,12 +411,25 @@ __global__ void __launch_bounds__(kApplyThreads)
 #pragma unroll
       for (int k = 0; k < N; ++k) uz[k] = pa[k * N2];
       eo_line<N, true, false>(tab.D, uz, g3);
-      const MetricColumn<N, MT, STAGE> mcol(STAGE ? sM + (size_t)s * BLK : a.metric + (size_t)e * BLK, c);
+      // bf16: the column's values into registers by 64-bit loads (MetricColumn);
+      // the component-major layouts point by point from the column's first value
+      // (measured 17 % faster for the double-float kernel than through MetricColumn)
+      const MT* mblk = STAGE ? sM + (size_t)s * BLK : a.metric + (size_t)e * BLK;
+      const MetricColumn<N, MT, STAGE> mcol(mblk, ML::kColumnMajor ? c : 0);
+      const MT* mp = mblk + c;
 #pragma unroll
       for (int k = 0; k < N; ++k) {
         const T g1 = pb[k * N2], g2 = pc[k * N2];
         T gm[kMetricComps];
-        mcol.point(k, gm);
+        if constexpr (ML::kColumnMajor) {
+          mcol.point(k, gm);
+        } else {
+#pragma unroll
+          for (int cc = 0; cc < kMetricComps; ++cc) {
+            const MT* q = mp + k * N2 + cc * padded_n3(N);
+            gm[cc] = STAGE ? ldsmetric(q) : ldmetric(q);
+          }
+        }
         const T G00 = gm[0], G01 = gm[1], G02 = gm[2], G11 = gm[3], G12 = gm[4], G22 = gm[5], W = gm[6];
         pb[k * N2] = fma(G02, g3[k], fma(G01, g2, G00 * g1));
         pc[k * N2] = fma(G12, g3[k], fma(G11, g2, G01 * g1));

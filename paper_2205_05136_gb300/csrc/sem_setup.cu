@@ -242,7 +242,6 @@ __global__ void k_convert<float>(int64_t n, const double* __restrict__ in, float
     out[i] = __double2float_rn(in[i]);
 }
 
-// bf16 copy in the point-major layout: out[e][q][c] = in[e][c][q] (c < 7), out[e][q][7] = 0.
 // FP64 component-major metric -> the column-major bf16 layout (MetricLayout).
 __global__ void k_convert_columns_bf16(int64_t n, int np, const double* __restrict__ in,
                                        __nv_bfloat16* __restrict__ out) {
