@@ -105,5 +105,20 @@ __device__ __forceinline__ df_pair split_pair(double x) {
   const float l = (m * __int_as_float((s1 + 127) << 23)) * __int_as_float((s2 + 127) << 23);
   return df_pair{__uint_as_float(hb), __uint_as_float(__float_as_uint(l) ^ sign)};
 }
+
+// Exact float -> double by integer operations (subnormal floats, below 1.2e-38,
+// become zero).
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned e = (b >> 23) & 0xffu;
+  const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+  if (e == 0u) return __longlong_as_double((long long)sign);
+  const unsigned long long d =
+      sign | ((unsigned long long)(e - 127u + 1023u) << 52) | ((unsigned long long)(b & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)d);
+}
+
+// Float pair -> FP64 with one FP64 instruction (the addition).
+__device__ __forceinline__ double df_to_double(df a) { return f2d_bits(a.h) + f2d_bits(a.l); }
 #endif
 }  // namespace sem
