@@ -584,6 +584,9 @@ def run_gpu(args):
         "mixed_vs_fp64": {"speedup": speed_g, "speedup_vs_fp64_gmg": speed_g, "speedup_vs_fp64_jacobi": speed_j,
                           "vs_fp64_gmg": field_errors(fmx[0], fmx[1], fg64[0], fg64[1]),
                           "vs_fp64_jacobi": field_errors(fmx[0], fmx[1], f64[0], f64[1]),
+                          # the two FP64 solvers against each other: the part of vs_fp64_jacobi that
+                          # comes from the solvers' different iterates at rtol, not from the precision
+                          "fp64_gmg_vs_fp64_jacobi": field_errors(fg64[0], fg64[1], f64[0], f64[1]),
                           "rel_l2_u_diff": field_errors(fmx[0], fmx[1], fg64[0], fg64[1])["u_rel_l2"],
                           "note": ("speedup = FP64-GMG step time / mixed step time (same hierarchy, so the "
                                    "precision alone); u and h after warm-up + timed steps of each path from the "
