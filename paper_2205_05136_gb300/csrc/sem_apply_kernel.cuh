@@ -523,17 +523,22 @@ __global__ void __launch_bounds__(kApplyThreads)
 //     (16-byte aligned), by 16-byte cp.async;
 //   - the unit's nodal values, gathered by plain loads into registers from the
 //     map entries (loaded one unit earlier still) and stored to the stage after
-//     this unit's sweeps.  (4-byte cp.async gathers measured the same time, with
-//     10 % more shared-memory wavefronts: the shared-side write of each gather is split
-//     by the global lines it touches.)
+//     this unit's sweeps.  Each lane gathers (and later scatters) the n nodes of
+//     its z-column: for each level the lanes read consecutive map entries.
 // Two stage buffers per warp; a stage is complete after cp.async.wait_group
 // and visible to the whole warp after __syncwarp.  The grid is persistent
-// (the CTAs that are resident at once), so the pipeline runs over several units.
+// (the CTAs that are resident at once, 3 per SM), so the pipeline runs over
+// several units.
 //
 // Every lane owns one line of each sweep (G n^2 <= 32 for p <= 4).  Lanes
 // beyond the unit's G n^2 lines run the same instructions on the line of lane
 // (lane - (32 - G n^2)): their loads are broadcasts of that lane's, their
-// stores are predicated off, so no sweep needs a divergent branch.
+// stores are predicated off, so no sweep needs a divergent branch.  The unit
+// tiles use the bank-skewed placement of pipe_word, so that no x-, y- or z-line
+// access conflicts; each lane keeps the tile words of its three lines in
+// registers (80 registers, 3 CTAs per SM: at p = 4 it cut shared-memory
+// wavefronts 14 % and the mixed time step 2.7 % against the plain [k][j][i]
+// tile with 64 registers and 4 CTAs per SM).
 template <int P, typename MT>
 struct PipeCfg {
   static constexpr int N = P + 1, N2 = N * N, N3 = N2 * N;
@@ -541,17 +546,27 @@ struct PipeCfg {
   static constexpr int G = WarpCfg<P>::G;
   static constexpr int NL = G * N2;                  // lines per sweep direction
   static constexpr int UT = G * N3;                  // nodal values of a unit
-  static constexpr int UTP = (UT + 3) / 4 * 4;       // float tile padded to 16 bytes
+  static constexpr int TW = 32 * N;                  // words of a unit tile (pipe_word)
   static constexpr int MV = G * BLK;                 // metric values of a unit
-  static constexpr int LPL = (UT + 31) / 32;         // nodes per lane
   static constexpr int CH = (int)(MV * sizeof(MT) / 16);  // 16-byte chunks of a unit's metric
   // two metric stages, two nodal stages and the two work tiles of the sweeps
-  static constexpr size_t warp_bytes = 2 * (size_t)MV * sizeof(MT) + 4 * (size_t)UTP * sizeof(float);
+  static constexpr size_t warp_bytes = 2 * (size_t)MV * sizeof(MT) + 4 * (size_t)TW * sizeof(float);
   static constexpr size_t cta_bytes = kWarpsPerCta * warp_bytes;
   static_assert(NL <= 32, "a unit must have at most 32 lines per direction");
-  static_assert((MV * sizeof(MT)) % 16 == 0 && (UTP * sizeof(float)) % 16 == 0,
-                "stage buffers must stay 16-byte aligned");
+  static_assert((MV * sizeof(MT)) % 16 == 0, "stage buffers must stay 16-byte aligned");
 };
+
+// Word of node (i, j, k) of element slot s in a unit tile: row i of 32 words,
+// bank s n^2 + n ((j - i) mod n) + ((k - i) mod n).  For every sweep pattern the
+// warp's lanes run over the slots and two of (i, j, k) with the third fixed, and
+// the banks (i, j, k) -> ((j - i) mod n, (k - i) mod n) are distinct on each such
+// plane (a Latin-square placement), so no line access has a bank conflict; no
+// affine layout of the 5^3 tile does that for x-, y- and z-lines at once.
+template <int N>
+__device__ __forceinline__ int pipe_word(int s, int i, int j, int k) {
+  const int jj = j - i + (j < i ? N : 0), kk = k - i + (k < i ? N : 0);
+  return 32 * i + s * N * N + N * jj + kk;
+}
 
 __device__ __forceinline__ void cp_async_16(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
@@ -562,19 +577,17 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int K>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory"); }
 
-// Map entries of unit `unit` for this lane (node idx = lane + 32 t of the unit);
-// entries of nodes outside the mesh are 0 and never used.
+// Map entries of the lane's z-column of unit `unit`: node zc + n^2 t of the unit
+// for t < n (zc = slot s n^3 + column (i + n j)); 0 for elements past the mesh.
 template <int P, typename MT>
-__device__ __forceinline__ void pipe_load_map(const ApplyArgs<float, MT>& a, int unit, int nunits, int lane,
-                                              int (&m)[PipeCfg<P, MT>::LPL]) {
+__device__ __forceinline__ void pipe_load_map(const ApplyArgs<float, MT>& a, int unit, int nunits, int slot, int zc,
+                                              int (&m)[P + 1]) {
   using C = PipeCfg<P, MT>;
-  const int nv = unit < nunits ? min(C::UT, (a.nelem - unit * C::G) * C::N3) : 0;  // nodes present
-  const int* src = a.map + (size_t)unit * C::UT;
+  const bool present = unit < nunits && unit * C::G + slot < a.nelem;
+  const int* src = a.map + (size_t)unit * C::UT + zc;
 #pragma unroll
-  for (int t = 0; t < C::LPL; ++t) {
-    const int idx = lane + 32 * t;
-    m[t] = idx < nv ? (int)SEM_IDX(__ldg(src + idx), a.ndofs, a.dbg, kDbgGather) : 0;
-  }
+  for (int t = 0; t < C::N; ++t)
+    m[t] = present ? (int)SEM_IDX(__ldg(src + t * C::N2), a.ndofs, a.dbg, kDbgGather) : 0;
 }
 
 // Issues the cp.async copies of one unit's metric block into a stage.
@@ -596,54 +609,32 @@ __device__ __forceinline__ void pipe_issue_metric(const ApplyArgs<float, MT>& a,
   }
 }
 
-// Gathered nodal values of a unit into registers (node lane + 32 t), zero for
-// the nodes of elements past the mesh; pipe_put_gather stores them to a stage.
-template <int P, typename MT>
-__device__ __forceinline__ void pipe_gather(const ApplyArgs<float, MT>& a, int unit, int lane,
-                                            const int (&m)[PipeCfg<P, MT>::LPL], float (&v)[PipeCfg<P, MT>::LPL]) {
-  using C = PipeCfg<P, MT>;
-  const int nv = min(C::UT, (a.nelem - unit * C::G) * C::N3);
-#pragma unroll
-  for (int t = 0; t < C::LPL; ++t) {
-    const int idx = lane + 32 * t;
-    v[t] = (idx < nv) ? __ldg(a.u + m[t]) : 0.f;
-  }
-}
-template <int P, typename MT>
-__device__ __forceinline__ void pipe_put_gather(int lane, const float (&v)[PipeCfg<P, MT>::LPL], float* sU) {
-  using C = PipeCfg<P, MT>;
-#pragma unroll
-  for (int t = 0; t < C::LPL; ++t) {
-    const int idx = lane + 32 * t;
-    if (C::UT % 32 == 0 || idx < C::UT) sU[idx] = v[t];
-  }
-}
-
-// One 1-D line of n values at stride STRIDE: dst = M src (ACC: dst += M src),
+// One 1-D line of n values at tile words off[]: dst = M src (ACC: dst += M src),
 // M in even-odd form.  src may equal dst.
-template <int N, int STRIDE, bool ANTI, bool ACC, typename T>
-__device__ __forceinline__ void lane_line(const EoMat<N, T>& M, const T* src, T* dst, bool store) {
+template <int N, bool ANTI, bool ACC, typename T>
+__device__ __forceinline__ void lane_line(const EoMat<N, T>& M, const T* src, T* dst, const int (&off)[N],
+                                          bool store) {
   T in[N], out[N];
 #pragma unroll
-  for (int t = 0; t < N; ++t) in[t] = src[t * STRIDE];
+  for (int t = 0; t < N; ++t) in[t] = src[off[t]];
   if (ACC) {
 #pragma unroll
-    for (int t = 0; t < N; ++t) out[t] = dst[t * STRIDE];
+    for (int t = 0; t < N; ++t) out[t] = dst[off[t]];
   }
   eo_line<N, ANTI, ACC>(M, in, out);
 #pragma unroll
   for (int t = 0; t < N; ++t)
-    if (store) dst[t * STRIDE] = out[t];
+    if (store) dst[off[t]] = out[t];
 }
 
 template <int P, int QUAD, typename MT>
-__global__ void __launch_bounds__(kApplyThreads, 4)
+__global__ void __launch_bounds__(kApplyThreads, 3)
     sem_apply_pipe_kernel(const ApplyArgs<float, MT> a, const __grid_constant__ KTab<P + 1, float> tab,
                           int nunits) {
   pdl_trigger();
   using C = PipeCfg<P, MT>;
   using T = float;
-  constexpr int N = C::N, N2 = C::N2, N3 = C::N3, G = C::G, LPL = C::LPL, NL = C::NL;
+  constexpr int N = C::N, N2 = C::N2, N3 = C::N3, G = C::G, NL = C::NL;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int unit = blockIdx.x * kWarpsPerCta + warp;
@@ -659,76 +650,88 @@ __global__ void __launch_bounds__(kApplyThreads, 4)
   unsigned char* wb = smem_raw + (size_t)warp * C::warp_bytes;
   MT* sM0 = reinterpret_cast<MT*>(wb);
   T* sU0 = reinterpret_cast<T*>(wb + 2 * (size_t)C::MV * sizeof(MT));
-  T* sB = sU0 + 2 * C::UTP;
-  T* sC = sB + C::UTP;  // followed by the scratch lines of the lanes >= NL
+  T* sB = sU0 + 2 * C::TW;
+  T* sC = sB + C::TW;
 
-  // line offsets of this lane (of lane - (32 - NL) for the lanes >= NL, a lane of
-  // the same half-warp, so that the 64-bit metric loads of the idle lanes are
-  // broadcasts within their phase): element slot ls, line ll
+  // The lane's lines (those of lane - (32 - NL) for the lanes >= NL, a lane of the
+  // same half-warp, so that the 64-bit metric loads of the idle lanes are
+  // broadcasts within their phase): element slot ls, line ll = r + n q, which is
+  // the x-line (j, k) = (r, q), the y-line (i, k) = (r, q) and the z-line
+  // (i, j) = (r, q); their tile words for t = 0..n-1.
   static_assert(NL >= 24, "idle lanes must replay a lane of their half-warp");
   const bool act = lane < NL;
   const int lw = act ? lane : lane - (32 - NL);
-  const int ls = lw / N2, ll = lw - ls * N2;
-  const int ox = ls * N3 + ll * N;                      // x-line (j, k) = ll
-  const int oy = ls * N3 + (ll / N) * N2 + (ll % N);    // y-line (i, k): i = ll % N, k = ll / N
-  const int oz = ls * N3 + ll;                          // z-line (i, j) = ll
+  const int ls = lw / N2, ll = lw - ls * N2, r = ll % N, q = ll / N;
+  int ox[N], oy[N], oz[N];
+#pragma unroll
+  for (int t = 0; t < N; ++t) {
+    ox[t] = pipe_word<N>(ls, t, r, q);
+    oy[t] = pipe_word<N>(ls, r, t, q);
+    oz[t] = pipe_word<N>(ls, r, q, t);
+  }
+  const int zc = ls * N3 + ll;  // first node of the lane's z-column in the unit
 
-  int mc[LPL], mn[LPL], mnn[LPL];  // map entries of units j, j+1, j+2
-  pipe_load_map<P>(a, unit, nunits, lane, mc);
-  float gv[LPL];  // the next unit's gathered values, in flight during this unit's sweeps
+  int mc[N], mn[N], mnn[N];  // map entries of the lane's z-column in units j, j+1, j+2
+  pipe_load_map<P>(a, unit, nunits, ls, zc, mc);
+  float gv[N];  // the next unit's gathered values, in flight during this unit's sweeps
   pipe_issue_metric<P>(a, unit, lane, sM0);
-  pipe_gather<P>(a, unit, lane, mc, gv);
-  pipe_put_gather<P, MT>(lane, gv, sU0);
+  {
+    const bool present = unit * G + ls < a.nelem;
+#pragma unroll
+    for (int t = 0; t < N; ++t) gv[t] = present ? __ldg(a.u + mc[t]) : 0.f;
+#pragma unroll
+    for (int t = 0; t < N; ++t)
+      if (act) sU0[oz[t]] = gv[t];
+  }
   cp_async_commit();
-  pipe_load_map<P>(a, unit + tw, nunits, lane, mn);
+  pipe_load_map<P>(a, unit + tw, nunits, ls, zc, mn);
   int b = 0;
   for (; unit < nunits; unit += tw) {
     const int nxt = unit + tw;
     if (nxt < nunits) {
       pipe_issue_metric<P>(a, nxt, lane, sM0 + (b ^ 1) * C::MV);
-      pipe_gather<P>(a, nxt, lane, mn, gv);
+      const bool present = nxt * G + ls < a.nelem;
+#pragma unroll
+      for (int t = 0; t < N; ++t) gv[t] = present ? __ldg(a.u + mn[t]) : 0.f;
     }
     cp_async_commit();  // possibly empty group: keeps "all but the newest group" = stage b
-    pipe_load_map<P>(a, nxt + tw, nunits, lane, mnn);
+    pipe_load_map<P>(a, nxt + tw, nunits, ls, zc, mnn);
     cp_async_wait<1>();
     __syncwarp();
 
-    T* sA = sU0 + b * C::UTP;
+    T* sA = sU0 + b * C::TW;
     const MT* sM = sM0 + b * C::MV;
-    const int e0 = unit * G;
+    const int e = unit * G + ls;  // the lane's element
     if (QUAD == SEM_QUAD_LG) {  // values at the Gauss points
-      lane_line<N, 1, false, false>(tab.Bi, sA + ox, sB + ox, act);
+      lane_line<N, false, false>(tab.Bi, sA, sB, ox, act);
       __syncwarp();
-      lane_line<N, N, false, false>(tab.Bi, sB + oy, sC + oy, act);
+      lane_line<N, false, false>(tab.Bi, sB, sC, oy, act);
       __syncwarp();
-      lane_line<N, N2, false, false>(tab.Bi, sC + oz, sA + oz, act);
+      lane_line<N, false, false>(tab.Bi, sC, sA, oz, act);
       __syncwarp();
     }
     // reference gradient along x and y (into sB, sC)
-    lane_line<N, 1, true, false>(tab.D, sA + ox, sB + ox, act);
-    lane_line<N, N, true, false>(tab.D, sA + oy, sC + oy, act);
+    lane_line<N, true, false>(tab.D, sA, sB, ox, act);
+    lane_line<N, true, false>(tab.D, sA, sC, oy, act);
     __syncwarp();
     // z-gradient, quadrature-point stage and transposed z-sweep on the lane's column
     {
-      T* pa = sA + oz;
-      T* pb = sB + oz;
-      T* pc = sC + oz;
       T uz[N], g3[N], q3[N], m[N];
 #pragma unroll
-      for (int k = 0; k < N; ++k) uz[k] = pa[k * N2];
+      for (int k = 0; k < N; ++k) uz[k] = sA[oz[k]];
       eo_line<N, true, false>(tab.D, uz, g3);
       const MetricColumn<N, MT, true> mcol(sM + ls * C::BLK, ll);
 #pragma unroll
       for (int k = 0; k < N; ++k) {
-        const T g1 = pb[k * N2], g2 = pc[k * N2];
+        const T g1 = sB[oz[k]], g2 = sC[oz[k]];
         T gm[kMetricComps];
         mcol.point(k, gm);
         const T G00 = gm[0], G01 = gm[1], G02 = gm[2], G11 = gm[3], G12 = gm[4], G22 = gm[5], W = gm[6];
         const T q1 = fma(G02, g3[k], fma(G01, g2, G00 * g1));
         const T q2 = fma(G12, g3[k], fma(G11, g2, G01 * g1));
         if (act) {
-          pb[k * N2] = q1;
-          pc[k * N2] = q2;
+          sB[oz[k]] = q1;
+          sC[oz[k]] = q2;
         }
         q3[k] = fma(G22, g3[k], fma(G12, g2, G02 * g1));
         m[k] = (a.mass_coef * W) * uz[k];
@@ -736,46 +739,40 @@ __global__ void __launch_bounds__(kApplyThreads, 4)
       eo_line<N, true, true>(tab.Dt, q3, m);
 #pragma unroll
       for (int k = 0; k < N; ++k)
-        if (act) pa[k * N2] = m[k];
+        if (act) sA[oz[k]] = m[k];
     }
     __syncwarp();
-    lane_line<N, N, true, true>(tab.Dt, sC + oy, sA + oy, act);
+    lane_line<N, true, true>(tab.Dt, sC, sA, oy, act);
     __syncwarp();
-    lane_line<N, 1, true, true>(tab.Dt, sB + ox, sA + ox, act);
+    lane_line<N, true, true>(tab.Dt, sB, sA, ox, act);
     __syncwarp();
     if (QUAD == SEM_QUAD_LG) {  // back from the Gauss points to the nodes
-      lane_line<N, 1, false, false>(tab.Bit, sA + ox, sB + ox, act);
+      lane_line<N, false, false>(tab.Bit, sA, sB, ox, act);
       __syncwarp();
-      lane_line<N, N, false, false>(tab.Bit, sB + oy, sC + oy, act);
+      lane_line<N, false, false>(tab.Bit, sB, sC, oy, act);
       __syncwarp();
-      lane_line<N, N2, false, false>(tab.Bit, sC + oz, sA + oz, act);
+      lane_line<N, false, false>(tab.Bit, sC, sA, oz, act);
       __syncwarp();
     }
-    // scatter-add y += P_e^T y_e
+    // scatter-add y += P_e^T y_e along the lane's z-column
     const T sc = a.scale_out ? a.out_scale : T(1);
-    if (a.yloc != nullptr) {  // deterministic mode: element-local results
+    if (act && e < a.nelem) {
+      if (a.yloc != nullptr) {  // deterministic mode: element-local results
 #pragma unroll
-      for (int t = 0; t < LPL; ++t) {
-        const int idx = lane + 32 * t;
-        if (idx < C::UT && e0 + idx / N3 < a.nelem) a.yloc[(size_t)e0 * N3 + idx] = sA[idx] * sc;
-      }
-    } else if (e0 + G <= a.nelem) {
+        for (int t = 0; t < N; ++t) a.yloc[(size_t)unit * C::UT + zc + t * N2] = sA[oz[t]] * sc;
+      } else {
 #pragma unroll
-      for (int t = 0; t < LPL; ++t) {
-        const int idx = lane + 32 * t;
-        if (C::UT % 32 == 0 || idx < C::UT) atomicAdd(a.y + mc[t], sA[idx] * sc);
-      }
-    } else {
-#pragma unroll
-      for (int t = 0; t < LPL; ++t) {
-        const int idx = lane + 32 * t;
-        if (idx < C::UT && e0 + idx / N3 < a.nelem) atomicAdd(a.y + mc[t], sA[idx] * sc);
+        for (int t = 0; t < N; ++t) atomicAdd(a.y + mc[t], sA[oz[t]] * sc);
       }
     }
-    if (nxt < nunits) pipe_put_gather<P, MT>(lane, gv, sU0 + (b ^ 1) * C::UTP);
+    if (nxt < nunits) {
+#pragma unroll
+      for (int t = 0; t < N; ++t)
+        if (act) sU0[(b ^ 1) * C::TW + oz[t]] = gv[t];
+    }
     __syncwarp();  // stage b is refilled by the next iteration's issue
 #pragma unroll
-    for (int t = 0; t < LPL; ++t) {
+    for (int t = 0; t < N; ++t) {
       mc[t] = mn[t];
       mn[t] = mnn[t];
     }
