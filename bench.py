@@ -60,8 +60,8 @@ FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64: 152 SMs x 2 DFMA/clk x 2 flop x ~
 # was taken from: a figure whose kernel sources have changed since is reported as
 # null (kernel_source_hash below).
 NCU_TRAFFIC = {(4, "LGL"): (273.041664e6 + 13.248e6, "apply")}
-NCU_TRAFFIC_SMOOTHER = {(4, "LGL", "bf16"): (88.761344e6 + 2.063616e6, "apply")}
-NCU_SOURCE_HASH = {"apply": "2de4ceb90d767cc4"}
+NCU_TRAFFIC_SMOOTHER = {(4, "LGL", "bf16"): (88.764160e6 + 2.301184e6, "apply")}
+NCU_SOURCE_HASH = {"apply": "4d91686559f13864"}
 KERNEL_SOURCES = {"apply": ("sem_apply_kernel.cuh", "sem_apply_fp32.cu", "sem_apply_fp64.cu",
                             "sem_internal.cuh")}
 
