@@ -358,6 +358,7 @@ int adjoint_grad(sem_ctx* ctx, const double* trace_bar, double* g_sl, double* g_
     ADJ_CK(cudaMemcpyAsync(tp->seg_u + n, ck, bytes, cudaMemcpyDeviceToDevice, s));        // u^start
     ADJ_CK(cudaMemcpyAsync(tp->seg_h, ck + 3 * n, bytes, cudaMemcpyDeviceToDevice, s));
     ADJ_CK(cudaMemcpyAsync(tp->seg_h + n, ck + 2 * n, bytes, cudaMemcpyDeviceToDevice, s));
+    ctx->carry.valid = false;  // the state was restored from a checkpoint
     for (int64_t k = start; k < stop; ++k) {
       int rc = time_steps(ctx, st, dt, 1, rtol, atol, maxit, precond, nullptr, s);
       if (rc != SEM_OK) return rc;

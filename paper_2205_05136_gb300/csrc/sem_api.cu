@@ -25,6 +25,17 @@ namespace {
 
 thread_local std::string g_create_err;
 
+// Entry points that change the operator, the preconditioner, a state or the CG
+// workspace end the carried initial residual of consecutive time steps.
+void invalidate_carry(sem_ctx* ctx) {
+  if (ctx != nullptr) ctx->carry.valid = false;
+}
+// ... also on the way out, for entry points that step states of their own.
+struct CarryScope {
+  sem_ctx* ctx;
+  ~CarryScope() { invalidate_carry(ctx); }
+};
+
 struct DeviceGuard {
   int prev = -1;
   explicit DeviceGuard(int d) {
@@ -277,6 +288,7 @@ int sem_dof_coords(sem_ctx* ctx, double* xyz, void* stream) {
 int sem_set_tissue(sem_ctx* ctx, const double* sigma_l, const double* sigma_t,
                    const double* theta, void* stream) {
   CK_CTX(ctx);
+  invalidate_carry(ctx);
   DeviceGuard guard(ctx->device);
   CK_DEV(sigma_l, "sigma_l");
   CK_DEV(sigma_t, "sigma_t");
@@ -327,6 +339,7 @@ int sem_apply(sem_ctx* ctx, double alpha, double beta, const void* u, void* y, i
 
 int sem_set_operator_precision(sem_ctx* ctx, int precision) {
   CK_CTX(ctx);
+  invalidate_carry(ctx);
   if (precision != SEM_PREC_FP64 && precision != SEM_PREC_DF64)
     return fail(ctx, SEM_ERR_ARG, "operator precision must be SEM_PREC_FP64 or SEM_PREC_DF64");
   DeviceGuard guard(ctx->device);
@@ -338,6 +351,7 @@ int sem_set_operator_precision(sem_ctx* ctx, int precision) {
 
 int sem_set_deterministic(sem_ctx* ctx, int enable) {
   CK_CTX(ctx);
+  invalidate_carry(ctx);
   DeviceGuard guard(ctx->device);
   cudaDeviceSynchronize();
   if (enable && ctx->det_scratch == nullptr) {
@@ -368,6 +382,7 @@ int sem_cg_solve(sem_ctx* ctx, double alpha, const double* b, double* x, double 
                  double atol, int maxit, int precond, int* iters, double* final_res,
                  void* stream) {
   CK_CTX(ctx);
+  invalidate_carry(ctx);
   DeviceGuard guard(ctx->device);
   CK_DEV(b, "b");
   CK_DEV(x, "x");
@@ -427,6 +442,7 @@ int sem_state_create(sem_ctx* ctx, sem_state** out) {
 
 int sem_state_destroy(sem_state* st) {
   if (st == nullptr) return SEM_OK;
+  invalidate_carry(st->ctx);
   DeviceGuard guard(st->ctx->device);
   cudaDeviceSynchronize();
   for (int j = 0; j < 3; ++j) { cudaFree(st->U[j]); cudaFree(st->H[j]); }
@@ -480,6 +496,7 @@ int sem_state_get_activation(sem_state* st, double* tau, double* dudt_max, void*
 int sem_state_set(sem_state* st, const double* u0, const double* h0, void* stream) {
   if (st == nullptr) return SEM_ERR_ARG;
   sem_ctx* ctx = st->ctx;
+  invalidate_carry(ctx);
   DeviceGuard guard(ctx->device);
   CK_DEV(u0, "u0");
   CK_DEV(h0, "h0");
@@ -516,6 +533,7 @@ int sem_state_restore(sem_state* st, const double* u, const double* u_prev, cons
                       const double* h_prev, int64_t n, void* stream) {
   if (st == nullptr) return SEM_ERR_ARG;
   sem_ctx* ctx = st->ctx;
+  invalidate_carry(ctx);
   DeviceGuard guard(ctx->device);
   if (n < 0) return fail(ctx, SEM_ERR_ARG, "n must be >= 0");
   CK_DEV(u, "u");
@@ -562,6 +580,8 @@ int sem_step_host(sem_ctx* ctx, double* u, double* u_prev, double* h, double* h_
                   double dt, double rtol, double atol, int maxit, int precond, sem_stats* stats,
                   void* stream) {
   CK_CTX(ctx);
+  invalidate_carry(ctx);
+  CarryScope carry_scope{ctx};
   DeviceGuard guard(ctx->device);
   if (!is_host_ptr(u) || !is_host_ptr(u_prev) || !is_host_ptr(h) || !is_host_ptr(h_prev))
     return fail(ctx, SEM_ERR_ARG, "u, u_prev, h, h_prev must be host memory");
@@ -611,6 +631,8 @@ int sem_step_host_out(sem_ctx* ctx, const double* u, const double* u_prev, const
                       const double* h_prev, double* u_next, double* h_next, int64_t n, double dt,
                       double rtol, double atol, int maxit, int precond, sem_stats* stats, void* stream) {
   CK_CTX(ctx);
+  invalidate_carry(ctx);
+  CarryScope carry_scope{ctx};
   DeviceGuard guard(ctx->device);
   const void* all[6] = {u, u_prev, h, h_prev, u_next, h_next};
   for (const void* p : all)
@@ -668,6 +690,7 @@ int sem_step_host_out(sem_ctx* ctx, const double* u, const double* u_prev, const
 
 int sem_set_gmg(sem_ctx* ctx, int degree, int coarse_degree, int min_coarse_dofs, int precision) {
   CK_CTX(ctx);
+  invalidate_carry(ctx);
   if (degree < 1 || degree > 20 || coarse_degree < 1 || coarse_degree > 200 || min_coarse_dofs < 1)
     return fail(ctx, SEM_ERR_ARG, "bad multigrid parameters");
   if (precision != SEM_PREC_FP64 && precision != SEM_PREC_FP32 && precision != SEM_PREC_FP32_BF16 &&
@@ -687,6 +710,7 @@ int sem_set_gmg(sem_ctx* ctx, int degree, int coarse_degree, int min_coarse_dofs
 
 int sem_vcycle(sem_ctx* ctx, double alpha, const double* r, double* z, void* stream) {
   CK_CTX(ctx);
+  invalidate_carry(ctx);
   DeviceGuard guard(ctx->device);
   CK_DEV(r, "r");
   CK_DEV(z, "z");
@@ -696,6 +720,7 @@ int sem_vcycle(sem_ctx* ctx, double alpha, const double* r, double* z, void* str
 
 int sem_debug_set_map_entry(sem_ctx* ctx, int64_t entry, int value, int* previous) {
   CK_CTX(ctx);
+  invalidate_carry(ctx);
 #ifdef SEM_DEBUG
   const Level& L = ctx->L;
   if (entry < 0 || entry >= (int64_t)L.nelem * L.n * L.n * L.n)
@@ -727,6 +752,7 @@ int sem_forward_record(sem_ctx* ctx, sem_state* st, double dt, int nsteps, int c
                        const int* sensors, int nsens, double* traces, double rtol, double atol,
                        int maxit, int precond, sem_stats* stats, void* stream) {
   CK_CTX(ctx);
+  invalidate_carry(ctx);
   if (st == nullptr || st->ctx != ctx) return fail(ctx, SEM_ERR_ARG, "state does not belong to ctx");
   if (!(dt > 0.0) || nsteps < 1 || checkpoint_every < 1 || nsens < 1 || maxit < 0 ||
       !(rtol >= 0.0) || !(atol >= 0.0))
@@ -754,6 +780,8 @@ int sem_adjoint_grad(sem_ctx* ctx, const double* trace_bar, double* g_sigma_l, d
                      double* g_theta, double rtol, double atol, int maxit, int precond,
                      sem_stats* stats, void* stream) {
   CK_CTX(ctx);
+  invalidate_carry(ctx);
+  CarryScope carry_scope{ctx};
   if (maxit < 0 || !(rtol >= 0.0) || !(atol >= 0.0)) return fail(ctx, SEM_ERR_ARG, "bad solver parameters");
   DeviceGuard guard(ctx->device);
   CK_DEV(trace_bar, "trace_bar");

@@ -14,6 +14,7 @@ struct Workspace {
   bool ready = false;
   double *r = nullptr, *z = nullptr, *p = nullptr, *Ap = nullptr, *invdiag = nullptr;
   double *b = nullptr, *g = nullptr;
+  double* Ax = nullptr;      // A x of the last time step's solution (its b - r), see sem_ctx::carry
   df_pair* p2 = nullptr;     // p split into float pairs for the double-float operator's gather
   double inv_alpha = -1.0;   // alpha for which invdiag holds 1 / diag(alpha M + K)
   CgScalars* cg = nullptr;   // device
@@ -36,6 +37,11 @@ struct Timing {
   int64_t smoother_count = 0;
 };
 
+}  // namespace sem
+
+namespace sem {
+// Time steps between true initial residuals when the residual is carried (sem_ctx::carry).
+constexpr int kCarrySteps = 50;
 }  // namespace sem
 
 struct sem_ctx {
@@ -65,6 +71,22 @@ struct sem_ctx {
   // device address of sem_apply_dot_static's static scratch array in the CUDA
   // context this sem_ctx was created in (looked up on that entry point's first call)
   double* static_scratch = nullptr;
+  // Initial residual of the next time step without an operator apply: each
+  // step's solve starts from x0 = u^n, the previous step's solution, with the
+  // same A (alpha and tissue unchanged), and that solve ended with
+  // r = b_prev - A u^n, so A x0 = b_prev - r (kept in ws.Ax) and
+  // r0 = b - A x0.  Valid for the state `st` at step `n` while nothing but time
+  // steps touched the context (every other mutating entry point clears it);
+  // refreshed by a real apply every kCarrySteps steps, which bounds the drift of
+  // the recursively updated residual.
+  struct ResidualCarry {
+    bool valid = false;
+    const sem_state* st = nullptr;
+    int64_t n = -1;
+    double alpha = 0.0;
+    int precond = -1;
+    int age = 0;
+  } carry;
   // sem_step_host_out: a second stream for the copy of h^{n+1} to the host,
   // which the ionic update writes first thing in the step and which then
   // overlaps the linear solve (time_steps issues it when h_dst is set)
@@ -94,9 +116,11 @@ namespace sem {
 int ensure_workspace(sem_ctx* ctx);
 int apply_fp64(sem_ctx* ctx, double alpha, double beta, const double* u, double* y,
                cudaStream_t s);
+// ax0: when set, A x for the initial residual r = b - A x is taken from it (and it
+// is overwritten) instead of an operator apply.
 int cg_solve(sem_ctx* ctx, double alpha, const double* b, double* x, double rtol, double atol,
              int maxit, int precond, int* iters, double* final_res, sem_stats* stats,
-             cudaStream_t s);
+             cudaStream_t s, double* ax0 = nullptr);
 int time_steps(sem_ctx* ctx, sem_state* st, double dt, int nsteps, double rtol, double atol,
                int maxit, int precond, sem_stats* stats, cudaStream_t s);
 int fail(sem_ctx* ctx, int code, const std::string& msg);
@@ -117,7 +141,8 @@ cudaError_t launch_operator(sem_ctx* ctx, const ApplyArgs64& a, cudaStream_t s);
 void gmg_free(sem_ctx* ctx);
 int gmg_vcycle(sem_ctx* ctx, double alpha, const double* r, double* z, cudaStream_t s);
 int gmg_pcg(sem_ctx* ctx, double alpha, const double* b, double* x, double rtol, double atol,
-            int maxit, int* iters, double* final_res, sem_stats* stats, cudaStream_t s);
+            int maxit, int* iters, double* final_res, sem_stats* stats, cudaStream_t s,
+            double* ax0 = nullptr);
 int gmg_info(sem_ctx* ctx, double alpha, int max_levels, int* nlevels, int* p, int* dims,
              int64_t* ndofs, double* lambda_max, cudaStream_t s);
 

@@ -67,7 +67,8 @@ struct Gmg {
     double alpha = 0.0;
     double rtol = 0.0, atol = 0.0;
     cudaGraphExec_t init = nullptr, iter = nullptr;
-    int64_t init_kernels = 0, iter_kernels = 0;
+    cudaGraphExec_t init_carried = nullptr;  // set-up from the carried A x (ws.Ax)
+    int64_t init_kernels = 0, iter_kernels = 0, init_carried_kernels = 0;
     int last_iters = 0;  // iterations the previous solve with these graphs took
   };
   Graphs graphs[16];
@@ -908,6 +909,7 @@ void free_gmg_struct(Gmg* g) {
   for (auto& gr : g->graphs) {
     if (gr.init) cudaGraphExecDestroy(gr.init);
     if (gr.iter) cudaGraphExecDestroy(gr.iter);
+    if (gr.init_carried) cudaGraphExecDestroy(gr.init_carried);
   }
   if (g->capture) cudaStreamDestroy(g->capture);
   if (g->ev0) cudaEventDestroy(g->ev0);
@@ -1055,17 +1057,20 @@ int64_t count_kernels(cudaGraph_t graph) {
 // z = V(r), beta, p = z + beta p, A p with alpha = r.z / p.Ap, x and r updated,
 // convergence test.  The iteration ends with the test, so the host launches no
 // V-cycle after convergence.
+// carried: A x is read from ws.Ax (the last time step's b - r) instead of
+// applied; ws.Ap is then already zero (every PCG iteration leaves it zero).
 template <typename T>
 int pcg_init_seq(sem_ctx* ctx, Gmg& g, double alpha, const double* b, const double* x, double rtol,
-                 double atol, cudaStream_t s) {
+                 double atol, bool carried, cudaStream_t s) {
   Workspace& w = ctx->ws;
   Level& L = ctx->L;
   const int64_t n = L.ndofs;
   const int gr = grid1d(n);
   T* b0 = (T*)g.lv[0].b;
   const int stride = g.partial_len;
-  launch_k(k_zero<double>, gr, kThreads, 0, s, n, w.Ap, nullptr);
-  {
+  double* ax = carried ? w.Ax : w.Ap;
+  if (!carried) {
+    launch_k(k_zero<double>, gr, kThreads, 0, s, n, w.Ap, nullptr);
     ApplyArgs64 a{};
     a.map = L.map; a.metric = L.metric; a.u = x; a.y = w.Ap; a.nelem = L.nelem;
     a.mass_coef = alpha; a.out_scale = 1.0; a.scale_out = 0;
@@ -1073,10 +1078,10 @@ int pcg_init_seq(sem_ctx* ctx, Gmg& g, double alpha, const double* b, const doub
     GMG_CK(launch_operator(ctx, a, s));
   }
   if (aligned16(b))
-    launch_k(k_fpcg_init<T, true>, gr, kThreads, 0, s, n, b, w.Ap, w.r, b0, w.cg, g.partials, stride, g.tickets,
+    launch_k(k_fpcg_init<T, true>, gr, kThreads, 0, s, n, b, ax, w.r, b0, w.cg, g.partials, stride, g.tickets,
                                                rtol, atol);
   else
-    launch_k(k_fpcg_init<T, false>, gr, kThreads, 0, s, n, b, w.Ap, w.r, b0, w.cg, g.partials, stride, g.tickets,
+    launch_k(k_fpcg_init<T, false>, gr, kThreads, 0, s, n, b, ax, w.r, b0, w.cg, g.partials, stride, g.tickets,
                                                 rtol, atol);
   GMG_CK(cudaGetLastError());
   return SEM_OK;
@@ -1131,12 +1136,13 @@ int get_graphs(sem_ctx* ctx, Gmg& g, double alpha, const double* b, double* x, d
   g.next_graph = (g.next_graph + 1) % 16;
   if (gr.init) { cudaGraphExecDestroy(gr.init); gr.init = nullptr; }
   if (gr.iter) { cudaGraphExecDestroy(gr.iter); gr.iter = nullptr; }
+  if (gr.init_carried) { cudaGraphExecDestroy(gr.init_carried); gr.init_carried = nullptr; }
   cudaStream_t cs = g.capture;
   const int64_t l0 = ctx->launches;
-  for (int which = 0; which < 2; ++which) {
+  for (int which = 0; which < 3; ++which) {
     GMG_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    int rc = which == 0 ? pcg_init_seq<T>(ctx, g, alpha, b, x, rtol, atol, cs)
-                        : pcg_iter_seq<T>(ctx, g, alpha, x, cs);
+    int rc = which == 1 ? pcg_iter_seq<T>(ctx, g, alpha, x, cs)
+                        : pcg_init_seq<T>(ctx, g, alpha, b, x, rtol, atol, which == 2, cs);
     cudaGraph_t graph = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
     if (rc != SEM_OK) {
@@ -1150,7 +1156,8 @@ int get_graphs(sem_ctx* ctx, Gmg& g, double alpha, const double* b, double* x, d
     cudaGraphDestroy(graph);
     if (ei != cudaSuccess) return cuda_fail(ctx, ei, "cudaGraphInstantiate");
     if (which == 0) { gr.init = exec; gr.init_kernels = nk; }
-    else { gr.iter = exec; gr.iter_kernels = nk; }
+    else if (which == 1) { gr.iter = exec; gr.iter_kernels = nk; }
+    else { gr.init_carried = exec; gr.init_carried_kernels = nk; }
   }
   ctx->launches = l0;  // capture launched nothing; replays are counted
   gr.x = x;
@@ -1164,13 +1171,14 @@ int get_graphs(sem_ctx* ctx, Gmg& g, double alpha, const double* b, double* x, d
 
 template <typename T>
 int pcg_t(sem_ctx* ctx, Gmg& g, double alpha, const double* b, double* x, double rtol,
-          double atol, int maxit, int* iters, double* final_res, sem_stats* stats, cudaStream_t s) {
+          double atol, int maxit, int* iters, double* final_res, sem_stats* stats, bool carried,
+          cudaStream_t s) {
   Workspace& w = ctx->ws;
   Gmg::Graphs* gr = nullptr;
   int rc = get_graphs<T>(ctx, g, alpha, b, x, rtol, atol, &gr);
   if (rc != SEM_OK) return rc;
-  GMG_CK(cudaGraphLaunch(gr->init, s));
-  ctx->launches += gr->init_kernels;
+  GMG_CK(cudaGraphLaunch(carried ? gr->init_carried : gr->init, s));
+  ctx->launches += carried ? gr->init_carried_kernels : gr->init_kernels;
   Timing& tm = ctx->timing;
   bool done_h = false;
   int launched = 0;
@@ -1233,7 +1241,9 @@ void gmg_free(sem_ctx* ctx) {
 }
 
 int gmg_pcg(sem_ctx* ctx, double alpha, const double* b, double* x, double rtol, double atol,
-            int maxit, int* iters, double* final_res, sem_stats* stats, cudaStream_t s) {
+            int maxit, int* iters, double* final_res, sem_stats* stats, cudaStream_t s, double* ax0) {
+  // the carried A x is always the workspace's (captured into the set-up graph)
+  if (ax0 != nullptr && ax0 != ctx->ws.Ax) return fail(ctx, SEM_ERR_ARG, "carried A x must be the workspace's");
   int rc = ensure_workspace(ctx);
   if (rc != SEM_OK) return rc;
   if ((rc = build(ctx, s)) != SEM_OK) return rc;
@@ -1241,8 +1251,8 @@ int gmg_pcg(sem_ctx* ctx, double alpha, const double* b, double* x, double rtol,
   Gmg& g = *ctx->gmg;
   if ((rc = set_alpha(ctx, g, alpha, s)) != SEM_OK) return rc;
   if (g.precision == SEM_PREC_FP64)
-    return pcg_t<double>(ctx, g, alpha, b, x, rtol, atol, maxit, iters, final_res, stats, s);
-  return pcg_t<float>(ctx, g, alpha, b, x, rtol, atol, maxit, iters, final_res, stats, s);
+    return pcg_t<double>(ctx, g, alpha, b, x, rtol, atol, maxit, iters, final_res, stats, ax0 != nullptr, s);
+  return pcg_t<float>(ctx, g, alpha, b, x, rtol, atol, maxit, iters, final_res, stats, ax0 != nullptr, s);
 }
 
 int gmg_vcycle(sem_ctx* ctx, double alpha, const double* r, double* z, cudaStream_t s) {
