@@ -30,6 +30,7 @@
 
 #include "sem_apply_kernel.cuh"
 #include "sem_context.cuh"
+#include "sem_dfmath.cuh"
 
 namespace sem {
 
@@ -606,6 +607,205 @@ __global__ void k_fpcg_xr(int64_t n, double* __restrict__ x, const double* __res
   }
 }
 
+// ---- the same flexible PCG with the double-float operator: r and p are kept
+// as float pairs, z as the V-cycle's own values (type T), and their updates and
+// inner products run in double-float arithmetic on the FP32 pipe; only x, the
+// caller's FP64 solution, is updated by FP64 instructions (one DFMA and one
+// addition per entry).  GB300 issues two FP64 operations per clock per SM, which
+// bound the FP64 forms of these kernels (FP64 pipe 76 % busy).
+
+// double-float value of a T (exact for float)
+__device__ __forceinline__ df df_of(float v) { return df(v, 0.f); }
+__device__ __forceinline__ df df_of(double v) { return dfd(v); }
+// T-rounded high part for the V-cycle's right-hand side
+template <typename T> __device__ __forceinline__ T t_of(df v);
+template <> __device__ __forceinline__ float t_of<float>(df v) { return v.h; }
+template <> __device__ __forceinline__ double t_of<double>(df v) { return df_to_double(v); }
+
+// Block sum of double-float values: the warps add in double-float (FP32
+// shuffles), each warp's sum becomes a double once, and warp 0 adds those.
+__device__ __forceinline__ double block_sum_df(df v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h = __shfl_down_sync(0xffffffffu, v.h, o), l = __shfl_down_sync(0xffffffffu, v.l, o);
+    v = v + df(h, l);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = (double)v.h + (double)v.l;
+  __syncthreads();
+  double d = 0.0;
+  if (warp == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    d = (lane < nw) ? red[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+  }
+  return d;
+}
+
+// grid_sums_k with double-float per-thread values.
+template <int K>
+__device__ __forceinline__ bool grid_sums_df(df (&v)[K], double* partials, int stride, unsigned int* ticket,
+                                             double (&tot)[K]) {
+  __shared__ double red[K][32];
+  __shared__ bool is_last;
+  double bs[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) bs[k] = block_sum_df(v[k], red[k]);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) partials[k * stride + blockIdx.x] = bs[k];
+    __threadfence();
+    const unsigned int t = atomicAdd(ticket, 1u);
+    is_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+      s += ((volatile double*)partials)[k * stride + b];
+    tot[k] = block_sum(s, red[k]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *ticket = 0u;
+  return threadIdx.x == 0;
+}
+
+// r = b - A x, b0 = r; r.r, b.b; stopping threshold.  A x is the FP64 result of
+// an apply in Ap (zeroed here), or the carried float pairs in ax2 (Ap is then
+// already zero).
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    k_dfpcg_init(int64_t n, const double* __restrict__ b, double* __restrict__ Ap,
+                 const df_pair* __restrict__ ax2, df_pair* __restrict__ r2, T* __restrict__ b0, CgScalars* cg,
+                 double* partials, int stride, unsigned int* ticket, double rtol, double atol) {
+  pdl_entry();
+  df v[2] = {df(0.f, 0.f), df(0.f, 0.f)};
+#pragma unroll 1
+  GRID_LOOP(i, n) {
+    const df bd = dfd(b[i]);
+    df ax;
+    if (ax2 != nullptr) {
+      const df_pair a = ax2[i];
+      ax = df(a.h, a.l);
+    } else {
+      ax = dfd(Ap[i]);
+      Ap[i] = 0.0;
+    }
+    const df r = dfnorm(bd - ax);
+    r2[i] = df_pair{r.h, r.l};
+    b0[i] = t_of<T>(r);
+    v[0] = fma(r, r, v[0]);
+    v[1] = fma(bd, bd, v[1]);
+  }
+  double tot[2];
+  if (grid_sums_df<2>(v, partials, stride, ticket, tot)) {
+    cg->rr = tot[0];
+    cg->bb = tot[1];
+    cg->tol2 = fmax(rtol * rtol * tot[1], atol * atol);
+    cg->iters = 0;
+    cg->status = 0;
+    const bool finite = isfinite(tot[0]) && isfinite(tot[1]);
+    if (!finite) cg->status = SEM_ERR_NONFINITE;
+    cg->done = (!finite || tot[0] <= cg->tol2) ? 1 : 0;
+  }
+}
+
+// z_new = x0 (kept in zs, which holds z_old on entry); first iteration: p = z_new,
+// rz = r.z_new; else beta = (r.z_new - r.z_old) / rz, rz = r.z_new.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    k_dfpcg_z(int64_t n, const T* __restrict__ x0, T* __restrict__ zs, const df_pair* __restrict__ r2,
+              df_pair* __restrict__ p2, CgScalars* cg, double* partials, int stride, unsigned int* ticket) {
+  pdl_entry();
+  if (cg->done) return;
+  const bool first = cg->iters == 0;
+  df v[2] = {df(0.f, 0.f), df(0.f, 0.f)};
+  if (first) {
+#pragma unroll 1
+    GRID_LOOP(i, n) {
+      const T z = x0[i];
+      const df_pair rp = r2[i];
+      const df zd = df_of(z);
+      v[0] = fma(df(rp.h, rp.l), zd, v[0]);
+      p2[i] = df_pair{zd.h, zd.l};
+      zs[i] = z;
+    }
+  } else {
+#pragma unroll 1
+    GRID_LOOP(i, n) {
+      const T z = x0[i], zo = zs[i];
+      const df_pair rp = r2[i];
+      const df r(rp.h, rp.l);
+      v[0] = fma(r, df_of(z), v[0]);
+      v[1] = fma(r, df_of(zo), v[1]);
+      zs[i] = z;
+    }
+  }
+  double tot[2];
+  if (grid_sums_df<2>(v, partials, stride, ticket, tot)) {
+    cg->beta = first ? 0.0 : (tot[0] - tot[1]) / cg->rz;
+    cg->rz = tot[0];
+    if (!isfinite(tot[0]) || !isfinite(tot[1])) {
+      cg->status = SEM_ERR_NONFINITE;
+      cg->done = 1;
+    }
+  }
+}
+
+// p = z + beta p (float pairs)
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    k_dfpcg_p(int64_t n, const T* __restrict__ zs, df_pair* __restrict__ p2, const CgScalars* cg) {
+  pdl_entry();
+  if (cg->done || cg->iters == 0) return;  // first iteration: k_dfpcg_z set p = z
+  const df beta = dfd(cg->beta);
+#pragma unroll 1
+  GRID_LOOP(i, n) {
+    const df_pair pp = p2[i];
+    const df pn = dfnorm(fma(beta, df(pp.h, pp.l), df_of(zs[i])));
+    p2[i] = df_pair{pn.h, pn.l};
+  }
+}
+
+// x += alpha p (FP64), r -= alpha Ap, Ap = 0, b0 = r; r.r; convergence.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    k_dfpcg_xr(int64_t n, double* __restrict__ x, const df_pair* __restrict__ p2, double* __restrict__ Ap,
+               df_pair* __restrict__ r2, T* __restrict__ b0, CgScalars* cg, double* partials, int stride,
+               unsigned int* ticket) {
+  pdl_entry();
+  if (cg->done) return;
+  const double alpha = cg->alpha;
+  const df nalpha = dfneg(dfd(alpha));
+  df v[1] = {df(0.f, 0.f)};
+#pragma unroll 1
+  GRID_LOOP(i, n) {
+    const df_pair pp = p2[i];
+    x[i] = fma(alpha, df_to_double(df(pp.h, pp.l)), x[i]);
+    const df_pair rp = r2[i];
+    const df r = dfnorm(fma(nalpha, dfd(Ap[i]), df(rp.h, rp.l)));
+    r2[i] = df_pair{r.h, r.l};
+    Ap[i] = 0.0;
+    b0[i] = t_of<T>(r);
+    v[0] = fma(r, r, v[0]);
+  }
+  double tot[1];
+  if (grid_sums_df<1>(v, partials, stride, ticket, tot)) {
+    cg->rr = tot[0];
+    cg->iters += 1;
+    if (!isfinite(tot[0]) || !isfinite(alpha)) {
+      cg->status = SEM_ERR_NONFINITE;
+      cg->done = 1;
+    } else if (tot[0] <= cg->tol2) {
+      cg->done = 1;
+    }
+  }
+}
+
 template <typename T>
 __global__ void k_to_level0(int64_t n, const double* __restrict__ r, T* __restrict__ b0) {
   pdl_entry();
@@ -1077,7 +1277,11 @@ int pcg_init_seq(sem_ctx* ctx, Gmg& g, double alpha, const double* b, const doub
     a.yloc = ctx->deterministic ? ctx->det_scratch : nullptr;
     GMG_CK(launch_operator(ctx, a, s));
   }
-  if (aligned16(b))
+  if (ctx->op_precision == SEM_PREC_DF64)  // r kept as float pairs in ws.r, carried A x as pairs in ws.Ax
+    launch_k(k_dfpcg_init<T>, gr, kThreads, 0, s, n, b, w.Ap,
+             carried ? reinterpret_cast<const df_pair*>(w.Ax) : nullptr, reinterpret_cast<df_pair*>(w.r), b0,
+             w.cg, g.partials, stride, g.tickets, rtol, atol);
+  else if (aligned16(b))
     launch_k(k_fpcg_init<T, true>, gr, kThreads, 0, s, n, b, ax, w.r, b0, w.cg, g.partials, stride, g.tickets,
                                                rtol, atol);
   else
@@ -1098,10 +1302,18 @@ int pcg_iter_seq(sem_ctx* ctx, Gmg& g, double alpha, double* x, cudaStream_t s) 
   int rc = vcycle(ctx, g, done, s, true);
   if (rc != SEM_OK) return rc;
   // the double-float operator gathers p as the float pairs the p kernels write
-  df_pair* p2 = ctx->op_precision == SEM_PREC_DF64 ? w.p2 : nullptr;
-  launch_k(k_fpcg_z<T>, gr, kThreads, 0, s, n, (const T*)g.lv[0].x, g.z, w.r, w.p, p2, w.cg, g.partials,
-                                      stride, g.tickets + 1);
-  launch_k(k_fpcg_p, gr, kThreads, 0, s, n, g.z, w.p, p2, w.cg);
+  const bool dfop = ctx->op_precision == SEM_PREC_DF64;
+  df_pair* p2 = dfop ? w.p2 : nullptr;
+  df_pair* r2 = reinterpret_cast<df_pair*>(w.r);
+  if (dfop) {
+    launch_k(k_dfpcg_z<T>, gr, kThreads, 0, s, n, (const T*)g.lv[0].x, reinterpret_cast<T*>(g.z), r2, p2, w.cg,
+             g.partials, stride, g.tickets + 1);
+    launch_k(k_dfpcg_p<T>, gr, kThreads, 0, s, n, reinterpret_cast<const T*>(g.z), p2, w.cg);
+  } else {
+    launch_k(k_fpcg_z<T>, gr, kThreads, 0, s, n, (const T*)g.lv[0].x, g.z, w.r, w.p, p2, w.cg, g.partials,
+             stride, g.tickets + 1);
+    launch_k(k_fpcg_p, gr, kThreads, 0, s, n, g.z, w.p, p2, w.cg);
+  }
   GMG_CK(cudaGetLastError());
   ApplyArgs64 ap{};
   ap.map = L.map; ap.metric = L.metric; ap.u = w.p; ap.y = w.Ap; ap.nelem = L.nelem;
@@ -1112,7 +1324,10 @@ int pcg_iter_seq(sem_ctx* ctx, Gmg& g, double alpha, double* x, cudaStream_t s) 
   GMG_CK(cudaEventRecordWithFlags(g.ev0, s, cudaEventRecordExternal));
   GMG_CK(launch_operator(ctx, ap, s));
   GMG_CK(cudaEventRecordWithFlags(g.ev1, s, cudaEventRecordExternal));
-  if (aligned16(x))
+  if (dfop)
+    launch_k(k_dfpcg_xr<T>, gr, kThreads, 0, s, n, x, p2, w.Ap, r2, (T*)g.lv[0].b, w.cg, g.partials, stride,
+             g.tickets + 2);
+  else if (aligned16(x))
     launch_k(k_fpcg_xr<T, true>, gr, kThreads, 0, s, n, x, w.p, w.Ap, w.r, (T*)g.lv[0].b, w.cg, g.partials,
                                              stride, g.tickets + 2);
   else

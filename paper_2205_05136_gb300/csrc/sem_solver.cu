@@ -388,6 +388,19 @@ __global__ void __launch_bounds__(kVecThreads)
     c[i] = a[i] - b[i];
 }
 
+// c = a - b in double-float, b and c float pairs
+__global__ void __launch_bounds__(kVecThreads)
+    k_sub_pairs(int64_t n, const double* __restrict__ a, const df_pair* __restrict__ b, df_pair* __restrict__ c) {
+  pdl_entry();
+#pragma unroll 1
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const df_pair v = b[i];
+    const df d = dfnorm(dfd(a[i]) - df(v.h, v.l));
+    c[i] = df_pair{d.h, d.l};
+  }
+}
+
 __global__ void k_fill_pair(int64_t n, double* a, double va, double* b, double vb) {
   pdl_entry();
 #pragma unroll 1
@@ -826,8 +839,13 @@ int time_steps(sem_ctx* ctx, sem_state* st, double dt, int nsteps, double rtol, 
     rc = cg_solve(ctx, alpha, w.b, st->U[st->next], rtol, atol, maxit, precond, nullptr, nullptr,
                   stats, s, carried ? w.Ax : nullptr);
     if (rc != SEM_OK) return rc;
-    // A u^{n+1} = b - r for the next step's initial residual
-    launch_k(k_sub, vg, kVecThreads, 0, s, n, w.b, w.r, w.Ax);
+    // A u^{n+1} = b - r for the next step's initial residual (the multigrid PCG with
+    // the double-float operator keeps r as float pairs)
+    if (precond == SEM_PC_GMG && ctx->op_precision == SEM_PREC_DF64)  // kept as float pairs too
+      launch_k(k_sub_pairs, vg, kVecThreads, 0, s, n, w.b, reinterpret_cast<const df_pair*>(w.r),
+               reinterpret_cast<df_pair*>(w.Ax));
+    else
+      launch_k(k_sub, vg, kVecThreads, 0, s, n, w.b, w.r, w.Ax);
     SEM_CK(cudaGetLastError());
     ctx->launches += 1;
     const int old_prev = st->prev;
