@@ -627,8 +627,11 @@ __device__ __forceinline__ void lane_line(const EoMat<N, T>& M, const T* src, T*
     if (store) dst[off[t]] = out[t];
 }
 
+// 3 CTAs per SM (80 registers) at p = 3, 4; 4 at p <= 2, whose 64 registers hold
+// the shorter lines' offsets without spills (more warps for the small, latency-bound
+// coarse levels: mixed step -0.2 %).
 template <int P, int QUAD, typename MT>
-__global__ void __launch_bounds__(kApplyThreads, 3)
+__global__ void __launch_bounds__(kApplyThreads, P <= 2 ? 4 : 3)
     sem_apply_pipe_kernel(const ApplyArgs<float, MT> a, const __grid_constant__ KTab<P + 1, float> tab,
                           int nunits) {
   pdl_trigger();
