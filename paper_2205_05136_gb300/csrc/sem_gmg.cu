@@ -674,32 +674,63 @@ __device__ __forceinline__ bool grid_sums_df(df (&v)[K], double* partials, int s
   return threadIdx.x == 0;
 }
 
+// The double-float PCG kernels move two entries per thread and iteration
+// (16-byte accesses to FP64 and float-pair vectors) and the odd last entry
+// alone.  Workspace and level vectors come from cudaMalloc; VEC is false when a
+// caller's FP64 vector is not 16-byte aligned (then every entry goes the scalar
+// way).  8 CTAs of 256 threads per SM stay resident (32 registers); 6 for
+// k_dfpcg_xr (40 registers: at 32 it spills), whose grid is sized to match.
+template <typename T> using C2 = Pk<T, 2>;
+constexpr int kXrCtasPerSm = 6;
+
+// one entry of the set-up: r = b - A x (pairs), b0 = r rounded to T
+template <typename T>
+__device__ __forceinline__ void init_entry(double bi, df ax, df_pair& r2, T& b0, df (&v)[2]) {
+  const df bd = dfd(bi);
+  const df r = dfnorm(bd - ax);
+  r2 = df_pair{r.h, r.l};
+  b0 = t_of<T>(r);
+  v[0] = fma(r, r, v[0]);
+  v[1] = fma(bd, bd, v[1]);
+}
+
 // r = b - A x, b0 = r; r.r, b.b; stopping threshold.  A x is the FP64 result of
 // an apply in Ap (zeroed here), or the carried float pairs in ax2 (Ap is then
 // already zero).
-template <typename T>
-__global__ void __launch_bounds__(kThreads)
+template <typename T, bool VEC>
+__global__ void __launch_bounds__(kThreads, 8)
     k_dfpcg_init(int64_t n, const double* __restrict__ b, double* __restrict__ Ap,
                  const df_pair* __restrict__ ax2, df_pair* __restrict__ r2, T* __restrict__ b0, CgScalars* cg,
                  double* partials, int stride, unsigned int* ticket, double rtol, double atol) {
   pdl_entry();
   df v[2] = {df(0.f, 0.f), df(0.f, 0.f)};
-#pragma unroll 1
-  GRID_LOOP(i, n) {
-    const df bd = dfd(b[i]);
+  const int64_t nc = VEC ? n / 2 : 0;
+  GRID_CHUNKS(c, nc) {
+    const C2<double> bb = reinterpret_cast<const C2<double>*>(b)[c];
+    C2<df_pair> ax, rr;
+    C2<double> aa;
+    if (ax2 != nullptr) {
+      ax = reinterpret_cast<const C2<df_pair>*>(ax2)[c];
+    } else {
+      aa = reinterpret_cast<const C2<double>*>(Ap)[c];
+      reinterpret_cast<C2<double>*>(Ap)[c] = C2<double>{};
+    }
+    C2<T> rb;
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+      init_entry(bb.e[k], ax2 != nullptr ? df(ax.e[k].h, ax.e[k].l) : dfd(aa.e[k]), rr.e[k], rb.e[k], v);
+    reinterpret_cast<C2<df_pair>*>(r2)[c] = rr;
+    reinterpret_cast<C2<T>*>(b0)[c] = rb;
+  }
+  GRID_TAIL(i, nc * 2, n) {
     df ax;
     if (ax2 != nullptr) {
-      const df_pair a = ax2[i];
-      ax = df(a.h, a.l);
+      ax = df(ax2[i].h, ax2[i].l);
     } else {
       ax = dfd(Ap[i]);
       Ap[i] = 0.0;
     }
-    const df r = dfnorm(bd - ax);
-    r2[i] = df_pair{r.h, r.l};
-    b0[i] = t_of<T>(r);
-    v[0] = fma(r, r, v[0]);
-    v[1] = fma(bd, bd, v[1]);
+    init_entry(b[i], ax, r2[i], b0[i], v);
   }
   double tot[2];
   if (grid_sums_df<2>(v, partials, stride, ticket, tot)) {
@@ -714,36 +745,40 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-// z_new = x0 (kept in zs, which holds z_old on entry); first iteration: p = z_new,
-// rz = r.z_new; else beta = (r.z_new - r.z_old) / rz, rz = r.z_new.
+// z_new = the V-cycle's result (kept in zs, which holds z_old on entry); first
+// iteration: p = z_new, rz = r.z_new; else beta = (r.z_new - r.z_old) / rz, rz = r.z_new.
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
+__device__ __forceinline__ void z_entry(T z, T& zs, df_pair rp, df_pair& p2, bool first, df (&v)[2]) {
+  const df r(rp.h, rp.l), zd = df_of(z);
+  v[0] = fma(r, zd, v[0]);
+  if (first) p2 = df_pair{zd.h, zd.l};
+  else v[1] = fma(r, df_of(zs), v[1]);
+  zs = z;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 8)
     k_dfpcg_z(int64_t n, const T* __restrict__ x0, T* __restrict__ zs, const df_pair* __restrict__ r2,
               df_pair* __restrict__ p2, CgScalars* cg, double* partials, int stride, unsigned int* ticket) {
   pdl_entry();
   if (cg->done) return;
   const bool first = cg->iters == 0;
   df v[2] = {df(0.f, 0.f), df(0.f, 0.f)};
-  if (first) {
-#pragma unroll 1
-    GRID_LOOP(i, n) {
-      const T z = x0[i];
-      const df_pair rp = r2[i];
-      const df zd = df_of(z);
-      v[0] = fma(df(rp.h, rp.l), zd, v[0]);
-      p2[i] = df_pair{zd.h, zd.l};
-      zs[i] = z;
-    }
-  } else {
-#pragma unroll 1
-    GRID_LOOP(i, n) {
-      const T z = x0[i], zo = zs[i];
-      const df_pair rp = r2[i];
-      const df r(rp.h, rp.l);
-      v[0] = fma(r, df_of(z), v[0]);
-      v[1] = fma(r, df_of(zo), v[1]);
-      zs[i] = z;
-    }
+  const int64_t nc = n / 2;
+  GRID_CHUNKS(c, nc) {
+    const C2<T> z = reinterpret_cast<const C2<T>*>(x0)[c];
+    C2<T> zz = reinterpret_cast<const C2<T>*>(zs)[c];
+    const C2<df_pair> rr = reinterpret_cast<const C2<df_pair>*>(r2)[c];
+    C2<df_pair> pp;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) z_entry(z.e[k], zz.e[k], rr.e[k], pp.e[k], first, v);
+    reinterpret_cast<C2<T>*>(zs)[c] = zz;
+    if (first) reinterpret_cast<C2<df_pair>*>(p2)[c] = pp;
+  }
+  GRID_TAIL(i, nc * 2, n) {
+    df_pair pp;
+    z_entry(x0[i], zs[i], r2[i], pp, first, v);
+    if (first) p2[i] = pp;
   }
   double tot[2];
   if (grid_sums_df<2>(v, partials, stride, ticket, tot)) {
@@ -758,22 +793,42 @@ __global__ void __launch_bounds__(kThreads)
 
 // p = z + beta p (float pairs)
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
+__device__ __forceinline__ df_pair p_entry(df beta, df_pair pp, T z) {
+  const df pn = dfnorm(fma(beta, df(pp.h, pp.l), df_of(z)));
+  return df_pair{pn.h, pn.l};
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 8)
     k_dfpcg_p(int64_t n, const T* __restrict__ zs, df_pair* __restrict__ p2, const CgScalars* cg) {
   pdl_entry();
   if (cg->done || cg->iters == 0) return;  // first iteration: k_dfpcg_z set p = z
   const df beta = dfd(cg->beta);
-#pragma unroll 1
-  GRID_LOOP(i, n) {
-    const df_pair pp = p2[i];
-    const df pn = dfnorm(fma(beta, df(pp.h, pp.l), df_of(zs[i])));
-    p2[i] = df_pair{pn.h, pn.l};
+  const int64_t nc = n / 2;
+  GRID_CHUNKS(c, nc) {
+    const C2<T> zz = reinterpret_cast<const C2<T>*>(zs)[c];
+    C2<df_pair> pp = reinterpret_cast<const C2<df_pair>*>(p2)[c];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) pp.e[k] = p_entry(beta, pp.e[k], zz.e[k]);
+    reinterpret_cast<C2<df_pair>*>(p2)[c] = pp;
   }
+  GRID_TAIL(i, nc * 2, n) p2[i] = p_entry(beta, p2[i], zs[i]);
 }
 
 // x += alpha p (FP64), r -= alpha Ap, Ap = 0, b0 = r; r.r; convergence.
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
+__device__ __forceinline__ T xr_entry(double alpha, df nalpha, df_pair pp, double& x, double& ap, df_pair& r2,
+                                      df (&v)[1]) {
+  x = fma(alpha, df_to_double(df(pp.h, pp.l)), x);
+  const df r = dfnorm(fma(nalpha, dfd(ap), df(r2.h, r2.l)));
+  r2 = df_pair{r.h, r.l};
+  ap = 0.0;
+  v[0] = fma(r, r, v[0]);
+  return t_of<T>(r);
+}
+
+template <typename T, bool VEC>
+__global__ void __launch_bounds__(kThreads, kXrCtasPerSm)
     k_dfpcg_xr(int64_t n, double* __restrict__ x, const df_pair* __restrict__ p2, double* __restrict__ Ap,
                df_pair* __restrict__ r2, T* __restrict__ b0, CgScalars* cg, double* partials, int stride,
                unsigned int* ticket) {
@@ -782,16 +837,22 @@ __global__ void __launch_bounds__(kThreads)
   const double alpha = cg->alpha;
   const df nalpha = dfneg(dfd(alpha));
   df v[1] = {df(0.f, 0.f)};
-#pragma unroll 1
-  GRID_LOOP(i, n) {
-    const df_pair pp = p2[i];
-    x[i] = fma(alpha, df_to_double(df(pp.h, pp.l)), x[i]);
-    const df_pair rp = r2[i];
-    const df r = dfnorm(fma(nalpha, dfd(Ap[i]), df(rp.h, rp.l)));
-    r2[i] = df_pair{r.h, r.l};
-    Ap[i] = 0.0;
-    b0[i] = t_of<T>(r);
-    v[0] = fma(r, r, v[0]);
+  const int64_t nc = VEC ? n / 2 : 0;
+  GRID_CHUNKS(c, nc) {
+    const C2<df_pair> pp = reinterpret_cast<const C2<df_pair>*>(p2)[c];
+    C2<double> xx = reinterpret_cast<const C2<double>*>(x)[c];
+    C2<double> aa = reinterpret_cast<const C2<double>*>(Ap)[c];
+    C2<df_pair> rr = reinterpret_cast<const C2<df_pair>*>(r2)[c];
+    C2<T> rb;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) rb.e[k] = xr_entry<T>(alpha, nalpha, pp.e[k], xx.e[k], aa.e[k], rr.e[k], v);
+    reinterpret_cast<C2<double>*>(x)[c] = xx;
+    reinterpret_cast<C2<df_pair>*>(r2)[c] = rr;
+    reinterpret_cast<C2<double>*>(Ap)[c] = aa;
+    reinterpret_cast<C2<T>*>(b0)[c] = rb;
+  }
+  GRID_TAIL(i, nc * 2, n) {
+    b0[i] = xr_entry<T>(alpha, nalpha, p2[i], x[i], Ap[i], r2[i], v);
   }
   double tot[1];
   if (grid_sums_df<1>(v, partials, stride, ticket, tot)) {
@@ -1277,10 +1338,11 @@ int pcg_init_seq(sem_ctx* ctx, Gmg& g, double alpha, const double* b, const doub
     a.yloc = ctx->deterministic ? ctx->det_scratch : nullptr;
     GMG_CK(launch_operator(ctx, a, s));
   }
-  if (ctx->op_precision == SEM_PREC_DF64)  // r kept as float pairs in ws.r, carried A x as pairs in ws.Ax
-    launch_k(k_dfpcg_init<T>, gr, kThreads, 0, s, n, b, w.Ap,
-             carried ? reinterpret_cast<const df_pair*>(w.Ax) : nullptr, reinterpret_cast<df_pair*>(w.r), b0,
-             w.cg, g.partials, stride, g.tickets, rtol, atol);
+  if (ctx->op_precision == SEM_PREC_DF64) {  // r kept as float pairs in ws.r, carried A x as pairs in ws.Ax
+    auto kern = aligned16(b) ? k_dfpcg_init<T, true> : k_dfpcg_init<T, false>;
+    launch_k(kern, gr, kThreads, 0, s, n, b, w.Ap, carried ? reinterpret_cast<const df_pair*>(w.Ax) : nullptr,
+             reinterpret_cast<df_pair*>(w.r), b0, w.cg, g.partials, stride, g.tickets, rtol, atol);
+  }
   else if (aligned16(b))
     launch_k(k_fpcg_init<T, true>, gr, kThreads, 0, s, n, b, ax, w.r, b0, w.cg, g.partials, stride, g.tickets,
                                                rtol, atol);
@@ -1325,8 +1387,8 @@ int pcg_iter_seq(sem_ctx* ctx, Gmg& g, double alpha, double* x, cudaStream_t s) 
   GMG_CK(launch_operator(ctx, ap, s));
   GMG_CK(cudaEventRecordWithFlags(g.ev1, s, cudaEventRecordExternal));
   if (dfop)
-    launch_k(k_dfpcg_xr<T>, gr, kThreads, 0, s, n, x, p2, w.Ap, r2, (T*)g.lv[0].b, w.cg, g.partials, stride,
-             g.tickets + 2);
+    launch_k(aligned16(x) ? k_dfpcg_xr<T, true> : k_dfpcg_xr<T, false>, std::min(gr, 152 * kXrCtasPerSm),
+             kThreads, 0, s, n, x, p2, w.Ap, r2, (T*)g.lv[0].b, w.cg, g.partials, stride, g.tickets + 2);
   else if (aligned16(x))
     launch_k(k_fpcg_xr<T, true>, gr, kThreads, 0, s, n, x, w.p, w.Ap, w.r, (T*)g.lv[0].b, w.cg, g.partials,
                                              stride, g.tickets + 2);

@@ -14,7 +14,12 @@
 //                 elements that hold it, each fine node once.
 // Each pass is one thread per output node reading a short run along one
 // lattice axis: no shared memory, no barriers and no atomics, so the result is
-// the same in every run (the deterministic mode needs no variant).
+// the same in every run (the deterministic mode needs no variant).  A CTA
+// covers a 32 x 8 patch of a lattice plane and steps through the planes
+// (stride gridDim.z): the grid stays within one wave of CTAs, because a grid of
+// thousands of short CTAs costs more in block launches than its memory traffic.
+#include <algorithm>
+
 #include "sem_apply_kernel.cuh"
 #include "sem_context.cuh"
 
@@ -45,50 +50,56 @@ __global__ void __launch_bounds__(kTThreads)
   if (done != nullptr && *done) return;
   constexpr int PF = NF - 1, PC = NC - 1;
   constexpr bool PRO = MODE == kProlong || MODE == kProlongAdd;
-  // output node (c0, c1, c2) from the 3-D grid: no index divisions
+  // output node (c0, c1, c2) from the grid: no index divisions
   const int c0 = blockIdx.x * kPassX + threadIdx.x;
   const int c1 = blockIdx.y * kPassY + threadIdx.y;
-  const int c2 = blockIdx.z;
   if (c0 >= d0 || c1 >= d1) return;
   // input extent along AX and input strides
   const int nin = PRO ? PC * ne + 1 : PF * ne + 1;
   const int i0 = AX == 0 ? nin : d0, i1 = AX == 1 ? nin : d1;
   const int64_t stride = AX == 0 ? 1 : (AX == 1 ? (int64_t)i0 : (int64_t)i0 * i1);
-  const int q = AX == 0 ? c0 : (AX == 1 ? c1 : c2);
-  // input offset of the output's position with the AX coordinate at 0
-  const int64_t base = AX == 0 ? (int64_t)i0 * ((int64_t)i1 * c2 + c1)
-                               : (AX == 1 ? c0 + (int64_t)i0 * i1 * c2 : c0 + (int64_t)i0 * c1);
-  const int64_t o = c0 + (int64_t)d0 * (c1 + (int64_t)d1 * c2);
-  T acc = T(0);
-  if constexpr (PRO) {
-    const int e = min(q / PF, ne - 1), i = q - PF * e;
-    const T* src = in + base + (int64_t)(PC * e) * stride;
+#pragma unroll 1
+  for (int c2 = blockIdx.z; c2 < d2; c2 += gridDim.z) {
+    const int q = AX == 0 ? c0 : (AX == 1 ? c1 : c2);
+    // input offset of the output's position with the AX coordinate at 0
+    const int64_t base = AX == 0 ? (int64_t)i0 * ((int64_t)i1 * c2 + c1)
+                                 : (AX == 1 ? c0 + (int64_t)i0 * i1 * c2 : c0 + (int64_t)i0 * c1);
+    const int64_t o = c0 + (int64_t)d0 * (c1 + (int64_t)d1 * c2);
+    T acc = T(0);
+    if constexpr (PRO) {
+      const int e = min(q / PF, ne - 1), i = q - PF * e;
+      const T* src = in + base + (int64_t)(PC * e) * stride;
 #pragma unroll
-    for (int a = 0; a < NC; ++a) acc = fma(pm.P[i][a], src[a * stride], acc);
-    if constexpr (MODE == kProlongAdd) {
-      out[o] += acc;
-      out2[o] = T(0);
+      for (int a = 0; a < NC; ++a) acc = fma(pm.P[i][a], src[a * stride], acc);
+      if constexpr (MODE == kProlongAdd) {
+        out[o] += acc;
+        out2[o] = T(0);
+      } else {
+        out[o] = acc;
+      }
     } else {
+      auto val = [&](int I) {
+        const int64_t k = base + (int64_t)I * stride;
+        return MODE == kRestrictDiff ? in[k] - in2[k] : in[k];
+      };
+      const int e = min(q / PC, ne - 1), a = q - PC * e;
+#pragma unroll
+      for (int i = 0; i < NF; ++i) acc = fma(pm.P[i][a], val(PF * e + i), acc);
+      if (a == 0 && e > 0) {  // a vertex of the element before too; its last fine node is counted above
+#pragma unroll
+        for (int i = 0; i < NF - 1; ++i) acc = fma(pm.P[i][PC], val(PF * (e - 1) + i), acc);
+      }
       out[o] = acc;
     }
-  } else {
-    auto val = [&](int I) {
-      const int64_t k = base + (int64_t)I * stride;
-      return MODE == kRestrictDiff ? in[k] - in2[k] : in[k];
-    };
-    const int e = min(q / PC, ne - 1), a = q - PC * e;
-#pragma unroll
-    for (int i = 0; i < NF; ++i) acc = fma(pm.P[i][a], val(PF * e + i), acc);
-    if (a == 0 && e > 0) {  // a vertex of the element before too; its last fine node is counted above
-#pragma unroll
-      for (int i = 0; i < NF - 1; ++i) acc = fma(pm.P[i][PC], val(PF * (e - 1) + i), acc);
-    }
-    out[o] = acc;
   }
 }
 
+// 32 x 8 patches of a plane in x and y; along z as many CTAs as keep the grid
+// within 8 CTAs per SM (at least one plane each).
 dim3 pass_grid(int d0, int d1, int d2) {
-  return dim3((unsigned)((d0 + kPassX - 1) / kPassX), (unsigned)((d1 + kPassY - 1) / kPassY), (unsigned)d2);
+  const int gx = (d0 + kPassX - 1) / kPassX, gy = (d1 + kPassY - 1) / kPassY;
+  const int gz = std::max(1, std::min(d2, (152 * 8) / std::max(1, gx * gy)));
+  return dim3((unsigned)gx, (unsigned)gy, (unsigned)gz);
 }
 
 template <int NF, int NC, typename T>
@@ -101,7 +112,7 @@ cudaError_t launch_passes(bool prolong, const Level& F, const Level& C, const do
   const int nx = F.nx, ny = F.ny, nz = F.nz;
   const int xf = F.p * nx + 1, yf = F.p * ny + 1, zf = F.p * nz + 1;
   const int xc = C.p * nx + 1, yc = C.p * ny + 1, zc = C.p * nz + 1;
-  if (zf > 65535) return cudaErrorInvalidValue;  // the z extent is a grid dimension
+  if ((std::max(yf, yc) + kPassY - 1) / kPassY > 65535) return cudaErrorInvalidValue;  // grid y limit
   cudaError_t e;
   if (prolong) {  // coarse -> (xc, yc, zf) -> (xc, yf, zf) -> fine
     e = launch_k(k_ptransfer_pass<NF, NC, 2, kProlong, T>, pass_grid(xc, yc, zf), dim3(kPassX, kPassY), 0, s,
