@@ -94,6 +94,28 @@ def test_gmg_pcg_reaches_fp64_solution(precision, quad):
     assert abs(it - it_ref) <= 3, (it, it_ref)
 
 
+@pytest.mark.parametrize("offset", [0, 1])
+def test_gmg_pcg_double_float_operator(offset):
+    """The flexible PCG with the double-float operator (its vector kernels move
+    two entries at a time with 16-byte accesses): an odd node count (9009) for
+    the one-entry tail, and with offset 1 a solution and right-hand side that
+    start 8 bytes past a 16-byte boundary, which the kernels take one entry at a
+    time.  Both reach the direct solution."""
+    s, tissue, g, o, H = _setup((8, 5, 3), 4, "LGL", 200, capi.SEM_PREC_FP32_BF16)
+    capi.sem_set_operator_precision(g.ctx, capi.SEM_PREC_DF64)
+    assert o.ndofs % 2 == 1
+    A = H.A[0]
+    b = W.uniform_vector(o.ndofs, -1.0, 1.0, seed=5)
+    xref = spla.spsolve(A.tocsc(), b)
+    bb = torch.zeros(o.ndofs + offset, dtype=torch.float64, device="cuda")[offset:]
+    bb.copy_(torch.tensor(b))
+    x = torch.zeros(o.ndofs + offset, dtype=torch.float64, device="cuda")[offset:]
+    assert (x.data_ptr() % 16 == 8) == (offset == 1) and (bb.data_ptr() % 16 == 8) == (offset == 1)
+    it, res = g.cg_solve(ALPHA, bb, x, rtol=1e-12, maxit=200, precond=capi.SEM_PC_GMG)
+    assert rel(x.cpu().numpy(), xref) < 1e-10
+    assert it <= 20, it
+
+
 @pytest.mark.parametrize("quad", ["LGL", "LG"])
 def test_time_steps_with_fp32_multigrid_match_oracle(quad):
     s = W.slab(8, 4, 2, (20.0, 7.0, 3.0))
