@@ -96,6 +96,8 @@ typedef struct {
   int64_t kernel_launches; /* libsem kernels launched by the call */
   double smoother_apply_ms;   /* device time of timed fine-level multigrid smoother applies */
   int64_t n_smoother_apply;   /* fine-level smoother applies timed (one per V-cycle) */
+  int64_t carried_solves;     /* time-step solves whose initial residual came from the
+                                 previous step's solve (no operator apply) */
 } sem_stats;
 
 /* Library version string (static storage). */
@@ -252,6 +254,10 @@ int sem_state_get_activation(sem_state* st, double* tau, double* dudt_max, void*
  *   gate update and I_ion per node (Eq. ionic_discr),
  *   b = M(history) - M I_ion + M I_app(t^{n+1})   (Eqs. algebraic_ionic, matrix_rhs),
  *   CG solve warm-started from u^n to ||r|| <= max(rtol ||b||, atol).
+ * Consecutive steps of one state with the same operator take the initial
+ * residual's A u^n from the previous step's solve (A u^n = b_prev - r_prev)
+ * instead of applying the operator; every 50th step applies it, and any other
+ * call that changes the context or the state ends this.
  * stats may be NULL.  Synchronises stream. */
 int sem_step(sem_ctx* ctx, sem_state* st, double dt, int nsteps, double rtol, double atol,
              int maxit, int precond, sem_stats* stats, void* stream);
@@ -274,8 +280,14 @@ int sem_step_host(sem_ctx* ctx, double* u, double* u_prev, double* h, double* h_
  * With page-locked inputs the ionic update reads them over the host link
  * while it computes; pageable inputs are staged by copies.  h^{n+1} is copied
  * back on a second stream of the context while the linear solve runs, u^{n+1}
- * after the solve.  The host must not change the arrays during the call.  SEM_ERR_ARG when an array is device memory or when u_next
- * or h_next overlaps another array.  Synchronises stream. */
+ * after the solve.  With the multigrid preconditioner, a call whose n follows
+ * the previous call's and whose u equals, bit for bit, the u_next that call
+ * returned takes the initial residual from that call's solve as sem_step
+ * does; the device checks the equality while it reads u and otherwise applies
+ * the operator (stats->carried_solves counts the carried solves).  The host
+ * must not change the arrays during the call.  SEM_ERR_ARG when an array is
+ * device memory or when u_next or h_next overlaps another array.
+ * Synchronises stream. */
 int sem_step_host_out(sem_ctx* ctx, const double* u, const double* u_prev, const double* h,
                       const double* h_prev, double* u_next, double* h_next, int64_t n, double dt,
                       double rtol, double atol, int maxit, int precond, sem_stats* stats, void* stream);

@@ -70,7 +70,8 @@ class sem_stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int64), ("cg_iters", ctypes.c_int64),
                 ("last_residual", ctypes.c_double), ("apply_ms", ctypes.c_double),
                 ("n_apply", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
-                ("smoother_apply_ms", ctypes.c_double), ("n_smoother_apply", ctypes.c_int64)]
+                ("smoother_apply_ms", ctypes.c_double), ("n_smoother_apply", ctypes.c_int64),
+                ("carried_solves", ctypes.c_int64)]
 
 
 _LIB = None

@@ -28,12 +28,24 @@ thread_local std::string g_create_err;
 // Entry points that change the operator, the preconditioner, a state or the CG
 // workspace end the carried initial residual of consecutive time steps.
 void invalidate_carry(sem_ctx* ctx) {
-  if (ctx != nullptr) ctx->carry.valid = false;
+  if (ctx == nullptr) return;
+  ctx->carry.valid = false;
+  ctx->carry.same = nullptr;
+  ctx->host_carry.valid = false;
 }
 // ... also on the way out, for entry points that step states of their own.
 struct CarryScope {
   sem_ctx* ctx;
   ~CarryScope() { invalidate_carry(ctx); }
+};
+// sem_step_host_out: the state's own carry ends with the call, the one kept
+// for the next call (host_carry) is set by the call itself.
+struct StateCarryScope {
+  sem_ctx* ctx;
+  ~StateCarryScope() {
+    ctx->carry.valid = false;
+    ctx->carry.same = nullptr;
+  }
 };
 
 struct DeviceGuard {
@@ -100,7 +112,7 @@ void free_ctx(sem_ctx* ctx) {
   cudaFree(ctx->stim_mask);
   Workspace& w = ctx->ws;
   cudaFree(w.r); cudaFree(w.z); cudaFree(w.p); cudaFree(w.Ap); cudaFree(w.invdiag);
-  cudaFree(w.b); cudaFree(w.g); cudaFree(w.p2);
+  cudaFree(w.b); cudaFree(w.g); cudaFree(w.Ax); cudaFree(w.p2);
   cudaFree(ctx->det_scratch);
   cudaFree(w.cg);
   if (w.cg_host) cudaFreeHost(w.cg_host);
@@ -108,6 +120,8 @@ void free_ctx(sem_ctx* ctx) {
   cudaFree(w.tickets);
   cudaFree(w.apply_partials);
   cudaFree(w.dot_result);
+  cudaFree(w.same);
+  if (w.same_host) cudaFreeHost(w.same_host);
 }
 
 __global__ void k_fill(int64_t n, double v, double* x) {
@@ -631,8 +645,9 @@ int sem_step_host_out(sem_ctx* ctx, const double* u, const double* u_prev, const
                       const double* h_prev, double* u_next, double* h_next, int64_t n, double dt,
                       double rtol, double atol, int maxit, int precond, sem_stats* stats, void* stream) {
   CK_CTX(ctx);
+  const sem_ctx::HostCarry hcy = ctx->host_carry;
   invalidate_carry(ctx);
-  CarryScope carry_scope{ctx};
+  StateCarryScope carry_scope{ctx};
   DeviceGuard guard(ctx->device);
   const void* all[6] = {u, u_prev, h, h_prev, u_next, h_next};
   for (const void* p : all)
@@ -675,16 +690,49 @@ int sem_step_host_out(sem_ctx* ctx, const double* u, const double* u_prev, const
   view.U[0] = use[0]; view.U[1] = use[1]; view.H[0] = use[2]; view.H[1] = use[3];
   view.U[2] = st->U[2];
   view.H[2] = st->H[2];
+  // The last call left its u^{n+1} in U[2] and A u^{n+1} in the workspace.  If
+  // this call continues it (n, operator) and its u is that u^{n+1}, the solve
+  // takes the initial residual from there: the ionic update compares u with
+  // U[2] as it overwrites U[2] by the warm start, and the set-up applies the
+  // operator after all where they differ.
+  int rc = ensure_workspace(ctx);
+  if (rc != SEM_OK) return rc;
+  const bool checked = hcy.valid && hcy.n == n && precond == SEM_PC_GMG;
+  if (checked) {
+    sem_ctx::ResidualCarry& cy = ctx->carry;
+    cy.valid = true;
+    cy.st = &view;
+    cy.n = n;
+    cy.alpha = hcy.alpha;
+    cy.precond = hcy.precond;
+    cy.age = hcy.age;
+    cy.same = ctx->ws.same;
+  }
   hc.h_dst = h_next;
-  const int rc = sem_step(ctx, &view, dt, 1, rtol, atol, maxit, precond, stats, stream);
+  rc = sem_step(ctx, &view, dt, 1, rtol, atol, maxit, precond, stats, stream);
   hc.h_dst = nullptr;
   if (rc != SEM_OK) {
     cudaStreamSynchronize(hc.side);
     return rc;
   }
+  // whether this call's solve used the carry (time_steps does not count checked ones)
+  const bool used_check = ctx->carry.valid && ctx->carry.age > 0 && checked;
+  if (used_check) SEM_CK(cudaMemcpyAsync(ctx->ws.same_host, ctx->ws.same, sizeof(int), cudaMemcpyDeviceToHost, s));
   SEM_CK(cudaMemcpyAsync(u_next, st->U[2], bytes, cudaMemcpyDeviceToHost, s));
   SEM_CK(cudaStreamWaitEvent(s, hc.ev_h, 0));
   SEM_CK(cudaStreamSynchronize(s));
+  const bool carried = used_check && *ctx->ws.same_host != 0;
+  if (stats && carried) stats->carried_solves += 1;
+  // for the next call: its n, this solve's operator, and the carry's age
+  const sem_ctx::ResidualCarry& cy = ctx->carry;
+  if (cy.valid) {
+    sem_ctx::HostCarry& next = ctx->host_carry;
+    next.valid = true;
+    next.n = n + 1;
+    next.alpha = cy.alpha;
+    next.precond = cy.precond;
+    next.age = carried ? cy.age : 0;
+  }
   return SEM_OK;
 }
 

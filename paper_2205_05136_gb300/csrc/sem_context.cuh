@@ -23,6 +23,8 @@ struct Workspace {
   unsigned int* tickets = nullptr;    // [4]: [0] the CG vector kernels' reductions, the rest spare
   double* apply_partials = nullptr;   // [apply grid]
   double* dot_result = nullptr;       // 1 double
+  int* same = nullptr;        // device flag of sem_step_host_out's carry check (sem_ctx::carry)
+  int* same_host = nullptr;   // page-locked copy, read after the call
 };
 
 struct Gmg;   // geometric multigrid hierarchy (sem_gmg.cu)
@@ -86,7 +88,22 @@ struct sem_ctx {
     double alpha = 0.0;
     int precond = -1;
     int age = 0;
+    // sem_step_host_out: the state's u^n comes from the caller's host array, so
+    // the carry holds only if it equals, bit for bit, the solution the last call
+    // left in the state's solution buffer.  The ionic update compares the two
+    // while it reads u^n and clears *same on a difference; the solve then
+    // applies the operator after all (device-side choice, no host round trip).
+    int* same = nullptr;
   } carry;
+  // The carry left by the last sem_step_host_out call (step index of the next
+  // call, operator and age); any other entry point that mutates clears it.
+  struct HostCarry {
+    bool valid = false;
+    int64_t n = -1;
+    double alpha = 0.0;
+    int precond = -1;
+    int age = 0;
+  } host_carry;
   // sem_step_host_out: a second stream for the copy of h^{n+1} to the host,
   // which the ionic update writes first thing in the step and which then
   // overlaps the linear solve (time_steps issues it when h_dst is set)
@@ -117,10 +134,11 @@ int ensure_workspace(sem_ctx* ctx);
 int apply_fp64(sem_ctx* ctx, double alpha, double beta, const double* u, double* y,
                cudaStream_t s);
 // ax0: when set, A x for the initial residual r = b - A x is taken from it (and it
-// is overwritten) instead of an operator apply.
+// is overwritten) instead of an operator apply.  ax0_ok (multigrid PCG only): a
+// device flag; where it reads zero at the set-up the operator is applied after all.
 int cg_solve(sem_ctx* ctx, double alpha, const double* b, double* x, double rtol, double atol,
              int maxit, int precond, int* iters, double* final_res, sem_stats* stats,
-             cudaStream_t s, double* ax0 = nullptr);
+             cudaStream_t s, double* ax0 = nullptr, const int* ax0_ok = nullptr);
 int time_steps(sem_ctx* ctx, sem_state* st, double dt, int nsteps, double rtol, double atol,
                int maxit, int precond, sem_stats* stats, cudaStream_t s);
 int fail(sem_ctx* ctx, int code, const std::string& msg);
@@ -142,7 +160,7 @@ void gmg_free(sem_ctx* ctx);
 int gmg_vcycle(sem_ctx* ctx, double alpha, const double* r, double* z, cudaStream_t s);
 int gmg_pcg(sem_ctx* ctx, double alpha, const double* b, double* x, double rtol, double atol,
             int maxit, int* iters, double* final_res, sem_stats* stats, cudaStream_t s,
-            double* ax0 = nullptr);
+            double* ax0 = nullptr, const int* ax0_ok = nullptr);
 int gmg_info(sem_ctx* ctx, double alpha, int max_levels, int* nlevels, int* p, int* dims,
              int64_t* ndofs, double* lambda_max, cudaStream_t s);
 

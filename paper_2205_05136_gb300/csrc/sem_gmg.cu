@@ -69,7 +69,8 @@ struct Gmg {
     double rtol = 0.0, atol = 0.0;
     cudaGraphExec_t init = nullptr, iter = nullptr;
     cudaGraphExec_t init_carried = nullptr;  // set-up from the carried A x (ws.Ax)
-    int64_t init_kernels = 0, iter_kernels = 0, init_carried_kernels = 0;
+    cudaGraphExec_t init_checked = nullptr;  // the same where ws.same reads nonzero, else applied
+    int64_t init_kernels = 0, iter_kernels = 0, init_carried_kernels = 0, init_checked_kernels = 0;
     int last_iters = 0;  // iterations the previous solve with these graphs took
   };
   Graphs graphs[16];
@@ -425,11 +426,13 @@ __device__ __forceinline__ bool grid_sums_k(double (&v)[K], double* partials, in
 // r = b - Ap, Ap = 0, b0 = (T) r; r.r, b.b; stopping threshold.  VEC: b is
 // 16-byte aligned (pairs of entries by 16-byte accesses).
 template <typename T, bool VEC>
-__global__ void k_fpcg_init(int64_t n, const double* __restrict__ b, double* __restrict__ Ap,
-                            double* __restrict__ r, T* __restrict__ b0, CgScalars* cg,
+__global__ void k_fpcg_init(int64_t n, const double* __restrict__ b, double* Ap_main, double* Ap_alt,
+                            const int* use_main, double* __restrict__ r, T* __restrict__ b0, CgScalars* cg,
                             double* partials, int stride, unsigned int* ticket, double rtol,
                             double atol) {
   pdl_entry();
+  // A x: Ap_main, or Ap_alt where the flag use_main reads zero
+  double* __restrict__ Ap = (use_main == nullptr || *use_main != 0) ? Ap_main : Ap_alt;
   double v[2] = {0.0, 0.0};
   const int64_t nc = VEC ? n / 2 : 0;
   GRID_CHUNKS(c, nc) {
@@ -695,14 +698,17 @@ __device__ __forceinline__ void init_entry(double bi, df ax, df_pair& r2, T& b0,
 }
 
 // r = b - A x, b0 = r; r.r, b.b; stopping threshold.  A x is the FP64 result of
-// an apply in Ap (zeroed here), or the carried float pairs in ax2 (Ap is then
+// an apply in Ap (zeroed here), or the carried float pairs in ax2_in (Ap is then
 // already zero).
 template <typename T, bool VEC>
 __global__ void __launch_bounds__(kThreads, 8)
     k_dfpcg_init(int64_t n, const double* __restrict__ b, double* __restrict__ Ap,
-                 const df_pair* __restrict__ ax2, df_pair* __restrict__ r2, T* __restrict__ b0, CgScalars* cg,
-                 double* partials, int stride, unsigned int* ticket, double rtol, double atol) {
+                 const df_pair* __restrict__ ax2_in, const int* ax2_ok, df_pair* __restrict__ r2,
+                 T* __restrict__ b0, CgScalars* cg, double* partials, int stride, unsigned int* ticket,
+                 double rtol, double atol) {
   pdl_entry();
+  // the carried pairs, unless the flag ax2_ok reads zero (then A x is in Ap)
+  const df_pair* __restrict__ ax2 = (ax2_ok == nullptr || *ax2_ok != 0) ? ax2_in : nullptr;
   df v[2] = {df(0.f, 0.f), df(0.f, 0.f)};
   const int64_t nc = VEC ? n / 2 : 0;
   GRID_CHUNKS(c, nc) {
@@ -1171,6 +1177,7 @@ void free_gmg_struct(Gmg* g) {
     if (gr.init) cudaGraphExecDestroy(gr.init);
     if (gr.iter) cudaGraphExecDestroy(gr.iter);
     if (gr.init_carried) cudaGraphExecDestroy(gr.init_carried);
+    if (gr.init_checked) cudaGraphExecDestroy(gr.init_checked);
   }
   if (g->capture) cudaStreamDestroy(g->capture);
   if (g->ev0) cudaEventDestroy(g->ev0);
@@ -1320,35 +1327,35 @@ int64_t count_kernels(cudaGraph_t graph) {
 // V-cycle after convergence.
 // carried: A x is read from ws.Ax (the last time step's b - r) instead of
 // applied; ws.Ap is then already zero (every PCG iteration leaves it zero).
+// checked (with carried): a device flag; the zeroing of ws.Ap and the apply run
+// only where it reads zero (they return at once otherwise), and the residual
+// kernel reads ws.Ax or ws.Ap accordingly.
 template <typename T>
 int pcg_init_seq(sem_ctx* ctx, Gmg& g, double alpha, const double* b, const double* x, double rtol,
-                 double atol, bool carried, cudaStream_t s) {
+                 double atol, bool carried, const int* checked, cudaStream_t s) {
   Workspace& w = ctx->ws;
   Level& L = ctx->L;
   const int64_t n = L.ndofs;
   const int gr = grid1d(n);
   T* b0 = (T*)g.lv[0].b;
   const int stride = g.partial_len;
-  double* ax = carried ? w.Ax : w.Ap;
-  if (!carried) {
-    launch_k(k_zero<double>, gr, kThreads, 0, s, n, w.Ap, nullptr);
+  if (!carried || checked != nullptr) {
+    launch_k(k_zero<double>, gr, kThreads, 0, s, n, w.Ap, checked);
     ApplyArgs64 a{};
     a.map = L.map; a.metric = L.metric; a.u = x; a.y = w.Ap; a.nelem = L.nelem;
-    a.mass_coef = alpha; a.out_scale = 1.0; a.scale_out = 0;
+    a.mass_coef = alpha; a.out_scale = 1.0; a.scale_out = 0; a.done = checked;
     a.yloc = ctx->deterministic ? ctx->det_scratch : nullptr;
     GMG_CK(launch_operator(ctx, a, s));
   }
   if (ctx->op_precision == SEM_PREC_DF64) {  // r kept as float pairs in ws.r, carried A x as pairs in ws.Ax
     auto kern = aligned16(b) ? k_dfpcg_init<T, true> : k_dfpcg_init<T, false>;
     launch_k(kern, gr, kThreads, 0, s, n, b, w.Ap, carried ? reinterpret_cast<const df_pair*>(w.Ax) : nullptr,
-             reinterpret_cast<df_pair*>(w.r), b0, w.cg, g.partials, stride, g.tickets, rtol, atol);
+             checked, reinterpret_cast<df_pair*>(w.r), b0, w.cg, g.partials, stride, g.tickets, rtol, atol);
+  } else {
+    auto kern = aligned16(b) ? k_fpcg_init<T, true> : k_fpcg_init<T, false>;
+    launch_k(kern, gr, kThreads, 0, s, n, b, carried ? w.Ax : w.Ap, w.Ap, checked, w.r, b0, w.cg, g.partials,
+             stride, g.tickets, rtol, atol);
   }
-  else if (aligned16(b))
-    launch_k(k_fpcg_init<T, true>, gr, kThreads, 0, s, n, b, ax, w.r, b0, w.cg, g.partials, stride, g.tickets,
-                                               rtol, atol);
-  else
-    launch_k(k_fpcg_init<T, false>, gr, kThreads, 0, s, n, b, ax, w.r, b0, w.cg, g.partials, stride, g.tickets,
-                                                rtol, atol);
   GMG_CK(cudaGetLastError());
   return SEM_OK;
 }
@@ -1414,12 +1421,14 @@ int get_graphs(sem_ctx* ctx, Gmg& g, double alpha, const double* b, double* x, d
   if (gr.init) { cudaGraphExecDestroy(gr.init); gr.init = nullptr; }
   if (gr.iter) { cudaGraphExecDestroy(gr.iter); gr.iter = nullptr; }
   if (gr.init_carried) { cudaGraphExecDestroy(gr.init_carried); gr.init_carried = nullptr; }
+  if (gr.init_checked) { cudaGraphExecDestroy(gr.init_checked); gr.init_checked = nullptr; }
   cudaStream_t cs = g.capture;
   const int64_t l0 = ctx->launches;
-  for (int which = 0; which < 3; ++which) {
+  for (int which = 0; which < 4; ++which) {
     GMG_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     int rc = which == 1 ? pcg_iter_seq<T>(ctx, g, alpha, x, cs)
-                        : pcg_init_seq<T>(ctx, g, alpha, b, x, rtol, atol, which == 2, cs);
+                        : pcg_init_seq<T>(ctx, g, alpha, b, x, rtol, atol, which >= 2,
+                                          which == 3 ? ctx->ws.same : nullptr, cs);
     cudaGraph_t graph = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
     if (rc != SEM_OK) {
@@ -1434,7 +1443,8 @@ int get_graphs(sem_ctx* ctx, Gmg& g, double alpha, const double* b, double* x, d
     if (ei != cudaSuccess) return cuda_fail(ctx, ei, "cudaGraphInstantiate");
     if (which == 0) { gr.init = exec; gr.init_kernels = nk; }
     else if (which == 1) { gr.iter = exec; gr.iter_kernels = nk; }
-    else { gr.init_carried = exec; gr.init_carried_kernels = nk; }
+    else if (which == 2) { gr.init_carried = exec; gr.init_carried_kernels = nk; }
+    else { gr.init_checked = exec; gr.init_checked_kernels = nk; }
   }
   ctx->launches = l0;  // capture launched nothing; replays are counted
   gr.x = x;
@@ -1449,13 +1459,13 @@ int get_graphs(sem_ctx* ctx, Gmg& g, double alpha, const double* b, double* x, d
 template <typename T>
 int pcg_t(sem_ctx* ctx, Gmg& g, double alpha, const double* b, double* x, double rtol,
           double atol, int maxit, int* iters, double* final_res, sem_stats* stats, bool carried,
-          cudaStream_t s) {
+          bool checked, cudaStream_t s) {
   Workspace& w = ctx->ws;
   Gmg::Graphs* gr = nullptr;
   int rc = get_graphs<T>(ctx, g, alpha, b, x, rtol, atol, &gr);
   if (rc != SEM_OK) return rc;
-  GMG_CK(cudaGraphLaunch(carried ? gr->init_carried : gr->init, s));
-  ctx->launches += carried ? gr->init_carried_kernels : gr->init_kernels;
+  GMG_CK(cudaGraphLaunch(!carried ? gr->init : (checked ? gr->init_checked : gr->init_carried), s));
+  ctx->launches += !carried ? gr->init_kernels : (checked ? gr->init_checked_kernels : gr->init_carried_kernels);
   Timing& tm = ctx->timing;
   bool done_h = false;
   int launched = 0;
@@ -1518,18 +1528,23 @@ void gmg_free(sem_ctx* ctx) {
 }
 
 int gmg_pcg(sem_ctx* ctx, double alpha, const double* b, double* x, double rtol, double atol,
-            int maxit, int* iters, double* final_res, sem_stats* stats, cudaStream_t s, double* ax0) {
-  // the carried A x is always the workspace's (captured into the set-up graph)
-  if (ax0 != nullptr && ax0 != ctx->ws.Ax) return fail(ctx, SEM_ERR_ARG, "carried A x must be the workspace's");
+            int maxit, int* iters, double* final_res, sem_stats* stats, cudaStream_t s, double* ax0,
+            const int* ax0_ok) {
   int rc = ensure_workspace(ctx);
+  if (rc != SEM_OK) return rc;
+  // the carried A x and its check flag are always the workspace's (captured into the set-up graphs)
+  if (ax0 != nullptr && ax0 != ctx->ws.Ax) return fail(ctx, SEM_ERR_ARG, "carried A x must be the workspace's");
+  if (ax0_ok != nullptr && ax0_ok != ctx->ws.same) return fail(ctx, SEM_ERR_ARG, "carry check must be the workspace's");
   if (rc != SEM_OK) return rc;
   if ((rc = build(ctx, s)) != SEM_OK) return rc;
   GMG_CK(prepare_operator(ctx, s));
   Gmg& g = *ctx->gmg;
   if ((rc = set_alpha(ctx, g, alpha, s)) != SEM_OK) return rc;
   if (g.precision == SEM_PREC_FP64)
-    return pcg_t<double>(ctx, g, alpha, b, x, rtol, atol, maxit, iters, final_res, stats, ax0 != nullptr, s);
-  return pcg_t<float>(ctx, g, alpha, b, x, rtol, atol, maxit, iters, final_res, stats, ax0 != nullptr, s);
+    return pcg_t<double>(ctx, g, alpha, b, x, rtol, atol, maxit, iters, final_res, stats, ax0 != nullptr,
+                         ax0_ok != nullptr, s);
+  return pcg_t<float>(ctx, g, alpha, b, x, rtol, atol, maxit, iters, final_res, stats, ax0 != nullptr,
+                      ax0_ok != nullptr, s);
 }
 
 int gmg_vcycle(sem_ctx* ctx, double alpha, const double* r, double* z, cudaStream_t s) {

@@ -227,6 +227,12 @@ __global__ void __launch_bounds__(kVecThreads)
   }
 }
 
+// With `same` set (sem_step_host_out), x0 still holds the solution the last call
+// left there: a value that differs from the incoming u^n, bit for bit, clears *same.
+__device__ __forceinline__ void check_same(int* same, double old, double u) {
+  if (same != nullptr && __double_as_longlong(old) != __double_as_longlong(u)) *same = 0;
+}
+
 // Ionic parameters folded into the constants of the per-node arithmetic (host side):
 //   v = u* inv_amp + v_off            (v_off = -u_rest / u_amp)
 //   exponent = x_off - v inv_kappa    (x_off = v_gate / kappa)
@@ -256,7 +262,7 @@ __global__ void __launch_bounds__(kVecThreads)
                 const double* __restrict__ hn, const double* __restrict__ hnm1,
                 double* __restrict__ hnext, double* __restrict__ x0, double* __restrict__ out,
                 const double* __restrict__ mdiag, const double* __restrict__ mask, double iapp,
-                const IonicArgs prm, double dt, int first) {
+                const IonicArgs prm, double dt, int first, int* same) {
   pdl_entry();
   const double inv_dt = 1.0 / dt, inv_2dt = 0.5 / dt;
   const double c_open = (first ? dt : 2.0 * dt) * prm.inv_tau_open;
@@ -278,6 +284,7 @@ __global__ void __launch_bounds__(kVecThreads)
     double g = first ? fma(u0, inv_dt, -iion) : fma(fma(4.0, u0, -u1), inv_2dt, -iion);
     if (mask != nullptr) g += iapp * mask[i];
     hnext[i] = h;
+    if (same != nullptr) check_same(same, x0[i], u0);
     x0[i] = u0;
     out[i] = mdiag ? mdiag[i] * g : g;
   }
@@ -323,12 +330,13 @@ __global__ void __launch_bounds__(kVecThreads)
                    const double* __restrict__ hn, const double* __restrict__ hnm1,
                    double* __restrict__ hnext, double* __restrict__ x0, double* __restrict__ out,
                    const double* __restrict__ mdiag, const double* __restrict__ mask,
-                   const IonicDfArgs P, int first) {
+                   const IonicDfArgs P, int first, int* same) {
   pdl_entry();
 #pragma unroll 1
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double u0d = un[i];
+    if (same != nullptr) check_same(same, x0[i], u0d);
     // the stimulus mask holds 0 or 1
     const bool stim = mask != nullptr && __double2hiint(mask[i]) != 0;
     ionic_df_node(u0d, first ? 0.0 : unm1[i], hn[i], first ? 0.0 : hnm1[i], mdiag ? mdiag[i] : 0.0,
@@ -346,12 +354,13 @@ __global__ void __launch_bounds__(kVecThreads)
                     const double2* __restrict__ hn, const double2* __restrict__ hnm1,
                     double2* __restrict__ hnext, double2* __restrict__ x0, double2* __restrict__ out,
                     const double2* __restrict__ mdiag, const double2* __restrict__ mask,
-                    const IonicDfArgs P, int first) {
+                    const IonicDfArgs P, int first, int* same) {
   pdl_entry();
   if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
     const int64_t t = n - 1;
     auto r = [](const double2* q, int64_t i) { return reinterpret_cast<const double*>(q)[i]; };
     const double u0 = r(un, t);
+    if (same != nullptr) check_same(same, reinterpret_cast<const double*>(x0)[t], u0);
     ionic_df_node(u0, first ? 0.0 : r(unm1, t), r(hn, t), first ? 0.0 : r(hnm1, t),
                   mdiag ? r(mdiag, t) : 0.0, mdiag != nullptr, mask != nullptr && __double2hiint(r(mask, t)) != 0,
                   P, first, reinterpret_cast<double*>(hnext)[t], reinterpret_cast<double*>(out)[t]);
@@ -374,6 +383,11 @@ __global__ void __launch_bounds__(kVecThreads)
                   rr.y);
     hnext[i] = hh;
     out[i] = rr;
+    if (same != nullptr) {
+      const double2 old = x0[i];
+      check_same(same, old.x, u0.x);
+      check_same(same, old.y, u0.y);
+    }
     x0[i] = u0;
   }
 }
@@ -475,6 +489,8 @@ int ensure_workspace(sem_ctx* ctx) {
   const int ag = std::max(1, apply_grid_blocks(ctx->L));
   SEM_CK(cudaMalloc(&w.apply_partials, sizeof(double) * ag));
   SEM_CK(cudaMalloc(&w.dot_result, sizeof(double)));
+  SEM_CK(cudaMalloc(&w.same, sizeof(int)));
+  SEM_CK(cudaMallocHost(&w.same_host, sizeof(int)));
   w.inv_alpha = -1.0;
   w.ready = true;
   return SEM_OK;
@@ -623,7 +639,7 @@ int apply_tc(sem_ctx* ctx, double alpha, double beta, const float* u, float* y, 
 
 int cg_solve(sem_ctx* ctx, double alpha, const double* b, double* x, double rtol, double atol,
              int maxit, int precond, int* iters, double* final_res, sem_stats* stats,
-             cudaStream_t s, double* ax0) {
+             cudaStream_t s, double* ax0, const int* ax0_ok) {
   int rc = ensure_workspace(ctx);
   if (rc != SEM_OK) return rc;
   SEM_CK(prepare_operator(ctx, s));
@@ -641,10 +657,11 @@ int cg_solve(sem_ctx* ctx, double alpha, const double* b, double* x, double rtol
     }
     inv = w.invdiag;
   } else if (precond == SEM_PC_GMG) {
-    return gmg_pcg(ctx, alpha, b, x, rtol, atol, maxit, iters, final_res, stats, s, ax0);
+    return gmg_pcg(ctx, alpha, b, x, rtol, atol, maxit, iters, final_res, stats, s, ax0, ax0_ok);
   } else if (precond != SEM_PC_NONE) {
     return fail(ctx, SEM_ERR_ARG, "unknown preconditioner");
   }
+  if (ax0_ok != nullptr) ax0 = nullptr;  // no device-side choice here: apply the operator
   // Ap = A x (or the carried ax0), then the initial residual; Ap is zero for the iterations
   SEM_CK(cudaMemsetAsync(w.Ap, 0, sizeof(double) * n, s));
   if (ax0 == nullptr) {
@@ -785,6 +802,13 @@ int time_steps(sem_ctx* ctx, sem_state* st, double dt, int nsteps, double rtol, 
   }
   for (int k = 0; k < nsteps; ++k) {
     const int first = st->n == 0 ? 1 : 0;
+    const double alpha = first ? 1.0 / dt : 1.5 / dt;
+    sem_ctx::ResidualCarry& cy = ctx->carry;
+    const bool carried = cy.valid && cy.st == st && cy.n == st->n && cy.alpha == alpha &&
+                         cy.precond == precond && cy.age < kCarrySteps;
+    // a carry that depends on the caller's u^n: checked by the ionic update
+    int* same = carried ? cy.same : nullptr;
+    if (same != nullptr) SEM_CK(cudaMemsetAsync(same, 0x01, sizeof(int), s));
     const double t1 = (double)(st->n + 1) * dt;
     const bool on = ctx->stim_mask != nullptr && t1 > ctx->stim_on && t1 <= ctx->stim_off;
     double* out = L.quad == SEM_QUAD_LGL ? w.b : w.g;
@@ -806,16 +830,16 @@ int time_steps(sem_ctx* ctx, sem_state* st, double dt, int nsteps, double rtol, 
         auto w2 = [](double* q) { return reinterpret_cast<double2*>(q); };
         launch_k(k_ionic_rhs_df2, vec_grid(n / 2 + 1), kVecThreads, 0, s, n, d2(st->U[st->cur]),
                  d2(st->U[st->prev]), d2(st->H[st->cur]), d2(st->H[st->prev]), w2(st->H[st->next]),
-                 w2(st->U[st->next]), w2(out), d2(md), d2(mk), idf, first);
+                 w2(st->U[st->next]), w2(out), d2(md), d2(mk), idf, first, same);
       } else {
         launch_k(k_ionic_rhs_df, vg, kVecThreads, 0, s, n, st->U[st->cur], st->U[st->prev], st->H[st->cur],
-                 st->H[st->prev], st->H[st->next], st->U[st->next], out, md, mk, idf, first);
+                 st->H[st->prev], st->H[st->next], st->U[st->next], out, md, mk, idf, first, same);
       }
     } else {
       launch_k(k_ionic_rhs, vg, kVecThreads, 0, s,
           n, st->U[st->cur], st->U[st->prev], st->H[st->cur], st->H[st->prev], st->H[st->next],
           st->U[st->next], out, L.quad == SEM_QUAD_LGL ? L.mdiag : nullptr,
-          on ? ctx->stim_mask : nullptr, on ? ctx->stim_amp : 0.0, ia, dt, first);
+          on ? ctx->stim_mask : nullptr, on ? ctx->stim_amp : 0.0, ia, dt, first, same);
     }
     SEM_CK(cudaGetLastError());
     ctx->launches += 1;
@@ -831,14 +855,11 @@ int time_steps(sem_ctx* ctx, sem_state* st, double dt, int nsteps, double rtol, 
       rc = apply_fp64(ctx, 1.0, 0.0, w.g, w.b, s);
       if (rc != SEM_OK) return rc;
     }
-    const double alpha = first ? 1.0 / dt : 1.5 / dt;
-    sem_ctx::ResidualCarry& cy = ctx->carry;
-    const bool carried = cy.valid && cy.st == st && cy.n == st->n && cy.alpha == alpha &&
-                         cy.precond == precond && cy.age < kCarrySteps;
     cy.valid = false;
     rc = cg_solve(ctx, alpha, w.b, st->U[st->next], rtol, atol, maxit, precond, nullptr, nullptr,
-                  stats, s, carried ? w.Ax : nullptr);
+                  stats, s, carried ? w.Ax : nullptr, same);
     if (rc != SEM_OK) return rc;
+    if (stats && carried && same == nullptr) stats->carried_solves += 1;  // checked ones: by the caller
     // A u^{n+1} = b - r for the next step's initial residual (the multigrid PCG with
     // the double-float operator keeps r as float pairs)
     if (precond == SEM_PC_GMG && ctx->op_precision == SEM_PREC_DF64)  // kept as float pairs too

@@ -318,6 +318,76 @@ def test_carried_initial_residual(precond):
     g.close()
 
 
+@pytest.mark.parametrize("op", [capi.SEM_PREC_DF64, capi.SEM_PREC_FP64])
+@pytest.mark.parametrize("layout", ["pinned", "pageable"])
+def test_step_host_out_checked_carry(op, layout):
+    """sem_step_host_out with the multigrid PCG carries the initial residual from
+    one call to the next when the caller passes back the u_next it got (checked
+    on the device, bit for bit): the same carried-solve counts as sem_step (none
+    for the BDF1 step and the step after it, whose operator differs), the same
+    solution to the solver tolerance, and the oracle's 8 steps; a u changed by the
+    caller, or a call that does not continue the last one, applies the operator."""
+    s, tissue, g, o = _small(2, "LGL")
+    g.set_ionic()
+    box = (0.0, 0.0, 0.0, 1.5, 1.5, 1.5)
+    g.set_stimulus("box", box, 50.0, 0.0, 1.0)
+    capi.sem_set_operator_precision(g.ctx, op)
+    capi.sem_set_gmg(g.ctx, 3, 10, 100, capi.SEM_PREC_FP32_BF16)
+    nsteps, dt, rtol = 8, 0.05, 1e-13
+    st = g.new_state(-85.0, 1.0)
+    dev = st.step(dt, nsteps, rtol=rtol, maxit=2000, precond=capi.SEM_PC_GMG)
+    assert dev.carried_solves == nsteps - 2
+    ud, hd, _ = st.get()
+    st.close()
+
+    def arr(v):
+        t = torch.full((o.ndofs,), v, dtype=torch.float64)
+        return t.pin_memory() if layout == "pinned" else t
+
+    us = [arr(-85.0), arr(-85.0), arr(0.0)]  # u^{n-1}, u^n, free
+    hs = [arr(1.0), arr(1.0), arr(0.0)]
+    counts = []
+    for n in range(nsteps):
+        stt = capi.sem_step_host_out(g.ctx, us[1], us[0], hs[1], hs[0], us[2], hs[2], n, dt, rtol, 0.0, 2000,
+                                     capi.SEM_PC_GMG)
+        counts.append(stt.carried_solves)
+        us = [us[1], us[2], us[0]]
+        hs = [hs[1], hs[2], hs[0]]
+    assert counts == [0, 0] + [1] * (nsteps - 2), counts
+    assert rel(us[1].numpy(), ud.cpu().numpy()) < 1e-11 and rel(hs[1].numpy(), hd.cpu().numpy()) < 1e-13
+    ref = _oracle_run(o, tissue, dt, nsteps, ("box", box), 50.0, 1.0)
+    assert rel(us[1].numpy(), ref["u"]) < 1e-10
+
+    def step_from(u, u_prev, h, h_prev, n):
+        un, hn = arr(0.0), arr(0.0)
+        stt = capi.sem_step_host_out(g.ctx, u, u_prev, h, h_prev, un, hn, n, dt, rtol, 0.0, 2000,
+                                     capi.SEM_PC_GMG)
+        return stt.carried_solves, un, hn
+
+    # u changed by the caller in one entry: the operator is applied
+    u_mod = us[1].clone()
+    u_mod[o.ndofs // 2] += 1e-3
+    u_mod = u_mod.pin_memory() if layout == "pinned" else u_mod
+    c, un, hn = step_from(u_mod, us[0], hs[1], hs[0], nsteps)
+    assert c == 0
+    # the same n again does not continue the last call: no carry, the same result
+    c2, un2, hn2 = step_from(u_mod, us[0], hs[1], hs[0], nsteps)
+    assert c2 == 0 and rel(un2.numpy(), un.numpy()) < 1e-12
+    # continuing from what that call returned carries again
+    un2 = un2.pin_memory() if layout == "pinned" else un2
+    hn2 = hn2.pin_memory() if layout == "pinned" else hn2
+    c3, _, _ = step_from(un2, u_mod, hn2, hs[1], nsteps + 1)
+    assert c3 == 1
+    # the step from the changed u agrees with the same step of a state set from those arrays
+    st = g.new_state(0.0, 0.0)
+    st.restore(dict(u=u_mod.cuda(), u_prev=us[0].cuda(), h=hs[1].cuda(), h_prev=hs[0].cuda(), n=nsteps))
+    st.step(dt, 1, rtol=rtol, maxit=2000, precond=capi.SEM_PC_GMG)
+    ur, hr, _ = st.get()
+    st.close()
+    assert rel(un.numpy(), ur.cpu().numpy()) < 1e-11 and rel(hn.numpy(), hr.cpu().numpy()) < 1e-13
+    g.close()
+
+
 def test_ionic_parameters_reach_the_kernel():
     prm = dict(ionic.DEFAULT_PARAMS)
     prm["tau_out"] = 3.0
