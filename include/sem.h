@@ -52,6 +52,8 @@ extern "C" {
 #define SEM_ERR_NONFINITE (-5)     /* NaN or Inf met in a CG inner product */
 #define SEM_ERR_UNSUPPORTED (-6)   /* valid request that this library does not provide */
 #define SEM_ERR_NOMEM (-7)         /* device allocation failed */
+#define SEM_ERR_TIMEOUT (-8)       /* a kernel's bounded wait for its own copy gave up (reported by the
+                                      next multigrid solve; the context stays usable) */
 
 #define SEM_QUAD_LG 0  /* SEM: (p+1)-point Legendre-Gauss quadrature */
 #define SEM_QUAD_LGL 1 /* SEM-NI: (p+1)-point Legendre-Gauss-Lobatto quadrature */

@@ -22,6 +22,7 @@ SEM_ERR_NOT_CONVERGED = -4
 SEM_ERR_NONFINITE = -5
 SEM_ERR_UNSUPPORTED = -6
 SEM_ERR_NOMEM = -7
+SEM_ERR_TIMEOUT = -8
 
 SEM_QUAD_LG = 0
 SEM_QUAD_LGL = 1
@@ -40,6 +41,7 @@ ERROR_NAMES = {
     SEM_ERR_ARG: "SEM_ERR_ARG", SEM_ERR_CUDA: "SEM_ERR_CUDA", SEM_ERR_BAD_MESH: "SEM_ERR_BAD_MESH",
     SEM_ERR_NOT_CONVERGED: "SEM_ERR_NOT_CONVERGED", SEM_ERR_NONFINITE: "SEM_ERR_NONFINITE",
     SEM_ERR_UNSUPPORTED: "SEM_ERR_UNSUPPORTED", SEM_ERR_NOMEM: "SEM_ERR_NOMEM",
+    SEM_ERR_TIMEOUT: "SEM_ERR_TIMEOUT",
 }
 
 # Every symbol include/sem.h declares.

@@ -104,6 +104,7 @@ void free_ctx(sem_ctx* ctx) {
   gmg_free(ctx);
   tape_free(ctx);
   cudaFree(ctx->L.dbg);  // shared with the multigrid levels, freed once here
+  cudaFree(ctx->L.fault);  // the same
   level_free(ctx->L);
   cudaFree(ctx->sigma_l);
   cudaFree(ctx->sigma_t);
@@ -122,6 +123,7 @@ void free_ctx(sem_ctx* ctx) {
   cudaFree(w.dot_result);
   cudaFree(w.same);
   if (w.same_host) cudaFreeHost(w.same_host);
+  if (w.fault_host) cudaFreeHost(w.fault_host);
 }
 
 __global__ void k_fill(int64_t n, double v, double* x) {
@@ -158,6 +160,8 @@ int build_level(sem_ctx* ctx, int nx, int ny, int nz, const double* vertices, in
   SEM_CK(cudaGetLastError());
   SEM_CK(cudaMalloc(&ctx->d_flag, sizeof(int)));
   SEM_CK(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), s));
+  SEM_CK(cudaMalloc(&L.fault, sizeof(unsigned)));
+  SEM_CK(cudaMemsetAsync(L.fault, 0, sizeof(unsigned), s));
 #ifdef SEM_DEBUG
   SEM_CK(cudaMalloc(&L.dbg, sizeof(unsigned long long)));
   SEM_CK(cudaMemsetAsync(L.dbg, 0, sizeof(unsigned long long), s));

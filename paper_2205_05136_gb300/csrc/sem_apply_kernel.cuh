@@ -520,13 +520,14 @@ __global__ void __launch_bounds__(kApplyThreads)
 // (unit j of the warp is unit w + j W, W warps in the grid) and keeps the
 // copies of unit j+1 in flight while it computes unit j:
 //   - the unit's metric block, contiguous in the element-blocked layout
-//     (16-byte aligned), by 16-byte cp.async;
+//     (16-byte aligned), by one bulk copy (cp.async.bulk) that lane 0 issues;
 //   - the unit's nodal values, gathered by plain loads into registers from the
 //     map entries (loaded one unit earlier still) and stored to the stage after
 //     this unit's sweeps.  Each lane gathers (and later scatters) the n nodes of
 //     its z-column: for each level the lanes read consecutive map entries.
-// Two stage buffers per warp; a stage is complete after cp.async.wait_group
-// and visible to the whole warp after __syncwarp.  The grid is persistent
+// Two stage buffers per warp; a stage's metric is complete when its mbarrier's
+// phase completes (every lane waits on it), its nodal values after __syncwarp.
+// The grid is persistent
 // (the CTAs that are resident at once, 3 per SM), so the pipeline runs over
 // several units.
 //
@@ -549,11 +550,14 @@ struct PipeCfg {
   static constexpr int TW = 32 * N;                  // words of a unit tile (pipe_word)
   static constexpr int MV = G * BLK;                 // metric values of a unit
   static constexpr int CH = (int)(MV * sizeof(MT) / 16);  // 16-byte chunks of a unit's metric
-  // two metric stages, two nodal stages and the two work tiles of the sweeps
-  static constexpr size_t warp_bytes = 2 * (size_t)MV * sizeof(MT) + 4 * (size_t)TW * sizeof(float);
+  // two metric stages, two nodal stages, the two work tiles of the sweeps and the
+  // two metric stages' mbarriers
+  static constexpr size_t bar_offset = 2 * (size_t)MV * sizeof(MT) + 4 * (size_t)TW * sizeof(float);
+  static constexpr size_t warp_bytes = bar_offset + 2 * sizeof(uint64_t);
   static constexpr size_t cta_bytes = kWarpsPerCta * warp_bytes;
   static_assert(NL <= 32, "a unit must have at most 32 lines per direction");
   static_assert((MV * sizeof(MT)) % 16 == 0, "stage buffers must stay 16-byte aligned");
+  static_assert(bar_offset % 16 == 0 && warp_bytes % 16 == 0, "mbarriers and warp regions stay aligned");
 };
 
 // Word of node (i, j, k) of element slot s in a unit tile: row i of 32 words,
@@ -568,14 +572,40 @@ __device__ __forceinline__ int pipe_word(int s, int i, int j, int k) {
   return 32 * i + s * N * N + N * jj + kk;
 }
 
-__device__ __forceinline__ void cp_async_16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
-               "l"(src)
-               : "memory");
+// The metric block of a unit reaches shared memory by one bulk copy (the TMA
+// engine, cp.async.bulk), which writes shared memory without going through the
+// L1 data pipe that bounds this kernel (16-byte cp.async copies of the same
+// block took about 40 of that pipe's cycles per element).  Each of a warp's two
+// stages has an mbarrier of count 1: lane 0 arrives with the expected byte count
+// and the copy's completion ends the phase.
+// Shared-memory addresses are passed as 32-bit shared-window offsets.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int K>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory"); }
+__device__ __forceinline__ void bulk_copy(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+// Waits for the phase of the given parity to complete; false when it has not after
+// kMbarSpins polls (the copy is a few microseconds at most: the bound only turns a
+// fault into an error status).
+constexpr int kMbarSpins = 1 << 22;
+__device__ __forceinline__ bool mbar_wait(unsigned a, unsigned parity) {
+  for (int it = 0; it < kMbarSpins; ++it) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
 
 // Map entries of the lane's z-column of unit `unit`: node zc + n^2 t of the unit
 // for t < n (zc = slot s n^3 + column (i + n j)); 0 for elements past the mesh.
@@ -590,23 +620,17 @@ __device__ __forceinline__ void pipe_load_map(const ApplyArgs<float, MT>& a, int
     m[t] = present ? (int)SEM_IDX(__ldg(src + t * C::N2), a.ndofs, a.dbg, kDbgGather) : 0;
 }
 
-// Issues the cp.async copies of one unit's metric block into a stage.
+// Lane 0 issues the bulk copy of one unit's metric block (the elements of the unit
+// inside the mesh: a multiple of 16 bytes from a 16-byte aligned address) into a
+// stage.
 template <int P, typename MT>
-__device__ __forceinline__ void pipe_issue_metric(const ApplyArgs<float, MT>& a, int unit, int lane, MT* sM) {
+__device__ __forceinline__ void pipe_issue_metric(const ApplyArgs<float, MT>& a, int unit, int lane,
+                                                  unsigned sM, unsigned bar) {
   using C = PipeCfg<P, MT>;
   const int e0 = unit * C::G;
-  const char* src = reinterpret_cast<const char*>(a.metric + (size_t)e0 * C::BLK);
-  char* dst = reinterpret_cast<char*>(sM);
-  if (e0 + C::G <= a.nelem) {
-#pragma unroll
-    for (int t = 0; t < (C::CH + 31) / 32; ++t) {
-      const int c = lane + 32 * t;
-      if (C::CH % 32 == 0 || c < C::CH) cp_async_16(dst + 16 * c, src + 16 * c);
-    }
-  } else {
-    const int chunks = (int)((size_t)(a.nelem - e0) * C::BLK * sizeof(MT) / 16);
-    for (int c = lane; c < chunks; c += 32) cp_async_16(dst + 16 * c, src + 16 * c);
-  }
+  if (lane == 0)
+    bulk_copy(sM, a.metric + (size_t)e0 * C::BLK, (unsigned)(min(C::G, a.nelem - e0) * C::BLK * (int)sizeof(MT)),
+              bar);
 }
 
 // One 1-D line of n values at tile words off[]: dst = M src (ACC: dst += M src),
@@ -655,6 +679,16 @@ __global__ void __launch_bounds__(kApplyThreads, P <= 2 ? 4 : 3)
   T* sU0 = reinterpret_cast<T*>(wb + 2 * (size_t)C::MV * sizeof(MT));
   T* sB = sU0 + 2 * C::TW;
   T* sC = sB + C::TW;
+  // the two metric stages and their mbarriers, as shared-window offsets
+  const unsigned sm_s = smem_u32(sM0), bar_s = smem_u32(wb + C::bar_offset);
+  constexpr unsigned kStageBytes = (unsigned)(C::MV * sizeof(MT));
+  if (lane == 0) {
+    mbar_init(bar_s);
+    mbar_init(bar_s + 8);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncwarp();
+  unsigned phase = 0;  // bit s: parity of stage s's next completion
 
   // The lane's lines (those of lane - (32 - NL) for the lanes >= NL, a lane of the
   // same half-warp, so that the 64-bit metric loads of the idle lanes are
@@ -677,7 +711,7 @@ __global__ void __launch_bounds__(kApplyThreads, P <= 2 ? 4 : 3)
   int mc[N], mn[N], mnn[N];  // map entries of the lane's z-column in units j, j+1, j+2
   pipe_load_map<P>(a, unit, nunits, ls, zc, mc);
   float gv[N];  // the next unit's gathered values, in flight during this unit's sweeps
-  pipe_issue_metric<P>(a, unit, lane, sM0);
+  pipe_issue_metric<P>(a, unit, lane, sm_s, bar_s);
   {
     const bool present = unit * G + ls < a.nelem;
 #pragma unroll
@@ -686,20 +720,24 @@ __global__ void __launch_bounds__(kApplyThreads, P <= 2 ? 4 : 3)
     for (int t = 0; t < N; ++t)
       if (act) sU0[oz[t]] = gv[t];
   }
-  cp_async_commit();
   pipe_load_map<P>(a, unit + tw, nunits, ls, zc, mn);
   int b = 0;
   for (; unit < nunits; unit += tw) {
     const int nxt = unit + tw;
     if (nxt < nunits) {
-      pipe_issue_metric<P>(a, nxt, lane, sM0 + (b ^ 1) * C::MV);
+      pipe_issue_metric<P>(a, nxt, lane, sm_s + (b ^ 1) * kStageBytes, bar_s + 8 * (b ^ 1));
       const bool present = nxt * G + ls < a.nelem;
 #pragma unroll
       for (int t = 0; t < N; ++t) gv[t] = present ? __ldg(a.u + mn[t]) : 0.f;
     }
-    cp_async_commit();  // possibly empty group: keeps "all but the newest group" = stage b
     pipe_load_map<P>(a, nxt + tw, nunits, ls, zc, mnn);
-    cp_async_wait<1>();
+    if (!mbar_wait(bar_s + 8 * b, (phase >> b) & 1u)) {
+      // the copy did not complete: report it, let the other stage's copy land, stop
+      if (lane == 0 && a.fault != nullptr) atomicOr(a.fault, 1u);
+      if (nxt < nunits) mbar_wait(bar_s + 8 * (b ^ 1), (phase >> (b ^ 1)) & 1u);
+      return;
+    }
+    phase ^= 1u << b;
     __syncwarp();
 
     T* sA = sU0 + b * C::TW;
@@ -781,7 +819,6 @@ __global__ void __launch_bounds__(kApplyThreads, P <= 2 ? 4 : 3)
     }
     b ^= 1;
   }
-  cp_async_wait<0>();
 }
 
 // Persistent grid of the pipelined kernel: the CTAs resident on the device at
@@ -894,6 +931,7 @@ cudaError_t launch_apply_t(const Level& L, const ApplyArgs<T, MT>& a, bool mass_
   ApplyArgs<T, MT> b = a;
   b.ndofs = L.ndofs;
   b.dbg = L.dbg;
+  b.fault = L.fault;
   const cudaError_t e = launch_apply_kernels<P, QUAD, T, MT>(L, b, tab, mass_only, dot, s);
   if (e != cudaSuccess || a.yloc == nullptr) return e;
   return launch_assemble(L, a.yloc, a.y, a.done, s);

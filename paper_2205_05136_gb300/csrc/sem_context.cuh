@@ -25,6 +25,7 @@ struct Workspace {
   double* dot_result = nullptr;       // 1 double
   int* same = nullptr;        // device flag of sem_step_host_out's carry check (sem_ctx::carry)
   int* same_host = nullptr;   // page-locked copy, read after the call
+  unsigned* fault_host = nullptr;  // page-locked copy of the level's wait-timeout word
 };
 
 struct Gmg;   // geometric multigrid hierarchy (sem_gmg.cu)

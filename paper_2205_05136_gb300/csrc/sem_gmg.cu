@@ -1219,6 +1219,7 @@ int build(sem_ctx* ctx, cudaStream_t s) {
     g->lv.push_back(V);
     GMG_CK(level_create(*g->lv.back().L, nx, ny, nz, verts.data(), pc, quad, false, s));
     g->lv.back().L->dbg = ctx->L.dbg;
+    g->lv.back().L->fault = ctx->L.fault;
     GMG_CK(setup_geometry(*g->lv.back().L, V.sl, V.st, V.th, ctx->d_flag, s));
     GMG_CK(setup_diagonals(*g->lv.back().L, s));
     p = pc;
@@ -1250,6 +1251,7 @@ int build(sem_ctx* ctx, cudaStream_t s) {
     g->lv.push_back(V);
     GMG_CK(level_create(*g->lv.back().L, cx, cy, cz, cv.data(), 1, quad, false, s));
     g->lv.back().L->dbg = ctx->L.dbg;
+    g->lv.back().L->fault = ctx->L.fault;
     GMG_CK(setup_geometry(*g->lv.back().L, V.sl, V.st, V.th, ctx->d_flag, s));
     GMG_CK(setup_diagonals(*g->lv.back().L, s));
     verts.swap(cv);
@@ -1480,7 +1482,14 @@ int pcg_t(sem_ctx* ctx, Gmg& g, double alpha, const double* b, double* x, double
   }
   while (true) {
     GMG_CK(cudaMemcpyAsync(w.cg_host, w.cg, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+    GMG_CK(cudaMemcpyAsync(w.fault_host, ctx->L.fault, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     GMG_CK(cudaStreamSynchronize(s));
+    if (*w.fault_host != 0u) {  // an apply kernel gave up waiting for its metric copy
+      *w.fault_host = 0u;
+      GMG_CK(cudaMemsetAsync(ctx->L.fault, 0, sizeof(unsigned), s));
+      GMG_CK(cudaStreamSynchronize(s));
+      return fail(ctx, SEM_ERR_TIMEOUT, "an apply kernel's wait for its metric copy timed out");
+    }
     if (tm.enabled && launched > 0 && w.cg_host->iters == launched) {
       float ms = 0.f;
       if (cudaEventElapsedTime(&ms, g.ev0, g.ev1) == cudaSuccess) {

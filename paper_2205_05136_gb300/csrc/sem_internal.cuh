@@ -186,6 +186,7 @@ struct Level {
   uint32_t* tc_frag = nullptr;    // constant MMA fragments of the tensor-core kernel
   bool metric32_valid = false, metric16_valid = false, metric2_valid = false, metric_tc_valid = false;
   unsigned long long* dbg = nullptr;  // SEM_DEBUG build: the context's index-error word
+  unsigned* fault = nullptr;  // the context's wait-timeout word (nonzero: a kernel gave up a wait)
   double* mdiag = nullptr;
   double* kdiag = nullptr;
   double* xyz = nullptr;
@@ -252,9 +253,11 @@ struct ApplyArgs {
   // atomic adds, and a node kernel then adds each node's contributions to y in a
   // fixed order
   typename VecOf<T>::type* yloc;
-  // set by the launcher: the vectors' length and the SEM_DEBUG index-error word
+  // set by the launcher: the vectors' length, the SEM_DEBUG index-error word and
+  // the wait-timeout word
   int64_t ndofs;
   unsigned long long* dbg;
+  unsigned* fault;
 };
 using ApplyArgs64 = ApplyArgs<double, double>;
 

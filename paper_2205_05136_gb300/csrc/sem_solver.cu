@@ -491,6 +491,8 @@ int ensure_workspace(sem_ctx* ctx) {
   SEM_CK(cudaMalloc(&w.dot_result, sizeof(double)));
   SEM_CK(cudaMalloc(&w.same, sizeof(int)));
   SEM_CK(cudaMallocHost(&w.same_host, sizeof(int)));
+  SEM_CK(cudaMallocHost(&w.fault_host, sizeof(unsigned)));
+  *w.fault_host = 0u;
   w.inv_alpha = -1.0;
   w.ready = true;
   return SEM_OK;
