@@ -352,6 +352,16 @@ int sem_apply_dot_static(sem_ctx* ctx, double alpha, double beta, const double* 
  * SEM_ERR_UNSUPPORTED.  Synchronous. */
 int sem_debug_set_map_entry(sem_ctx* ctx, int64_t entry, int value, int* previous);
 
+/* SEM_DEBUG build only (the normal build returns SEM_ERR_UNSUPPORTED): the
+ * pipelined FP32 apply of the fine level leaves out the metric copy of element
+ * group `group` (its group index; -1: none), so that the warp's bounded wait
+ * for that copy runs out.  That warp then sets the context's wait-timeout word,
+ * lets its other copy in flight land and returns, and the next multigrid solve
+ * returns SEM_ERR_TIMEOUT (its result is not used).  Exercises the timeout
+ * path without any fault.  Drops the multigrid hierarchy (its captured graphs
+ * hold the launch arguments); the next solve rebuilds it.  Synchronous. */
+int sem_debug_hold_copy(sem_ctx* ctx, int group);
+
 /* Enable (1) or disable (0) CUDA-event timing of the operator-apply kernels
  * inside sem_step / sem_cg_solve (reported in sem_stats). */
 int sem_set_timing(sem_ctx* ctx, int enable);

@@ -53,7 +53,7 @@ EXPORTS = [
     "sem_state_track_activation", "sem_state_get_activation",
     "sem_set_timing", "sem_apply_dot_static", "sem_set_gmg", "sem_vcycle", "sem_gmg_info",
     "sem_forward_record", "sem_adjoint_grad", "sem_set_operator_precision", "sem_set_deterministic",
-    "sem_debug_set_map_entry",
+    "sem_debug_set_map_entry", "sem_debug_hold_copy",
 ]
 
 
@@ -123,6 +123,7 @@ def lib():
             "sem_set_operator_precision": (_I, [_P, _I]),
             "sem_set_deterministic": (_I, [_P, _I]),
             "sem_debug_set_map_entry": (_I, [_P, _I64, _I, ctypes.POINTER(_I)]),
+            "sem_debug_hold_copy": (_I, [_P, _I]),
             "sem_forward_record": (_I, [_P, _P, _D, _I, _I, _P, _I, _P, _D, _D, _I, _I,
                                         ctypes.POINTER(sem_stats), _P]),
             "sem_adjoint_grad": (_I, [_P, _P, _P, _P, _P, _D, _D, _I, _I, ctypes.POINTER(sem_stats), _P]),
@@ -350,6 +351,12 @@ def sem_debug_set_map_entry(ctx, entry: int, value: int) -> int:
     old = _I()
     _check(lib().sem_debug_set_map_entry(ctx, int(entry), int(value), ctypes.byref(old)), ctx)
     return old.value
+
+
+def sem_debug_hold_copy(ctx, group: int):
+    """SEM_DEBUG build only: the pipelined FP32 apply leaves out the metric copy of
+    element group `group` (-1: none), so that its bounded wait runs out."""
+    return _check(lib().sem_debug_hold_copy(ctx, int(group)), ctx)
 
 
 def sem_set_deterministic(ctx, enable: bool):

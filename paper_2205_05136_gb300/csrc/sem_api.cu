@@ -792,6 +792,22 @@ int sem_debug_set_map_entry(sem_ctx* ctx, int64_t entry, int value, int* previou
 #endif
 }
 
+int sem_debug_hold_copy(sem_ctx* ctx, int group) {
+  CK_CTX(ctx);
+#ifdef SEM_DEBUG
+  if (group < -1) return fail(ctx, SEM_ERR_ARG, "group must be >= -1");
+  invalidate_carry(ctx);
+  DeviceGuard guard(ctx->device);
+  cudaDeviceSynchronize();
+  gmg_free(ctx);  // the multigrid graphs hold the launch arguments, this one included
+  ctx->L.hold = group;
+  return SEM_OK;
+#else
+  (void)group;
+  return fail(ctx, SEM_ERR_UNSUPPORTED, "sem_debug_hold_copy needs the SEM_DEBUG build");
+#endif
+}
+
 int sem_gmg_info(sem_ctx* ctx, double alpha, int max_levels, int* nlevels, int* p, int* dims,
                  int64_t* ndofs, double* lambda_max, void* stream) {
   CK_CTX(ctx);

@@ -590,21 +590,39 @@ __device__ __forceinline__ void bulk_copy(unsigned dst, const void* src, unsigne
       "l"(src), "r"(bytes), "r"(bar)
       : "memory");
 }
-// Waits for the phase of the given parity to complete; false when it has not after
-// kMbarSpins polls (the copy is a few microseconds at most: the bound only turns a
-// fault into an error status).
-constexpr int kMbarSpins = 1 << 22;
-__device__ __forceinline__ bool mbar_wait(unsigned a, unsigned parity) {
-  for (int it = 0; it < kMbarSpins; ++it) {
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (ok) return true;
+// Waits for the phase of the given parity to complete; false when it has not
+// within kMbarTimeoutNs of the global timer (the copy takes microseconds: the
+// bound only turns a copy that never completes into an error status).
+#ifdef SEM_DEBUG
+constexpr unsigned long long kMbarTimeoutNs = 20000000ull;  // 20 ms: a test of the timeout path ends quickly
+#else
+constexpr unsigned long long kMbarTimeoutNs = 1000000000ull;  // 1 s
+#endif
+__device__ __forceinline__ bool mbar_try(unsigned a, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+  return t;
+}
+// (the polling loop out of line: it keeps the hot loop's registers free)
+static __device__ __noinline__ bool mbar_wait_timed(unsigned a, unsigned parity) {
+  const unsigned long long t0 = global_ns();
+  while (true) {
+    for (int i = 0; i < 64; ++i)
+      if (mbar_try(a, parity)) return true;
+    if (global_ns() - t0 > kMbarTimeoutNs) return false;
   }
-  return false;
+}
+__device__ __forceinline__ bool mbar_wait(unsigned a, unsigned parity) {
+  return mbar_try(a, parity) || mbar_wait_timed(a, parity);
 }
 
 // Map entries of the lane's z-column of unit `unit`: node zc + n^2 t of the unit
@@ -628,7 +646,7 @@ __device__ __forceinline__ void pipe_issue_metric(const ApplyArgs<float, MT>& a,
                                                   unsigned sM, unsigned bar) {
   using C = PipeCfg<P, MT>;
   const int e0 = unit * C::G;
-  if (lane == 0)
+  if (lane == 0 && !SEM_HOLD(a, unit))
     bulk_copy(sM, a.metric + (size_t)e0 * C::BLK, (unsigned)(min(C::G, a.nelem - e0) * C::BLK * (int)sizeof(MT)),
               bar);
 }
@@ -932,6 +950,7 @@ cudaError_t launch_apply_t(const Level& L, const ApplyArgs<T, MT>& a, bool mass_
   b.ndofs = L.ndofs;
   b.dbg = L.dbg;
   b.fault = L.fault;
+  b.hold = L.hold;
   const cudaError_t e = launch_apply_kernels<P, QUAD, T, MT>(L, b, tab, mass_only, dot, s);
   if (e != cudaSuccess || a.yloc == nullptr) return e;
   return launch_assemble(L, a.yloc, a.y, a.done, s);

@@ -41,8 +41,12 @@ __device__ __forceinline__ int64_t dbg_index(int64_t g, int64_t n, unsigned long
   return 0;
 }
 #define SEM_IDX(g, n, word, kind) dbg_index((g), (n), (word), (kind))
+// a copy the SEM_DEBUG build leaves out on request (sem_debug_hold_copy), so that
+// the wait for it runs out and the timeout path runs
+#define SEM_HOLD(a, unit) ((unit) == (a).hold)
 #else
 #define SEM_IDX(g, n, word, kind) (g)
+#define SEM_HOLD(a, unit) false
 #endif
 
 // Programmatic dependent launch (PDL).  A kernel launched by launch_k may be
@@ -187,6 +191,7 @@ struct Level {
   bool metric32_valid = false, metric16_valid = false, metric2_valid = false, metric_tc_valid = false;
   unsigned long long* dbg = nullptr;  // SEM_DEBUG build: the context's index-error word
   unsigned* fault = nullptr;  // the context's wait-timeout word (nonzero: a kernel gave up a wait)
+  int hold = -1;  // SEM_DEBUG build: element group whose metric copy the pipelined apply skips
   double* mdiag = nullptr;
   double* kdiag = nullptr;
   double* xyz = nullptr;
@@ -258,6 +263,7 @@ struct ApplyArgs {
   int64_t ndofs;
   unsigned long long* dbg;
   unsigned* fault;
+  int hold;  // SEM_DEBUG build: Level::hold
 };
 using ApplyArgs64 = ApplyArgs<double, double>;
 

@@ -7,8 +7,11 @@ builds the variant (libsem_debug.so), runs it in a child process selected by
 SEM_LIBRARY, plants an out-of-range entry in the map through
 sem_debug_set_map_entry, and checks that the FP64 apply, the FP32 smoother
 apply, a multigrid V-cycle and a CG solve all report it; with the entry
-restored the results are again those of the clean run.  The normal build
-answers sem_debug_set_map_entry with SEM_ERR_UNSUPPORTED.
+restored the results are again those of the clean run.  The same child also
+holds back one metric copy of the pipelined apply (sem_debug_hold_copy): the
+bounded wait for it runs out and the multigrid solve returns SEM_ERR_TIMEOUT,
+after which the context solves as before.  The normal build answers both
+debug entry points with SEM_ERR_UNSUPPORTED.
 """
 import os
 import subprocess
@@ -67,6 +70,21 @@ assert float(torch.linalg.norm(y1f - y0f) / torch.linalg.norm(y0f)) < 1e-6
 z1 = torch.empty_like(u)
 capi.sem_vcycle(g.ctx, 30.0, u, z1)
 assert float(torch.linalg.norm(z1 - z0) / torch.linalg.norm(z0)) < 1e-6
+# the timeout path: the fine level's pipelined apply leaves out the metric copy of
+# element group 3, the wait for it runs out, the multigrid solve reports it, and
+# the context then solves as before
+xr = torch.zeros_like(u)
+capi.sem_cg_solve(g.ctx, 30.0, u, xr, 1e-10, 0.0, 100, capi.SEM_PC_GMG)
+capi.sem_debug_hold_copy(g.ctx, 3)
+try:
+    capi.sem_cg_solve(g.ctx, 30.0, u, torch.zeros_like(u), 1e-10, 0.0, 100, capi.SEM_PC_GMG)
+    raise AssertionError("no timeout reported")
+except capi.SemError as e:
+    assert e.code == capi.SEM_ERR_TIMEOUT, (e.code, str(e))
+capi.sem_debug_hold_copy(g.ctx, -1)
+x2 = torch.zeros_like(u)
+capi.sem_cg_solve(g.ctx, 30.0, u, x2, 1e-10, 0.0, 100, capi.SEM_PC_GMG)
+assert float(torch.linalg.norm(x2 - xr) / torch.linalg.norm(xr)) < 1e-12
 g.close()
 print("debug build ok")
 """
@@ -89,6 +107,9 @@ def test_normal_build_has_no_map_fault_injection():
     assert "SEM_DEBUG" not in capi.sem_version()
     with pytest.raises(capi.SemError) as ei:
         capi.sem_debug_set_map_entry(g.ctx, 0, 5)
+    assert ei.value.code == capi.SEM_ERR_UNSUPPORTED
+    with pytest.raises(capi.SemError) as ei:
+        capi.sem_debug_hold_copy(g.ctx, 0)
     assert ei.value.code == capi.SEM_ERR_UNSUPPORTED
     u = torch.zeros(g.ndofs, dtype=torch.float64, device="cuda")
     g.apply(u, 1.0, 1.0)  # the context is unaffected
