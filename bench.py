@@ -59,9 +59,9 @@ FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64: 152 SMs x 2 DFMA/clk x 2 flop x ~
 # p = 4 SEM-NI slab of 2,064,933 nodes, each with the hash of the kernel sources it
 # was taken from: a figure whose kernel sources have changed since is reported as
 # null (kernel_source_hash below).
-NCU_TRAFFIC = {(4, "LGL"): (273.06368e6 + 12.978176e6, "apply")}
-NCU_TRAFFIC_SMOOTHER = {(4, "LGL", "bf16"): (88.76288e6 + 2.049536e6, "apply")}
-NCU_SOURCE_HASH = {"apply": "557c7d0a61863979"}
+NCU_TRAFFIC = {(4, "LGL"): (273.06752e6 + 13.02912e6, "apply")}
+NCU_TRAFFIC_SMOOTHER = {(4, "LGL", "bf16"): (88.76544e6 + 2.226176e6, "apply")}
+NCU_SOURCE_HASH = {"apply": "8fd277dec311765f"}
 KERNEL_SOURCES = {"apply": ("sem_apply_kernel.cuh", "sem_apply_fp32.cu", "sem_apply_fp64.cu",
                             "sem_internal.cuh")}
 
