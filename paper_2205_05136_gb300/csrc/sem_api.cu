@@ -869,6 +869,7 @@ int sem_adjoint_grad(sem_ctx* ctx, const double* trace_bar, double* g_sigma_l, d
 int sem_set_timing(sem_ctx* ctx, int enable) {
   CK_CTX(ctx);
   ctx->timing.enabled = enable != 0;
+  ctx->timing.solves = 0;
   return SEM_OK;
 }
 

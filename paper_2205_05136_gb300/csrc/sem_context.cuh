@@ -38,7 +38,11 @@ struct Timing {
   int64_t count = 0;
   double smoother_ms = 0.0;   // fine-level multigrid smoother applies (one per V-cycle timed)
   int64_t smoother_count = 0;
+  int64_t solves = 0;         // multigrid solves since timing was enabled (every kTimingEvery-th is sampled)
 };
+// With timing on, the first PCG iteration of one multigrid solve in kTimingEvery
+// runs the graph with event nodes (each costs a few microseconds of the step).
+constexpr int kTimingEvery = 10;
 
 }  // namespace sem
 

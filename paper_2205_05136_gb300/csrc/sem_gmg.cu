@@ -70,7 +70,9 @@ struct Gmg {
     cudaGraphExec_t init = nullptr, iter = nullptr;
     cudaGraphExec_t init_carried = nullptr;  // set-up from the carried A x (ws.Ax)
     cudaGraphExec_t init_checked = nullptr;  // the same where ws.same reads nonzero, else applied
+    cudaGraphExec_t iter_timed = nullptr;    // an iteration with event nodes around two applies
     int64_t init_kernels = 0, iter_kernels = 0, init_carried_kernels = 0, init_checked_kernels = 0;
+    int64_t iter_timed_kernels = 0;
     int last_iters = 0;  // iterations the previous solve with these graphs took
   };
   Graphs graphs[16];
@@ -1178,6 +1180,7 @@ void free_gmg_struct(Gmg* g) {
     if (gr.iter) cudaGraphExecDestroy(gr.iter);
     if (gr.init_carried) cudaGraphExecDestroy(gr.init_carried);
     if (gr.init_checked) cudaGraphExecDestroy(gr.init_checked);
+    if (gr.iter_timed) cudaGraphExecDestroy(gr.iter_timed);
   }
   if (g->capture) cudaStreamDestroy(g->capture);
   if (g->ev0) cudaEventDestroy(g->ev0);
@@ -1362,15 +1365,19 @@ int pcg_init_seq(sem_ctx* ctx, Gmg& g, double alpha, const double* b, const doub
   return SEM_OK;
 }
 
+// timed: external event nodes around the fine-level residual apply of the V-cycle
+// (ev2, ev3) and the outer operator apply (ev0, ev1).  Each event node costs a few
+// microseconds of the step (it breaks the programmatic dependent launch around it),
+// so only the sampled iterations use the timed graph.
 template <typename T>
-int pcg_iter_seq(sem_ctx* ctx, Gmg& g, double alpha, double* x, cudaStream_t s) {
+int pcg_iter_seq(sem_ctx* ctx, Gmg& g, double alpha, double* x, bool timed, cudaStream_t s) {
   Workspace& w = ctx->ws;
   Level& L = ctx->L;
   const int64_t n = L.ndofs;
   const int gr = grid1d(n);
   const int stride = g.partial_len;
   const int* done = &w.cg->done;
-  int rc = vcycle(ctx, g, done, s, true);
+  int rc = vcycle(ctx, g, done, s, timed);
   if (rc != SEM_OK) return rc;
   // the double-float operator gathers p as the float pairs the p kernels write
   const bool dfop = ctx->op_precision == SEM_PREC_DF64;
@@ -1392,9 +1399,9 @@ int pcg_iter_seq(sem_ctx* ctx, Gmg& g, double alpha, double* x, cudaStream_t s) 
   ap.dot_partials = w.apply_partials; ap.cg = w.cg; ap.u2 = p2;
   ap.yloc = ctx->deterministic ? ctx->det_scratch : nullptr;
   // external records become event nodes of the captured graph (timing of the outer apply)
-  GMG_CK(cudaEventRecordWithFlags(g.ev0, s, cudaEventRecordExternal));
+  if (timed) GMG_CK(cudaEventRecordWithFlags(g.ev0, s, cudaEventRecordExternal));
   GMG_CK(launch_operator(ctx, ap, s));
-  GMG_CK(cudaEventRecordWithFlags(g.ev1, s, cudaEventRecordExternal));
+  if (timed) GMG_CK(cudaEventRecordWithFlags(g.ev1, s, cudaEventRecordExternal));
   if (dfop)
     launch_k(aligned16(x) ? k_dfpcg_xr<T, true> : k_dfpcg_xr<T, false>, std::min(gr, 152 * kXrCtasPerSm),
              kThreads, 0, s, n, x, p2, w.Ap, r2, (T*)g.lv[0].b, w.cg, g.partials, stride, g.tickets + 2);
@@ -1424,13 +1431,14 @@ int get_graphs(sem_ctx* ctx, Gmg& g, double alpha, const double* b, double* x, d
   if (gr.iter) { cudaGraphExecDestroy(gr.iter); gr.iter = nullptr; }
   if (gr.init_carried) { cudaGraphExecDestroy(gr.init_carried); gr.init_carried = nullptr; }
   if (gr.init_checked) { cudaGraphExecDestroy(gr.init_checked); gr.init_checked = nullptr; }
+  if (gr.iter_timed) { cudaGraphExecDestroy(gr.iter_timed); gr.iter_timed = nullptr; }
   cudaStream_t cs = g.capture;
   const int64_t l0 = ctx->launches;
-  for (int which = 0; which < 4; ++which) {
+  for (int which = 0; which < 5; ++which) {
     GMG_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    int rc = which == 1 ? pcg_iter_seq<T>(ctx, g, alpha, x, cs)
-                        : pcg_init_seq<T>(ctx, g, alpha, b, x, rtol, atol, which >= 2,
-                                          which == 3 ? ctx->ws.same : nullptr, cs);
+    int rc = (which == 1 || which == 4) ? pcg_iter_seq<T>(ctx, g, alpha, x, which == 4, cs)
+                                        : pcg_init_seq<T>(ctx, g, alpha, b, x, rtol, atol, which >= 2,
+                                                          which == 3 ? ctx->ws.same : nullptr, cs);
     cudaGraph_t graph = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
     if (rc != SEM_OK) {
@@ -1446,7 +1454,8 @@ int get_graphs(sem_ctx* ctx, Gmg& g, double alpha, const double* b, double* x, d
     if (which == 0) { gr.init = exec; gr.init_kernels = nk; }
     else if (which == 1) { gr.iter = exec; gr.iter_kernels = nk; }
     else if (which == 2) { gr.init_carried = exec; gr.init_carried_kernels = nk; }
-    else { gr.init_checked = exec; gr.init_checked_kernels = nk; }
+    else if (which == 3) { gr.init_checked = exec; gr.init_checked_kernels = nk; }
+    else { gr.iter_timed = exec; gr.iter_timed_kernels = nk; }
   }
   ctx->launches = l0;  // capture launched nothing; replays are counted
   gr.x = x;
@@ -1471,15 +1480,20 @@ int pcg_t(sem_ctx* ctx, Gmg& g, double alpha, const double* b, double* x, double
   Timing& tm = ctx->timing;
   bool done_h = false;
   int launched = 0;
+  // with timing on, the first iteration of one solve in kTimingEvery is the timed one
+  bool sample = tm.enabled && (tm.solves++ % kTimingEvery) == 0;
+  auto launch_iter = [&]() -> cudaError_t {
+    const bool timed = sample && launched == 0;
+    const cudaError_t e = cudaGraphLaunch(timed ? gr->iter_timed : gr->iter, s);
+    ctx->launches += timed ? gr->iter_timed_kernels : gr->iter_kernels;
+    return e;
+  };
   // Successive solves (time steps) take about the same number of iterations:
   // launch the previous count before reading the scalars, so that a solve that
   // needs no more costs one host round trip.  An iteration launched after
   // convergence runs kernels that return at once.
   const int ahead = std::min(maxit, std::max(0, gr->last_iters));
-  for (; launched < ahead; ++launched) {
-    GMG_CK(cudaGraphLaunch(gr->iter, s));
-    ctx->launches += gr->iter_kernels;
-  }
+  for (; launched < ahead; ++launched) GMG_CK(launch_iter());
   while (true) {
     GMG_CK(cudaMemcpyAsync(w.cg_host, w.cg, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
     GMG_CK(cudaMemcpyAsync(w.fault_host, ctx->L.fault, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
@@ -1490,7 +1504,8 @@ int pcg_t(sem_ctx* ctx, Gmg& g, double alpha, const double* b, double* x, double
       GMG_CK(cudaStreamSynchronize(s));
       return fail(ctx, SEM_ERR_TIMEOUT, "an apply kernel's wait for its metric copy timed out");
     }
-    if (tm.enabled && launched > 0 && w.cg_host->iters == launched) {
+    if (sample && launched > 0 && w.cg_host->iters >= 1) {  // the timed first iteration ran
+      sample = false;
       float ms = 0.f;
       if (cudaEventElapsedTime(&ms, g.ev0, g.ev1) == cudaSuccess) {
         tm.ms += ms;
@@ -1507,8 +1522,7 @@ int pcg_t(sem_ctx* ctx, Gmg& g, double alpha, const double* b, double* x, double
     }
     if (w.cg_host->done) { done_h = true; break; }
     if (launched >= maxit) break;
-    GMG_CK(cudaGraphLaunch(gr->iter, s));
-    ctx->launches += gr->iter_kernels;
+    GMG_CK(launch_iter());
     ++launched;
   }
   const CgScalars& h = *w.cg_host;

@@ -388,6 +388,29 @@ def test_step_host_out_checked_carry(op, layout):
     g.close()
 
 
+def test_timing_samples_one_solve_in_ten():
+    """With timing on, the multigrid PCG times the outer apply and the fine-level
+    residual apply in the first iteration of one solve in ten (the first after
+    enabling, then every tenth); with timing off nothing is timed."""
+    s, tissue, g, o = _small(2, "LGL")
+    g.set_ionic()
+    g.set_stimulus("box", (0.0, 0.0, 0.0, 1.5, 1.5, 1.5), 50.0, 0.0, 2.0)  # every step iterates
+    capi.sem_set_operator_precision(g.ctx, gb.SEM_PREC_DF64)
+    capi.sem_set_gmg(g.ctx, 3, 10, 100, capi.SEM_PREC_FP32_BF16)
+    st = g.new_state(-85.0, 1.0)
+    off = st.step(0.05, 5, rtol=1e-12, maxit=200, precond=capi.SEM_PC_GMG)
+    assert off.cg_iters >= 5
+    assert off.n_apply == 0 and off.n_smoother_apply == 0
+    g.set_timing(True)
+    on = st.step(0.05, 20, rtol=1e-12, maxit=200, precond=capi.SEM_PC_GMG)
+    assert on.cg_iters >= 20
+    assert on.n_apply == 2 and on.n_smoother_apply == 2, (on.n_apply, on.n_smoother_apply)
+    assert on.apply_ms > 0.0 and on.smoother_apply_ms > 0.0
+    g.set_timing(False)
+    st.close()
+    g.close()
+
+
 def test_ionic_parameters_reach_the_kernel():
     prm = dict(ionic.DEFAULT_PARAMS)
     prm["tau_out"] = 3.0
