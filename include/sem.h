@@ -363,10 +363,11 @@ int sem_debug_set_map_entry(sem_ctx* ctx, int64_t entry, int value, int* previou
 int sem_debug_hold_copy(sem_ctx* ctx, int group);
 
 /* Enable (1) or disable (0) CUDA-event timing of the operator-apply kernels
- * inside sem_step / sem_cg_solve (reported in sem_stats).  With the multigrid
- * preconditioner one solve in ten (the first after enabling, then every tenth)
- * times the outer operator apply and the fine-level residual apply of its first
- * iteration: the event nodes that bracket them cost a few microseconds each. */
+ * inside sem_step / sem_cg_solve (reported in sem_stats).  One solve in ten
+ * (the first after enabling, then every tenth) times the operator apply of its
+ * first iteration, and with the multigrid preconditioner also the fine-level
+ * residual apply of that iteration's V-cycle: the events that bracket them cost
+ * a few microseconds each, so the other solves run without them. */
 int sem_set_timing(sem_ctx* ctx, int enable);
 
 #ifdef __cplusplus

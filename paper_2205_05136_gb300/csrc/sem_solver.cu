@@ -686,13 +686,14 @@ int cg_solve(sem_ctx* ctx, double alpha, const double* b, double* x, double rtol
 
   Timing& tm = ctx->timing;
   constexpr int kChunkMax = 16;
-  std::vector<cudaEvent_t> evs;
-  if (tm.enabled) {
-    evs.resize(2 * kChunkMax);
-    for (auto& e : evs) SEM_CK(cudaEventCreate(&e));
+  // with timing on, the apply of the first iteration of one solve in kTimingEvery
+  // is bracketed by events (they interrupt the programmatic dependent launch)
+  bool sample = tm.enabled && (tm.solves++ % kTimingEvery) == 0;
+  if (sample && (tm.start == nullptr || tm.stop == nullptr)) {
+    if (tm.start == nullptr) SEM_CK(cudaEventCreate(&tm.start));
+    if (tm.stop == nullptr) SEM_CK(cudaEventCreate(&tm.stop));
   }
   int launched = 0;
-  int prev_iters = 0;
   int chunk = 4;
   bool done = false;
   int rc_out = SEM_OK;
@@ -700,9 +701,10 @@ int cg_solve(sem_ctx* ctx, double alpha, const double* b, double* x, double rtol
     const int this_chunk = std::min(chunk, maxit - launched);
     if (this_chunk > 0) {
       for (int c = 0; c < this_chunk; ++c) {
-        if (tm.enabled) SEM_CK(cudaEventRecord(evs[2 * c], s));
+        const bool timed = sample && launched == 0 && c == 0;
+        if (timed) SEM_CK(cudaEventRecord(tm.start, s));
         SEM_CK(launch_operator(ctx, ap, s));
-        if (tm.enabled) SEM_CK(cudaEventRecord(evs[2 * c + 1], s));
+        if (timed) SEM_CK(cudaEventRecord(tm.stop, s));
         if ((reinterpret_cast<uintptr_t>(x) & 15u) == 0)
           launch_k(k_cg_xr<true>, vg, kVecThreads, 0, s, n, x, w.p, w.Ap, w.r, inv, w.z, w.cg, w.vec_partials,
                                                    w.tickets + 0);
@@ -718,21 +720,17 @@ int cg_solve(sem_ctx* ctx, double alpha, const double* b, double* x, double rtol
     SEM_CK(cudaMemcpyAsync(w.cg_host, w.cg, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
     SEM_CK(cudaStreamSynchronize(s));
     const CgScalars& h = *w.cg_host;
-    if (tm.enabled && this_chunk > 0) {
-      const int worked = std::min(this_chunk, h.iters - prev_iters);
-      for (int c = 0; c < worked; ++c) {
-        float ms = 0.f;
-        SEM_CK(cudaEventElapsedTime(&ms, evs[2 * c], evs[2 * c + 1]));
-        tm.ms += ms;
-        tm.count += 1;
-      }
+    if (sample && h.iters >= 1) {  // the timed first iteration ran
+      sample = false;
+      float ms = 0.f;
+      SEM_CK(cudaEventElapsedTime(&ms, tm.start, tm.stop));
+      tm.ms += ms;
+      tm.count += 1;
     }
-    prev_iters = h.iters;
     if (h.done) { done = true; break; }
     if (launched >= maxit) break;
     chunk = std::min(kChunkMax, chunk * 2);
   }
-  for (auto& e : evs) cudaEventDestroy(e);
   const CgScalars& h = *w.cg_host;
   if (iters) *iters = h.iters;
   if (final_res) *final_res = std::sqrt(h.rr);

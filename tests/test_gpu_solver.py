@@ -391,7 +391,8 @@ def test_step_host_out_checked_carry(op, layout):
 def test_timing_samples_one_solve_in_ten():
     """With timing on, the multigrid PCG times the outer apply and the fine-level
     residual apply in the first iteration of one solve in ten (the first after
-    enabling, then every tenth); with timing off nothing is timed."""
+    enabling, then every tenth), the Jacobi CG the apply of that iteration; with
+    timing off nothing is timed."""
     s, tissue, g, o = _small(2, "LGL")
     g.set_ionic()
     g.set_stimulus("box", (0.0, 0.0, 0.0, 1.5, 1.5, 1.5), 50.0, 0.0, 2.0)  # every step iterates
@@ -406,6 +407,9 @@ def test_timing_samples_one_solve_in_ten():
     assert on.cg_iters >= 20
     assert on.n_apply == 2 and on.n_smoother_apply == 2, (on.n_apply, on.n_smoother_apply)
     assert on.apply_ms > 0.0 and on.smoother_apply_ms > 0.0
+    g.set_timing(True)  # restarts the count: the Jacobi CG samples its first apply the same way
+    jac = st.step(0.05, 20, rtol=1e-12, maxit=2000, precond=capi.SEM_PC_JACOBI)
+    assert jac.n_apply == 2 and jac.n_smoother_apply == 0 and jac.apply_ms > 0.0, (jac.n_apply, jac.apply_ms)
     g.set_timing(False)
     st.close()
     g.close()
