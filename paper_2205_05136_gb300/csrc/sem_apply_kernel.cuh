@@ -573,11 +573,11 @@ __device__ __forceinline__ int pipe_word(int s, int i, int j, int k) {
 }
 
 // The metric block of a unit reaches shared memory by one bulk copy (the TMA
-// engine, cp.async.bulk), which writes shared memory without going through the
-// L1 data pipe that bounds this kernel (16-byte cp.async copies of the same
-// block took about 40 of that pipe's cycles per element).  Each of a warp's two
-// stages has an mbarrier of count 1: lane 0 arrives with the expected byte count
-// and the copy's completion ends the phase.
+// engine, cp.async.bulk) that lane 0 issues; 16-byte cp.async copies from every
+// lane took four load instructions of the warp and about 11 more L1 tag-stage
+// wavefronts per element, in a kernel bound by the L1 pipes and by issue.  Each
+// of a warp's two stages has an mbarrier of count 1: lane 0 arrives with the
+// expected byte count and the copy's completion ends the phase.
 // Shared-memory addresses are passed as 32-bit shared-window offsets.
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(unsigned bar) {
