@@ -74,6 +74,13 @@ struct Gmg {
     int64_t init_kernels = 0, iter_kernels = 0, init_carried_kernels = 0, init_checked_kernels = 0;
     int64_t iter_timed_kernels = 0;
     int last_iters = 0;  // iterations the previous solve with these graphs took
+    // the set-up (variant v: applied, carried, checked) and its first `n` iterations
+    // (the first one timed when t = 1) as one graph: one launch where five were
+    struct Combo {
+      cudaGraphExec_t exec = nullptr;
+      int n = 0;
+      int64_t kernels = 0;
+    } combo[3][2];
   };
   Graphs graphs[16];
   int next_graph = 0;
@@ -1181,6 +1188,9 @@ void free_gmg_struct(Gmg* g) {
     if (gr.init_carried) cudaGraphExecDestroy(gr.init_carried);
     if (gr.init_checked) cudaGraphExecDestroy(gr.init_checked);
     if (gr.iter_timed) cudaGraphExecDestroy(gr.iter_timed);
+    for (auto& cv : gr.combo)
+      for (auto& c : cv)
+        if (c.exec) cudaGraphExecDestroy(c.exec);
   }
   if (g->capture) cudaStreamDestroy(g->capture);
   if (g->ev0) cudaEventDestroy(g->ev0);
@@ -1432,6 +1442,11 @@ int get_graphs(sem_ctx* ctx, Gmg& g, double alpha, const double* b, double* x, d
   if (gr.init_carried) { cudaGraphExecDestroy(gr.init_carried); gr.init_carried = nullptr; }
   if (gr.init_checked) { cudaGraphExecDestroy(gr.init_checked); gr.init_checked = nullptr; }
   if (gr.iter_timed) { cudaGraphExecDestroy(gr.iter_timed); gr.iter_timed = nullptr; }
+  for (auto& cv : gr.combo)
+    for (auto& c : cv) {
+      if (c.exec) cudaGraphExecDestroy(c.exec);
+      c = Gmg::Graphs::Combo();
+    }
   cudaStream_t cs = g.capture;
   const int64_t l0 = ctx->launches;
   for (int which = 0; which < 5; ++which) {
@@ -1467,6 +1482,40 @@ int get_graphs(sem_ctx* ctx, Gmg& g, double alpha, const double* b, double* x, d
   return SEM_OK;
 }
 
+// The combined graph of set-up variant v and n iterations (the first timed when
+// timed), captured on first use and again when n changes.
+template <typename T>
+int get_combo(sem_ctx* ctx, Gmg& g, Gmg::Graphs& gr, int v, bool timed, int n, double alpha, const double* b,
+              double* x, double rtol, double atol, Gmg::Graphs::Combo** out) {
+  Gmg::Graphs::Combo& c = gr.combo[v][timed ? 1 : 0];
+  if (c.exec == nullptr || c.n != n) {
+    if (c.exec) { cudaGraphExecDestroy(c.exec); c = Gmg::Graphs::Combo(); }
+    cudaStream_t cs = g.capture;
+    const int64_t l0 = ctx->launches;
+    GMG_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    int rc = pcg_init_seq<T>(ctx, g, alpha, b, x, rtol, atol, v >= 1, v == 2 ? ctx->ws.same : nullptr, cs);
+    for (int i = 0; i < n && rc == SEM_OK; ++i) rc = pcg_iter_seq<T>(ctx, g, alpha, x, timed && i == 0, cs);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
+    ctx->launches = l0;
+    if (rc != SEM_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (ec != cudaSuccess) return cuda_fail(ctx, ec, "cudaStreamEndCapture");
+    const cudaError_t ei = cudaGraphInstantiate(&c.exec, graph, 0);
+    c.kernels = count_kernels(graph);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+      c.exec = nullptr;
+      return cuda_fail(ctx, ei, "cudaGraphInstantiate");
+    }
+    c.n = n;
+  }
+  *out = &c;
+  return SEM_OK;
+}
+
 template <typename T>
 int pcg_t(sem_ctx* ctx, Gmg& g, double alpha, const double* b, double* x, double rtol,
           double atol, int maxit, int* iters, double* final_res, sem_stats* stats, bool carried,
@@ -1475,8 +1524,6 @@ int pcg_t(sem_ctx* ctx, Gmg& g, double alpha, const double* b, double* x, double
   Gmg::Graphs* gr = nullptr;
   int rc = get_graphs<T>(ctx, g, alpha, b, x, rtol, atol, &gr);
   if (rc != SEM_OK) return rc;
-  GMG_CK(cudaGraphLaunch(!carried ? gr->init : (checked ? gr->init_checked : gr->init_carried), s));
-  ctx->launches += !carried ? gr->init_kernels : (checked ? gr->init_checked_kernels : gr->init_carried_kernels);
   Timing& tm = ctx->timing;
   bool done_h = false;
   int launched = 0;
@@ -1489,11 +1536,21 @@ int pcg_t(sem_ctx* ctx, Gmg& g, double alpha, const double* b, double* x, double
     return e;
   };
   // Successive solves (time steps) take about the same number of iterations:
-  // launch the previous count before reading the scalars, so that a solve that
-  // needs no more costs one host round trip.  An iteration launched after
-  // convergence runs kernels that return at once.
+  // the set-up and the previous count go out as one graph before the scalars are
+  // read, so that a solve that needs no more costs one launch and one host round
+  // trip.  An iteration launched after convergence runs kernels that return at once.
   const int ahead = std::min(maxit, std::max(0, gr->last_iters));
-  for (; launched < ahead; ++launched) GMG_CK(launch_iter());
+  const int variant = !carried ? 0 : (checked ? 2 : 1);
+  if (ahead > 0) {
+    Gmg::Graphs::Combo* c = nullptr;
+    if ((rc = get_combo<T>(ctx, g, *gr, variant, sample, ahead, alpha, b, x, rtol, atol, &c)) != SEM_OK) return rc;
+    GMG_CK(cudaGraphLaunch(c->exec, s));
+    ctx->launches += c->kernels;
+    launched = ahead;
+  } else {
+    GMG_CK(cudaGraphLaunch(variant == 0 ? gr->init : (variant == 2 ? gr->init_checked : gr->init_carried), s));
+    ctx->launches += variant == 0 ? gr->init_kernels : (variant == 2 ? gr->init_checked_kernels : gr->init_carried_kernels);
+  }
   while (true) {
     GMG_CK(cudaMemcpyAsync(w.cg_host, w.cg, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
     GMG_CK(cudaMemcpyAsync(w.fault_host, ctx->L.fault, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
