@@ -285,7 +285,7 @@ __host__ __device__ constexpr size_t apply_warp_tile_bytes() {
 }
 
 template <int P, int QUAD, typename T, typename MT, bool DOT, bool MASS_ONLY, bool WARP = false>
-__global__ void __launch_bounds__(kApplyThreads)
+__global__ void __launch_bounds__(kApplyThreads, std::is_same<T, df>::value ? 5 : 1)
     sem_apply_kernel(const ApplyArgs<T, MT> a, const __grid_constant__ KTab<P + 1, T> tab) {
   pdl_trigger();
   static_assert(!(WARP && DOT), "the fused inner product needs the CTA-wide mode");
