@@ -60,9 +60,9 @@ FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64: 152 SMs x 2 DFMA/clk x 2 flop x ~
 # p = 4 SEM-NI slab of 2,064,933 nodes, each with the hash of the kernel sources it
 # was taken from: a figure whose kernel code has changed since is reported as null
 # (kernel_source_hash below; comments do not count).
-NCU_TRAFFIC = {(4, "LGL"): (273.06752e6 + 13.02912e6, "apply")}
-NCU_TRAFFIC_SMOOTHER = {(4, "LGL", "bf16"): (88.76544e6 + 2.226176e6, "apply")}
-NCU_SOURCE_HASH = {"apply": "8d236e67c04e68b2"}
+NCU_TRAFFIC = {(4, "LGL"): (273.026048e6 + 13.037568e6, "apply")}
+NCU_TRAFFIC_SMOOTHER = {(4, "LGL", "bf16"): (88.76416e6 + 2.234112e6, "apply")}
+NCU_SOURCE_HASH = {"apply": "4eb56ec86310c194"}
 KERNEL_SOURCES = {"apply": ("sem_apply_kernel.cuh", "sem_apply_fp32.cu", "sem_apply_fp64.cu",
                             "sem_internal.cuh")}
 
@@ -73,6 +73,11 @@ def _code_only(text: str) -> str:
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     text = re.sub(r"//[^\n]*", "", text)
     return "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+
+
+def _per_s(amount, ms):
+    """amount per second over ms milliseconds (NaN when nothing was timed)."""
+    return amount / (ms * 1e-3) if ms > 0 else float("nan")
 
 
 def kernel_source_hash(kind: str) -> str:
@@ -329,6 +334,9 @@ def time_arm(slab, precond, args, dist, dev, clocks=False):
     state = slab.new_state(-85.0, 1.0)
     stream = torch.cuda.current_stream()
     state.step(DT, args.warmup, rtol=RTOL, maxit=MAXIT, precond=precond)
+    # restarts the library's sampling of apply timings (one solve in ten, the
+    # first timed step included), so that every timed run has samples
+    slab.set_timing(True)
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
@@ -443,7 +451,7 @@ def run_gpu(args):
     iters = stats.cg_iters / max(args.steps, 1)
     apply_ms = stats.apply_ms / max(stats.n_apply, 1)
     flops = n_e * apply_flops_per_element(p, quad)
-    achieved_tf = flops / (apply_ms * 1e-3) / 1e12
+    achieved_tf = _per_s(flops, apply_ms) / 1e12 if apply_ms > 0 else None
     algo_bytes = n_e * apply_bytes_per_element(p)
     apply64_ms = st64.apply_ms / max(st64.n_apply, 1)
     pk = peaks()
@@ -451,7 +459,7 @@ def run_gpu(args):
     outer_is_df = args.arms != "fp64" and args.op_precision == "df64"
     outer = {
         "kernel": f"sem_apply_kernel<P={p},{quad},{'df64' if outer_is_df else 'f64'},dot> (outer CG operator)",
-        "launches": int(stats.cg_iters), "timed": int(stats.n_apply), "avg_ms": apply_ms,
+        "launches": int(stats.cg_iters), "timed": int(stats.n_apply), "avg_ms": apply_ms if apply_ms > 0 else None,
         "total_ms": apply_ms * stats.cg_iters,
         "fp64_equivalent_tflops": achieved_tf,
         "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": algo_bytes,
@@ -480,12 +488,13 @@ def run_gpu(args):
                     "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs), burst figure"}
     elif outer_is_df:
         roofline = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": None, "kernel": outer["kernel"],
+                    "frac": achieved_tf / FP64_PEAK_TFLOPS if achieved_tf else None, "traffic": None,
+                    "kernel": outer["kernel"],
                     "peak_note": ("FP64-equivalent flops of the double-float operator, which runs on the FP32 pipe, "
                                   "against the nominal native FP64 peak of 1.25 TFLOP/s")}
     else:
         roofline = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved_tf / FP64_PEAK_TFLOPS,
+                    "frac": achieved_tf / FP64_PEAK_TFLOPS if achieved_tf else None,
                     "traffic": args.traffic if args.traffic is not None else ncu_traffic(NCU_TRAFFIC, (p, quad)),
                     "kernel": outer["kernel"],
                     "peak_note": "nominal FP64 1.25 TFLOP/s (no FP64 figure in MEASURED_PEAKS.json; DFMA probe measured 1.19)"}
@@ -584,12 +593,13 @@ def run_gpu(args):
         },
         "steps_per_s": args.steps / (ms * 1e-3),
         "cg_iters_per_step": iters,
-        "apply_gdofs": n_d / (apply_ms * 1e-3) / 1e9,
+        "apply_gdofs": _per_s(n_d, apply_ms) / 1e9 if apply_ms > 0 else None,
         "apply_ms": apply_ms,
         "fp64_path": {"solver": "Jacobi-CG, FP64 operator", "value": ws * n_d * args.steps / (ms64 * 1e-3) / 1e9,
                       "unit": UNIT, "ms_per_step": ms64 / args.steps,
                       "cg_iters_per_step": st64.cg_iters / max(args.steps, 1),
-                      "apply_ms": apply64_ms, "apply_gdofs": n_d / (apply64_ms * 1e-3) / 1e9},
+                      "apply_ms": apply64_ms,
+                      "apply_gdofs": _per_s(n_d, apply64_ms) / 1e9 if apply64_ms > 0 else None},
         "fp64_gmg_path": {"solver": (f"flexible PCG, FP64 operator + FP64 GMG V-cycle on the same hierarchy "
                                      f"(Chebyshev({args.mg_degree}), coarse Chebyshev({args.mg_coarse_degree}))"),
                           "value": ws * n_d * args.steps / (msg64 * 1e-3) / 1e9, "unit": UNIT,
@@ -608,8 +618,8 @@ def run_gpu(args):
         "roofline": roofline,
         "kernels": kernels,
         "fp64_apply_roofline": {"bound": "alu", "kernel": f"sem_apply_kernel<P={p},{quad},f64,dot> (plain FP64 path)",
-                                "achieved": flops / (apply64_ms * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
-                                "unit": "TFLOP/s", "frac": flops / (apply64_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+                                "achieved": _per_s(flops, apply64_ms) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                                "unit": "TFLOP/s", "frac": _per_s(flops, apply64_ms) / 1e12 / FP64_PEAK_TFLOPS,
                                 "traffic": ncu_traffic(NCU_TRAFFIC, (p, quad))} if args.arms != "mixed" else None,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * 8 * n_d,
                 "d2h_bytes_per_step": 2 * 8 * n_d, "steps": n_e2e,
