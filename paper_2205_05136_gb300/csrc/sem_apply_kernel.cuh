@@ -284,8 +284,11 @@ __host__ __device__ constexpr size_t apply_warp_tile_bytes() {
   return (size_t)3 * kWarpsPerCta * WarpCfg<P>::G * (P + 1) * (P + 1) * (P + 1) * sizeof(T);
 }
 
+// The double-float kernel at p = 4 (the outer operator of the benchmark's mixed
+// step) is bound by issue and memory latency: 5 CTAs per SM at 48 registers, with
+// small spills, measured faster than 4 at 62 (at p = 3, 5, 6 it would spill far more).
 template <int P, int QUAD, typename T, typename MT, bool DOT, bool MASS_ONLY, bool WARP = false>
-__global__ void __launch_bounds__(kApplyThreads, std::is_same<T, df>::value ? 5 : 1)
+__global__ void __launch_bounds__(kApplyThreads, (std::is_same<T, df>::value && P == 4) ? 5 : 1)
     sem_apply_kernel(const ApplyArgs<T, MT> a, const __grid_constant__ KTab<P + 1, T> tab) {
   pdl_trigger();
   static_assert(!(WARP && DOT), "the fused inner product needs the CTA-wide mode");
