@@ -60,9 +60,9 @@ FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64: 152 SMs x 2 DFMA/clk x 2 flop x ~
 # p = 4 SEM-NI slab of 2,064,933 nodes, each with the hash of the kernel sources it
 # was taken from: a figure whose kernel code has changed since is reported as null
 # (kernel_source_hash below; comments do not count).
-NCU_TRAFFIC = {(4, "LGL"): (273.026048e6 + 13.037568e6, "apply")}
-NCU_TRAFFIC_SMOOTHER = {(4, "LGL", "bf16"): (88.76416e6 + 2.234112e6, "apply")}
-NCU_SOURCE_HASH = {"apply": "4eb56ec86310c194"}
+NCU_TRAFFIC = {(4, "LGL"): (273.026304e6 + 12.97408e6, "apply")}
+NCU_TRAFFIC_SMOOTHER = {(4, "LGL", "bf16"): (88.765696e6 + 1.543936e6, "apply")}
+NCU_SOURCE_HASH = {"apply": "9c6bd0526832d33d"}
 KERNEL_SOURCES = {"apply": ("sem_apply_kernel.cuh", "sem_apply_fp32.cu", "sem_apply_fp64.cu",
                             "sem_internal.cuh")}
 
