@@ -94,10 +94,10 @@ typedef struct {
   int64_t cg_iters;       /* CG iterations summed over the call */
   double last_residual;   /* ||r||_2 at the end of the last solve */
   double apply_ms;        /* device time of operator-apply kernels (when timing on) */
-  int64_t n_apply;        /* operator-apply launches timed */
+  int64_t n_apply;        /* operator-apply launches timed (one per sampled solve, see sem_set_timing) */
   int64_t kernel_launches; /* libsem kernels launched by the call */
   double smoother_apply_ms;   /* device time of timed fine-level multigrid smoother applies */
-  int64_t n_smoother_apply;   /* fine-level smoother applies timed (one per V-cycle) */
+  int64_t n_smoother_apply;   /* fine-level smoother applies timed (one per sampled solve) */
   int64_t carried_solves;     /* time-step solves whose initial residual came from the
                                  previous step's solve (no operator apply) */
 } sem_stats;
