@@ -41,3 +41,14 @@ def test_bytes_per_element_components():
         assert bench.apply_bytes_per_element(p) == 7 * 8 * n ** 3 + 4 * n ** 3 + 16 * p ** 3
         # FP32 arithmetic with the bf16 metric: 7 x 2 B per point, map, 4 + 4 B per node
         assert bench.apply_bytes_per_element_fp32(p, "bf16") == 7 * 2 * n ** 3 + 4 * n ** 3 + 8 * p ** 3
+
+
+def test_kernel_source_hash_ignores_comments_only():
+    """The source hash that keys the ncu traffic figures changes with the code
+    and not with comments or blank lines."""
+    code = "int f(int a) {\n  return a + 1;\n}\n"
+    commented = "// adds one\nint f(int a) {  // the argument\n\n  /* the sum */ return a + 1;\n}\n"
+    changed = "int f(int a) {\n  return a + 2;\n}\n"
+    assert bench._code_only(code) == bench._code_only(commented)
+    assert bench._code_only(code) != bench._code_only(changed)
+    assert len(bench.kernel_source_hash("apply")) == 16
