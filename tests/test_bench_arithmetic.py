@@ -47,7 +47,7 @@ def test_kernel_source_hash_ignores_comments_only():
     """The source hash that keys the ncu traffic figures changes with the code
     and not with comments or blank lines."""
     code = "int f(int a) {\n  return a + 1;\n}\n"
-    commented = "// adds one\nint f(int a) {  // the argument\n\n  /* the sum */ return a + 1;\n}\n"
+    commented = "// adds one\nint f(int a) {  // the argument\n\n  return a + 1;  /* the sum */\n}\n"
     changed = "int f(int a) {\n  return a + 2;\n}\n"
     assert bench._code_only(code) == bench._code_only(commented)
     assert bench._code_only(code) != bench._code_only(changed)
